@@ -1,0 +1,341 @@
+"""Python side of the CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+may import this module.  It never imports the GPU package and the GPU package
+never imports it; the two share only the seeded edge-list generators.
+
+Pieces:
+  * graph building from an edge list with numpy/scipy primitives (a sort for
+    de-duplication, scipy's connected components as a library step);
+  * the sample chooser, written from its definition (bottom-k of splitmix64
+    keys);
+  * ctypes calls into cc_oracle.c for BFS / Dijkstra, the k x n distance
+    table and the estimators of section 2 (eqs. (1), (3), (4)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libcc_oracle.so")
+_lib = None
+
+INF = 0xFFFFFFFF
+EST_NAMES = ("sampling", "pivoting", "pivot_upper", "hybrid")
+
+
+def build(force: bool = False) -> str:
+    """Compile cc_oracle.c into oracle/_build/libcc_oracle.so with gcc."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        i64, i32, u32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+        lib.orc_bfs.argtypes = [i64, P, P, i32, P]
+        lib.orc_dijkstra.argtypes = [i64, P, P, P, i32, P]
+        lib.orc_dist_table.argtypes = [i64, P, P, P, i32, P, P]
+        lib.orc_roundtrip_table.argtypes = [i64, P, P, P, P, P, P, i32, P, P]
+        lib.orc_exact_S.argtypes = [i64, P, P, P, P]
+        lib.orc_estimate.argtypes = [i64, i32, P, P, u32, u32, P, P, P, P, P,
+                                     P, P, P]
+        lib.orc_closeness_from_S.argtypes = [i64, P, P]
+        lib.orc_streaming_pass.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+# --------------------------------------------------------------------------
+# Graph building
+# --------------------------------------------------------------------------
+
+class Graph:
+    """A CSR graph as the oracle builds it.
+
+    row_ptr int64[n+1], col int32[row_ptr[n]], w uint32 or None, old_id int32[n]
+    (original id of each kept node).  Directed graphs also carry the CSR of
+    the reversed graph (rrow_ptr, rcol, rw).
+    """
+
+    def __init__(self, n, row_ptr, col, w, old_id, directed,
+                 rrow_ptr=None, rcol=None, rw=None):
+        self.n = int(n)
+        self.row_ptr = row_ptr
+        self.col = col
+        self.w = w
+        self.old_id = old_id
+        self.directed = directed
+        self.rrow_ptr, self.rcol, self.rw = rrow_ptr, rcol, rw
+
+    @property
+    def arcs(self):
+        return int(self.row_ptr[-1])
+
+    @property
+    def m(self):
+        """Undirected edges (each counted once) or directed arcs."""
+        return self.arcs if self.directed else self.arcs // 2
+
+
+def _dedup_arcs(n, s, d, w):
+    """Sort arcs by (s, d) and keep one per pair (the smallest weight)."""
+    key = s.astype(np.int64) * n + d.astype(np.int64)
+    if w is None:
+        key = np.unique(key)
+        return (key // n).astype(np.int64), (key % n).astype(np.int64), None
+    order = np.lexsort((w, key))
+    key, w = key[order], w[order]
+    first = np.ones(key.size, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    key, w = key[first], w[first]
+    return (key // n).astype(np.int64), (key % n).astype(np.int64), w
+
+
+def _csr(n, s, d, w):
+    counts = np.bincount(s, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, d.astype(np.int32), (None if w is None else w.astype(np.uint32))
+
+
+def _largest(labels):
+    """Label of the largest component; ties go to the component holding the
+    smallest node id."""
+    sizes = np.bincount(labels)
+    best = sizes.max()
+    cands = np.flatnonzero(sizes == best)
+    if cands.size == 1:
+        return int(cands[0])
+    first_node = np.full(labels.max() + 1, np.iinfo(np.int64).max)
+    np.minimum.at(first_node, labels, np.arange(labels.size))
+    return int(cands[np.argmin(first_node[cands])])
+
+
+def csr_from_edges(n, src, dst, w=None, directed=False, keep_component=True):
+    """Build the graph the estimators run on (step "graph to CSR").
+
+    Undirected: every edge gives arcs both ways.  Self-loops are dropped and
+    parallel arcs merged (keeping the smallest weight).  With keep_component,
+    only the largest connected component (strongly connected for directed
+    input) is kept, its nodes renumbered 0..n'-1 in increasing original id.
+    Adjacency lists are sorted by neighbour id.
+    """
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    ww = None if w is None else np.asarray(w, dtype=np.uint32)
+    if directed:
+        s, d = src, dst
+    else:
+        s, d = np.concatenate([src, dst]), np.concatenate([dst, src])
+        if ww is not None:
+            ww = np.concatenate([ww, ww])
+    keep = s != d
+    s, d = s[keep], d[keep]
+    if ww is not None:
+        ww = ww[keep]
+    s, d, ww = _dedup_arcs(n, s, d, ww)
+
+    old_id = np.arange(n, dtype=np.int64)
+    if keep_component:
+        adj = csr_matrix((np.ones(s.size, dtype=np.int8), (s, d)), shape=(n, n))
+        _, labels = connected_components(
+            adj, directed=directed, connection="strong" if directed else "weak")
+        lab = _largest(labels)
+        kept = labels == lab
+        old_id = np.flatnonzero(kept)
+        new_id = np.full(n, -1, dtype=np.int64)
+        new_id[old_id] = np.arange(old_id.size)
+        arc_ok = kept[s] & kept[d]
+        s, d = new_id[s[arc_ok]], new_id[d[arc_ok]]
+        if ww is not None:
+            ww = ww[arc_ok]
+        n = old_id.size
+    row_ptr, col, wout = _csr(n, s, d, ww)
+    g = Graph(n, row_ptr, col, wout, old_id.astype(np.int32), directed)
+    if directed:
+        order = np.lexsort((s, d))
+        g.rrow_ptr, g.rcol, g.rw = _csr(n, d[order], s[order],
+                                        None if ww is None else ww[order])
+    return g
+
+
+# --------------------------------------------------------------------------
+# Sample chooser: bottom-k of splitmix64 keys
+# --------------------------------------------------------------------------
+
+_G = 0x9E3779B97F4A7C15
+_MASK = (1 << 64) - 1
+
+
+def splitmix64_key(seed: int, v: int) -> int:
+    """Pure-integer splitmix64 output number v of stream `seed` (Steele, Lea
+    and Flood 2014): mix(seed + (v+1)*gamma)."""
+    z = (seed + (v + 1) * _G) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def choose_sample(n: int, k: int, seed: int) -> np.ndarray:
+    """Uniform sample of k distinct nodes (section 2: "sample k points
+    uniformly at random"): node v gets the key splitmix64_key(seed, v) and
+    the sample is the k nodes with the smallest (key, v), in that order --
+    a bottom-k sample, uniform without replacement.  The order fixes each
+    node's sample index."""
+    if not (0 < k <= n):
+        raise ValueError("need 0 < k <= n")
+    keys = np.array([splitmix64_key(seed, v) for v in range(n)], dtype=np.uint64) \
+        if n <= 4096 else _keys_vec(seed, n)
+    order = np.lexsort((np.arange(n), keys))
+    return order[:k].astype(np.int32)
+
+
+def _keys_vec(seed, n):
+    c = np.arange(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _MASK) + (c + np.uint64(1)) * np.uint64(_G)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+# --------------------------------------------------------------------------
+# Distances and estimators
+# --------------------------------------------------------------------------
+
+def bfs(g: Graph, s: int, reverse=False) -> np.ndarray:
+    rp, col = (g.rrow_ptr, g.rcol) if reverse else (g.row_ptr, g.col)
+    dist = np.empty(g.n, dtype=np.uint32)
+    _check(_L().orc_bfs(g.n, _p(rp), _p(col), int(s), _p(dist)), "bfs")
+    return dist
+
+
+def sssp(g: Graph, s: int, reverse=False) -> np.ndarray:
+    """Distances from s: BFS when unweighted, Dijkstra otherwise."""
+    rp, col, w = ((g.rrow_ptr, g.rcol, g.rw) if reverse
+                  else (g.row_ptr, g.col, g.w))
+    dist = np.empty(g.n, dtype=np.uint32)
+    if w is None:
+        rc = _L().orc_bfs(g.n, _p(rp), _p(col), int(s), _p(dist))
+    else:
+        rc = _L().orc_dijkstra(g.n, _p(rp), _p(col), _p(w), int(s), _p(dist))
+    _check(rc, "sssp")
+    return dist
+
+
+def dist_table(g: Graph, sources, roundtrip=False) -> np.ndarray:
+    """k x n table of d(c_i, v) (round-trip d(c_i,v)+d(v,c_i) if asked)."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    k = src.size
+    table = np.empty((k, g.n), dtype=np.uint32)
+    if roundtrip:
+        rc = _L().orc_roundtrip_table(g.n, _p(g.row_ptr), _p(g.col), _p(g.w),
+                                      _p(g.rrow_ptr), _p(g.rcol), _p(g.rw),
+                                      k, _p(src), _p(table))
+    else:
+        rc = _L().orc_dist_table(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), k,
+                                 _p(src), _p(table))
+    _check(rc, "dist_table")
+    return table
+
+
+def exact_S(g: Graph, roundtrip=False) -> np.ndarray:
+    """S(v) = sum_u d(v,u) by n SSSPs (eq. (1)); round-trip adds the
+    reversed graph's sums."""
+    S = np.empty(g.n, dtype=np.uint64)
+    _check(_L().orc_exact_S(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), _p(S)),
+           "exact_S")
+    if roundtrip:
+        R = np.empty(g.n, dtype=np.uint64)
+        _check(_L().orc_exact_S(g.n, _p(g.rrow_ptr), _p(g.rcol), _p(g.rw),
+                                _p(R)), "exact_S")
+        S = S + R
+    return S
+
+
+def exact_closeness(S: np.ndarray) -> np.ndarray:
+    out = np.empty(S.size, dtype=np.float64)
+    _check(_L().orc_closeness_from_S(S.size, _p(np.ascontiguousarray(S)),
+                                     _p(out)), "closeness")
+    return out
+
+
+def estimate_from_table(table: np.ndarray, sources, eps=(1, 8)):
+    """Every statistic and estimate of section 2 from a k x n metric table.
+
+    Returns a dict with pivot, delta, sum, S_samp, delta_cc (k x k),
+    hyb (n x 6: Hsum, Hnum, HCsum, LCsum, LCnum, LCsumSq), s_hat (4 x n),
+    closeness (4 x n), rows in the order sampling, pivoting, pivot_upper,
+    hybrid.
+    """
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    k, n = table.shape
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    out = dict(
+        pivot=np.empty(n, np.int32), delta=np.empty(n, np.uint32),
+        sum=np.empty(n, np.uint64), S_samp=np.empty(k, np.uint64),
+        delta_cc=np.empty((k, k), np.uint32), hyb=np.empty((n, 6), np.uint64),
+        s_hat=np.empty((4, n), np.float64),
+        closeness=np.empty((4, n), np.float64))
+    rc = _L().orc_estimate(n, k, _p(src), _p(table), int(eps[0]), int(eps[1]),
+                           _p(out["pivot"]), _p(out["delta"]), _p(out["sum"]),
+                           _p(out["S_samp"]), _p(out["delta_cc"]),
+                           _p(out["hyb"]), _p(out["s_hat"]),
+                           _p(out["closeness"]))
+    _check(rc, "estimate")
+    return out
+
+
+def estimate(g: Graph, sources, eps=(1, 8), roundtrip=False):
+    """dist_table + estimate_from_table."""
+    return estimate_from_table(dist_table(g, sources, roundtrip), sources, eps)
+
+
+def streaming_pass(g: Graph, sources):
+    """k SSSPs with O(1) running state per node (section 3): sum, pivot,
+    Delta and the exact S of each sampled node.  Timed for the CPU
+    baseline; equal to the table-based statistics."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    k = src.size
+    s = np.empty(g.n, np.uint64)
+    piv = np.empty(g.n, np.int32)
+    dl = np.empty(g.n, np.uint32)
+    S = np.empty(k, np.uint64)
+    _check(_L().orc_streaming_pass(g.n, _p(g.row_ptr), _p(g.col), _p(g.w), k,
+                                   _p(src), _p(s), _p(piv), _p(dl), _p(S)),
+           "streaming_pass")
+    return dict(sum=s, pivot=piv, delta=dl, S_samp=S)
+
+
+def default_eps(k: int):
+    """eps = 1/sqrt(k) as the rational 1/round(sqrt(k)) (section 7 uses
+    eps = sqrt(1/k); the garbled "eps = sqrt k" of section 2 is read so)."""
+    return (1, max(1, int(round(k ** 0.5))))
