@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""All-nodes closeness estimation throughput on one GB300.
+
+Workload (the configuration the headline metric is quoted on): undirected
+R-MAT scale 20, edge factor 16 (a=0.57, b=c=0.19, graph seed 1), self-loops
+and duplicates removed, largest connected component, k = 256 sources (sample
+seed 2) in one bit-packed multi-source traversal (4 uint64 words per node),
+sampling, pivoting, pivoting-upper-bound and hybrid estimates (eps = 1/16)
+for every node.
+
+A step = one cc_estimate call (every estimator for every node) with the
+graph resident in HBM.  value = k * m / step time in GTEPS (m = undirected
+edges of the kept component, each counted once).  e2e = the same call with
+pinned host output buffers (sample upload and result download inside the
+timed region).  The L2 is flushed (256 MB write) before every timed step.
+
+--impl reference times the CPU oracle (k breadth-first searches with O(1)
+running state per node) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE, EF, GSEED, SSEED, K = 20, 16, 1, 2, 256
+WORKLOAD = "rmat-s20-ef16-lcc-k256"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--k", type=int, default=K)
+    ap.add_argument("--cpu-sources", type=int, default=12,
+                    help="sources in the bounded CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def config(args, n, m):
+    return {"workload": f"rmat-s{args.scale}-ef{EF}-lcc-k{args.k}",
+            "graph": f"undirected R-MAT scale {args.scale}, edge factor {EF}, "
+                     f"a=0.57 b=c=0.19, seed {GSEED}, LCC",
+            "n": n, "m": m, "k": args.k, "sample_seed": SSEED,
+            "estimators": ["sampling", "pivoting", "pivot_upper", "hybrid"],
+            "eps": f"1/{round(args.k ** 0.5)}",
+            "l2": "flushed before every timed step (256 MB write)",
+            "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_gteps(edges, k_all, nsrc, seed=SSEED):
+    """Time the oracle's streaming pass (k BFS with O(1) state per node) on
+    `nsrc` of the k sampled sources; returns (gteps, seconds, m)."""
+    from oracle import oracle as orc
+    n, s, d = edges
+    og = orc.csr_from_edges(n, s, d)
+    C = orc.choose_sample(og.n, k_all, seed)[:nsrc]
+    t0 = time.perf_counter()
+    orc.streaming_pass(og, C)
+    dt = time.perf_counter() - t0
+    return nsrc * og.m / dt / 1e9, dt, og.m
+
+
+def run_reference(args):
+    import synth
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    edges = synth.rmat_edges(args.scale, EF, seed=GSEED)
+    from oracle import oracle as orc
+    n, s, d = edges
+    og = orc.csr_from_edges(n, s, d)
+    C = orc.choose_sample(og.n, args.k, SSEED)
+    per_step = max(1, min(4, args.cpu_sources))
+    for i in range(args.warmup):
+        orc.streaming_pass(og, C[:1])
+    times = []
+    for i in range(args.steps):
+        sub = C[(i * per_step) % args.k:][:per_step]
+        t0 = time.perf_counter()
+        orc.streaming_pass(og, sub)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = per_step * og.m * args.steps / tot / 1e9
+    sample = (f"{per_step} of the {args.k} sampled sources per step "
+              f"(streaming pass: BFS + running sum/pivot per node), single thread")
+    line = {"impl": "reference", "metric": "source-edge traversals/s (GTEPS)",
+            "value": val, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": config(args, og.n, og.m),
+            "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi missing"]}
+        time.sleep(0.15)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for row in self.f.read().splitlines():
+            parts = [x.strip() for x in row.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(path_json):
+    """Per-launch DRAM bytes from the committed ncu summary, only while the
+    kernel source is unchanged since the capture."""
+    try:
+        meta = json.load(open(path_json))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1409_0035_gb300", "csrc", "msbfs.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if meta.get("source_sha256") != sha:
+        return None
+    return meta.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1409_0035_gb300 import build as ccbuild
+    ccbuild.build()
+    import paper_1409_0035_gb300 as cc
+    import synth
+
+    edges = synth.rmat_edges(args.scale, EF, seed=GSEED)
+    g, _ = cc.cc_graph_from_edges(*edges)
+    n, arcs, _, _ = cc.cc_graph_info(g)
+    m = arcs // 2
+    k = args.k
+    C = cc.cc_sample_choose(g, k, SSEED)
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+
+    # device outputs
+    shat = torch.empty((4, n), dtype=torch.float64, device=dev)
+    clo = torch.empty((4, n), dtype=torch.float64, device=dev)
+    piv = torch.empty(n, dtype=torch.int32, device=dev)
+    dl = torch.empty(n, dtype=torch.int32, device=dev)
+    ssum = torch.empty(n, dtype=torch.int64, device=dev)
+    hyb = torch.empty((n, 6), dtype=torch.int64, device=dev)
+    o = cc.cc_out()
+    for e in range(4):
+        o.s_hat[e] = shat[e].data_ptr()
+        o.closeness[e] = clo[e].data_ptr()
+    o.pivot, o.delta, o.sample_sum, o.hyb_int = (piv.data_ptr(), dl.data_ptr(),
+                                                 ssum.data_ptr(), hyb.data_ptr())
+    opts = cc.cc_opts_default(k)
+    opts.device_outputs = 1
+    opts.stream = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        cc.cc_estimate(g, C, opts, o)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    _ = cc.cc_last_call_timing(g)
+    stats = cc.cc_last_pass_stats(g)
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    t_total, kms, kbytes, klaunch, kall = 0.0, 0.0, 0.0, 0, 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        t_total += ev0.elapsed_time(ev1)
+        nl, ms, b, nk = cc.cc_last_call_timing(g)
+        kall += nk
+        klaunch += nl
+        kms += ms
+        kbytes += b
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    ms_step = t_total / args.steps
+    value = ws * k * m * args.steps / (t_total / 1e3) / 1e9
+
+    # End to end: pinned host outputs, result download inside the region.
+    host = {"s_hat": torch.empty((4, n), dtype=torch.float64, pin_memory=True),
+            "closeness": torch.empty((4, n), dtype=torch.float64, pin_memory=True),
+            "pivot": torch.empty(n, dtype=torch.int32, pin_memory=True),
+            "delta": torch.empty(n, dtype=torch.int32, pin_memory=True),
+            "sum": torch.empty(n, dtype=torch.int64, pin_memory=True),
+            "hyb": torch.empty((n, 6), dtype=torch.int64, pin_memory=True)}
+    oh = cc.cc_out()
+    for e in range(4):
+        oh.s_hat[e] = host["s_hat"][e].data_ptr()
+        oh.closeness[e] = host["closeness"][e].data_ptr()
+    oh.pivot, oh.delta = host["pivot"].data_ptr(), host["delta"].data_ptr()
+    oh.sample_sum, oh.hyb_int = host["sum"].data_ptr(), host["hyb"].data_ptr()
+    opts_h = cc.cc_opts_default(k)
+    opts_h.stream = stream.cuda_stream
+    d2h = sum(t.numel() * t.element_size() for t in host.values())
+    h2d = k * 4
+    cc.cc_estimate(g, C, opts_h, oh)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e2e_t = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cc.cc_estimate(g, C, opts_h, oh)
+        e2e_t += time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = ws * k * m * args.steps / e2e_t / 1e9
+
+    # One source per launch: the same traversal with one bit, k launches.
+    nsingle = 16
+    t0 = time.perf_counter()
+    cc.cc_sampling_sums_single(g, C[:nsingle])
+    single_t = time.perf_counter() - t0
+    single_gteps = nsingle * m / single_t / 1e9
+
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    per_launch_bytes = kbytes / max(1, klaunch)
+    per_launch_ms = kms / max(1, klaunch)
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = kernel_traffic(os.path.join(ROOT, "profiles",
+                                          "msbfs_rmat20_k256.json"))
+    gpu_launches = kall
+
+    line = {"metric": "source-edge traversals/s (GTEPS)", "value": value,
+            "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": config(args, n, m),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "msbfs_kernel<4>", "peak_source": peak_src,
+                         "alg_bytes_per_launch": per_launch_bytes,
+                         "ms_per_launch": per_launch_ms,
+                         "launches_per_step": klaunch / args.steps},
+            "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "single_source_per_launch": {"value": single_gteps, "unit": "GTEPS",
+                                         "sources": nsingle,
+                                         "speedup": value / single_gteps},
+            "pass_stats": stats,
+            "estimates_per_s": n / (ms_step / 1e3)}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        gteps, dt, _ = cpu_oracle_gteps(edges, k, args.cpu_sources)
+        line["cpu_baseline"] = {"value": gteps, "unit": "GTEPS", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"{args.cpu_sources} of the {k} sources "
+                                          f"(streaming BFS pass), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cc.cc_graph_free(g)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

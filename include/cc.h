@@ -1,0 +1,223 @@
+/*
+ * cc.h -- C ABI of the GB300 (sm_103a) library for all-nodes classic
+ * closeness estimation after Cohen, Delling, Pajor and Werneck, "Computing
+ * Classic Closeness Centrality, at Scale" (2014).
+ *
+ * Problem (eq. (1)): for a connected undirected graph G = (V, E) with n = |V|
+ * nodes, B^-1(v) = (n-1) / S(v) with S(v) = sum_u d_vu.  For a strongly
+ * connected directed graph the round-trip distance d_uv + d_vu is used
+ * instead (section 6.1).
+ *
+ * Method (sections 2 and 3): choose a uniform sample C = (c_0 .. c_{k-1}) of
+ * k nodes, run one shortest-path traversal from every sampled node (BFS when
+ * unweighted, SSSP with uint32 arc lengths otherwise) and reduce the
+ * distances on the fly into per-node statistics, never storing the k x n
+ * distance matrix.  From them the library forms, for every node, the sampling
+ * estimate (eq. (3)), the pivoting estimate B(c(v)), the pivoting upper bound
+ * B(c(v)) + Delta(v) and the hybrid estimate (eq. (4)).
+ *
+ * Conventions for every entry point:
+ *   - returns CC_OK (0) or a negative CC_ERR_* code; no exception crosses the
+ *     ABI; cc_strerror() names a code;
+ *   - host pointers unless stated; the library copies every input it keeps
+ *     and never takes ownership of caller memory;
+ *   - calls are synchronous: when one returns, its outputs are written;
+ *   - a graph handle may be used by one thread at a time.
+ *
+ * Readings of the paper fixed by this interface:
+ *   - eps is the rational eps_num / eps_den with 0 < eps_num <= eps_den;
+ *     "distance greater than Delta/eps" is evaluated exactly as
+ *     d * eps_num > Delta * eps_den (strictly greater goes to H / HC);
+ *   - the pivot c(v) is the sampled node at minimum distance, ties to the
+ *     smallest sample index; a sampled node is its own pivot;
+ *   - every estimator returns the exact S(v) for v in C;
+ *   - FP64 results: the integer numerator is formed in 128 bits, converted
+ *     to double once and divided once.
+ */
+#ifndef CC_GB300_H
+#define CC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define CC_OK 0
+#define CC_ERR_ARG (-1)          /* bad argument (null, range, duplicate) */
+#define CC_ERR_GRAPH (-2)        /* malformed graph (ids out of range, n<2) */
+#define CC_ERR_DISCONNECTED (-3) /* closeness undefined: not (strongly) connected */
+#define CC_ERR_OOM (-4)          /* device or host allocation failed */
+#define CC_ERR_TIMEOUT (-5)      /* a bounded device-side wait ran out */
+#define CC_ERR_CUDA (-6)         /* a CUDA runtime call failed */
+#define CC_ERR_TOO_LARGE (-7)    /* size beyond a documented limit */
+#define CC_ERR_NO_DEVICE (-8)    /* no usable CUDA device */
+
+/* Maximum sample size: k sources are packed 64 per uint64 word, at most 32
+ * words per node. */
+#define CC_MAX_K 2048
+
+/* ---- graphs ------------------------------------------------------------ */
+typedef struct cc_graph *cc_graph_t;
+
+/*
+ * cc_graph_from_edges -- build the device-resident graph the estimators run
+ * on (the "graph to CSR" step; section 7 counts this preprocessing in its
+ * times).
+ *   n              number of node ids; every src[e], dst[e] must be < n
+ *   m              number of edges in src/dst (and w)
+ *   src, dst       uint32[m] edge endpoints (host)
+ *   w              uint32[m] arc lengths >= 1, or NULL for unweighted
+ *   directed       0: each edge is undirected (arcs both ways);
+ *                  1: each edge is the arc src -> dst
+ *   keep_component 1: keep only the largest connected component (largest
+ *                  strongly connected component when directed; ties to the
+ *                  component holding the smallest id); 0: keep every node
+ *   out            receives the handle
+ *   old_id_out     optional int32[n] (caller-owned): old_id_out[v'] = the
+ *                  original id of kept node v' for v' < n' (the kept count,
+ *                  from cc_graph_info); entries beyond n' are untouched
+ * Self-loops are dropped, parallel arcs merged keeping the smallest length,
+ * kept nodes renumbered 0..n'-1 in increasing original id, adjacency lists
+ * sorted by neighbour.  Errors: CC_ERR_ARG, CC_ERR_GRAPH, CC_ERR_OOM,
+ * CC_ERR_CUDA, CC_ERR_TOO_LARGE (more than 2^31-1 arcs or nodes).
+ */
+int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src,
+                        const uint32_t *dst, const uint32_t *w, int directed,
+                        int keep_component, cc_graph_t *out,
+                        int32_t *old_id_out);
+
+/* Same as cc_graph_from_edges with the arcs given as a CSR
+ * (row_ptr int64[n+1], col int32[row_ptr[n]], w uint32[row_ptr[n]] or NULL):
+ * arc e of row u is u -> col[e].  For undirected graphs each listed arc
+ * also gives its reverse. */
+int cc_graph_load_csr(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                      const uint32_t *w, int directed, int keep_component,
+                      cc_graph_t *out, int32_t *old_id_out);
+
+/* Release the handle and all device memory it owns. */
+int cc_graph_free(cc_graph_t g);
+
+/* Sizes of a built graph: n kept nodes, arcs (CSR entries: 2m undirected,
+ * m directed), directed and weighted flags.  Any pointer may be NULL. */
+int cc_graph_info(cc_graph_t g, int64_t *n, int64_t *arcs, int *directed,
+                  int *weighted);
+
+/* Copy the built CSR back to caller host buffers (row_ptr int64[n+1],
+ * col int32[arcs], w uint32[arcs] or NULL).  With reverse = 1 the CSR of
+ * the reversed graph (directed graphs only). */
+int cc_graph_copy_csr(cc_graph_t g, int reverse, int64_t *row_ptr,
+                      int32_t *col, uint32_t *w);
+
+/* ---- sample ---------------------------------------------------------- */
+/*
+ * cc_sample_choose -- uniform sample of k distinct nodes (section 2: "sample
+ * k points uniformly at random"; Algorithm 1, first step).  Node v gets the
+ * key splitmix64(seed, v) = mix(seed + (v+1) * 0x9E3779B97F4A7C15) with the
+ * splitmix64 output function mix (Steele, Lea, Flood 2014); the sample is the
+ * k nodes with the smallest (key, v), in that order (bottom-k sampling,
+ * uniform without replacement).  sample_out int32[k] (host).  Computed on the
+ * device.  Errors: CC_ERR_ARG (k < 1, k > n or k > CC_MAX_K).
+ */
+int cc_sample_choose(cc_graph_t g, int32_t k, uint64_t seed,
+                     int32_t *sample_out);
+
+/* ---- estimation -------------------------------------------------------- */
+#define CC_EST_SAMPLING 0     /* eq. (3): (n-1)/k * sum_i d(c_i, v)   */
+#define CC_EST_PIVOTING 1     /* S(c(v))                                */
+#define CC_EST_PIVOT_UPPER 2  /* S(c(v)) + (n-1) Delta(v)               */
+#define CC_EST_HYBRID 3       /* eq. (4)                                */
+#define CC_NUM_EST 4
+
+/* Output pointers: host memory unless cc_opts.device_outputs = 1 (then
+ * device pointers on the current device).  Every pointer may be NULL. */
+typedef struct {
+    double *s_hat[CC_NUM_EST];     /* n each: estimate of S(v)            */
+    double *closeness[CC_NUM_EST]; /* n each: (n-1) / s_hat               */
+    int32_t *pivot;                /* n: c(v) as a sample index           */
+    uint32_t *delta;               /* n: Delta(v) = d(v, c(v))            */
+    uint64_t *sample_sum;          /* n: sum_i d(c_i, v)                  */
+    uint64_t *hyb_int;             /* n x 6: Hsum Hnum HCsum LCsum LCnum
+                                      LCsumSq of eq. (4); zeros for v in C */
+    uint64_t *S_sampled;           /* k: exact S(c_i)                     */
+    uint32_t *delta_cc;            /* k x k: d(c_i, c_j), row i           */
+} cc_out;
+
+typedef struct {
+    uint32_t eps_num, eps_den; /* hybrid eps = num/den; 0 < num <= den    */
+    int32_t want_hybrid;       /* 1: run the second traversal when eq. (4)
+                                  needs it; 0: skip (hybrid outputs unset) */
+    int32_t roundtrip;         /* directed graphs: 1 = round-trip distances
+                                  (section 6.1); required for directed     */
+    int32_t device_outputs;    /* 1: cc_out pointers are device pointers   */
+    void *stream;              /* cudaStream_t, NULL = legacy default      */
+} cc_opts;
+
+/* Fill defaults: eps = 1/round(sqrt(k)) (section 7: eps = sqrt(1/k)),
+ * want_hybrid = 1, roundtrip = 0, host outputs, default stream. */
+void cc_opts_default(cc_opts *o, int32_t k);
+
+/*
+ * cc_estimate -- all-nodes estimates from one seeded sample.
+ *   sample  int32[k] distinct node ids (host), e.g. from cc_sample_choose;
+ *           sample index i fixes the bit position and the pivot tie-break.
+ * Runs the k traversals as one bit-packed multi-source pass (pass 1: sums,
+ * pivots, Delta, d(c_i, c_j), per-source distance histograms) and, when the
+ * hybrid needs per-node thresholds below the largest sampled distance, a
+ * second pass with the per-node L(v) masks (section 3, Algorithm 1).
+ * Errors: CC_ERR_ARG, CC_ERR_DISCONNECTED, CC_ERR_OOM, CC_ERR_TIMEOUT,
+ * CC_ERR_CUDA, CC_ERR_TOO_LARGE (a distance >= 2^32-1).
+ */
+int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k,
+                const cc_opts *opts, cc_out *out);
+
+/*
+ * cc_exact -- exact S(v) and B^-1(v) = (n-1)/S(v) for every node (eq. (1))
+ * by traversals from every node, packed 64 per word.  Meant for small
+ * graphs (the cost is n traversals).  closeness double[n], S uint64[n] (host,
+ * either may be NULL).  Errors as cc_estimate.
+ */
+int cc_exact(cc_graph_t g, double *closeness, uint64_t *S);
+
+/*
+ * cc_sampling_sums_single -- reference form of the sampling pass: k
+ * separate single-source traversals, one launch per sampled node, each adding
+ * its distances to sum[v] (section 3, second paragraph).  Same results as
+ * cc_estimate's sample_sum; kept to measure what bit-packing k sources per
+ * traversal buys.  sum uint64[n] (host), S_sampled uint64[k] (host, may be
+ * NULL).
+ */
+int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k,
+                            uint64_t *sum, uint64_t *S_sampled);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/* Counters of the last traversal pass run on g: levels, top-down and
+ * bottom-up levels, CSR entries examined and frontier words gathered.
+ * Any pointer may be NULL. */
+int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td_levels,
+                       int64_t *bu_levels, int64_t *edges_examined,
+                       int64_t *words_gathered);
+
+/* Traversal kernel launches of the last cc_estimate / cc_exact /
+ * cc_sampling_sums_single call on g: their number, their summed device time
+ * in ms (CUDA events recorded on the launching stream around each launch)
+ * and the algorithmic bytes they moved under the library's roofline model
+ * (frontier words gathered x 8 B, CSR entries x 4 B, three W-word state
+ * arrays per node and level, row offsets of top-down levels, per-node
+ * results), and the number of all library kernels the call launched.
+ * Any pointer may be NULL. */
+int cc_last_call_timing(cc_graph_t g, int32_t *launches, double *kernel_ms,
+                        double *alg_bytes, int32_t *all_kernels);
+
+/* Run the device-side bounded wait on a barrier that can never complete
+ * (a team larger than the blocks launched) with the given limit; returns
+ * CC_ERR_TIMEOUT when the wait gives up as designed. */
+int cc_selftest_barrier_timeout(uint64_t timeout_ns);
+
+const char *cc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CC_GB300_H */

@@ -1,0 +1,245 @@
+"""Thin Python binding of libcc_gb300.so (the C ABI in include/cc.h).
+
+Every cc_* function here marshals arguments and calls the C entry point of
+the same name; all computation runs in the library's sm_103a kernels.  The
+library must be built (``paper_1409_0035_gb300.build.build()``); importing
+fails loudly when it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcc_gb300.so")
+
+CC_OK = 0
+CC_ERR_ARG = -1
+CC_ERR_GRAPH = -2
+CC_ERR_DISCONNECTED = -3
+CC_ERR_OOM = -4
+CC_ERR_TIMEOUT = -5
+CC_ERR_CUDA = -6
+CC_ERR_TOO_LARGE = -7
+CC_ERR_NO_DEVICE = -8
+CC_MAX_K = 2048
+CC_NUM_EST = 4
+EST_NAMES = ("sampling", "pivoting", "pivot_upper", "hybrid")
+
+# Every symbol include/cc.h declares.
+EXPORTS = (
+    "cc_graph_from_edges", "cc_graph_load_csr", "cc_graph_free", "cc_graph_info",
+    "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
+    "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
+    "cc_last_call_timing",
+    "cc_selftest_barrier_timeout", "cc_strerror",
+)
+
+
+class CCError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {cc_strerror(code)} ({code})")
+        self.code = code
+
+
+class cc_opts(ctypes.Structure):
+    _fields_ = [("eps_num", ctypes.c_uint32), ("eps_den", ctypes.c_uint32),
+                ("want_hybrid", ctypes.c_int32), ("roundtrip", ctypes.c_int32),
+                ("device_outputs", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class cc_out(ctypes.Structure):
+    _fields_ = [("s_hat", ctypes.c_void_p * CC_NUM_EST),
+                ("closeness", ctypes.c_void_p * CC_NUM_EST),
+                ("pivot", ctypes.c_void_p), ("delta", ctypes.c_void_p),
+                ("sample_sum", ctypes.c_void_p), ("hyb_int", ctypes.c_void_p),
+                ("S_sampled", ctypes.c_void_p), ("delta_cc", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcc_gb300.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run "
+                              "paper_1409_0035_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        c_int = ctypes.c_int
+        L.cc_graph_from_edges.argtypes = [i64, i64, P, P, P, c_int, c_int, P, P]
+        L.cc_graph_load_csr.argtypes = [i64, P, P, P, c_int, c_int, P, P]
+        L.cc_graph_free.argtypes = [P]
+        L.cc_graph_info.argtypes = [P, P, P, P, P]
+        L.cc_graph_copy_csr.argtypes = [P, c_int, P, P, P]
+        L.cc_sample_choose.argtypes = [P, i32, u64, P]
+        L.cc_opts_default.argtypes = [P, i32]
+        L.cc_opts_default.restype = None
+        L.cc_estimate.argtypes = [P, P, i32, P, P]
+        L.cc_exact.argtypes = [P, P, P]
+        L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
+        L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
+        L.cc_last_call_timing.argtypes = [P, P, P, P, P]
+        L.cc_selftest_barrier_timeout.argtypes = [u64]
+        L.cc_strerror.argtypes = [c_int]
+        L.cc_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _chk(rc, what):
+    if rc != CC_OK:
+        raise CCError(rc, what)
+
+
+def cc_strerror(code: int) -> str:
+    return lib().cc_strerror(int(code)).decode()
+
+
+# ---------------------------------------------------------------- graphs
+
+def cc_graph_from_edges(n, src, dst, w=None, directed=False, keep_component=True):
+    """Returns (handle, old_id) -- see include/cc.h."""
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    ww = None if w is None else np.ascontiguousarray(w, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    old = np.empty(int(n), dtype=np.int32)
+    _chk(lib().cc_graph_from_edges(int(n), src.size, _p(src), _p(dst), _p(ww),
+                                   int(directed), int(keep_component),
+                                   ctypes.byref(h), _p(old)), "cc_graph_from_edges")
+    nn = cc_graph_info(h.value)[0]
+    return h.value, old[:nn].copy()
+
+
+def cc_graph_load_csr(n, row_ptr, col, w=None, directed=False, keep_component=True):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    ww = None if w is None else np.ascontiguousarray(w, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    old = np.empty(int(n), dtype=np.int32)
+    _chk(lib().cc_graph_load_csr(int(n), _p(rp), _p(cl), _p(ww), int(directed),
+                                 int(keep_component), ctypes.byref(h), _p(old)),
+         "cc_graph_load_csr")
+    nn = cc_graph_info(h.value)[0]
+    return h.value, old[:nn].copy()
+
+
+def cc_graph_free(g):
+    _chk(lib().cc_graph_free(g), "cc_graph_free")
+
+
+def cc_graph_info(g):
+    """(n, arcs, directed, weighted)."""
+    n, a = ctypes.c_int64(), ctypes.c_int64()
+    d, w = ctypes.c_int(), ctypes.c_int()
+    _chk(lib().cc_graph_info(g, ctypes.byref(n), ctypes.byref(a), ctypes.byref(d),
+                             ctypes.byref(w)), "cc_graph_info")
+    return n.value, a.value, bool(d.value), bool(w.value)
+
+
+def cc_graph_copy_csr(g, reverse=False):
+    n, arcs, _, weighted = cc_graph_info(g)
+    rp = np.empty(n + 1, np.int64)
+    col = np.empty(arcs, np.int32)
+    w = np.empty(arcs, np.uint32) if weighted else None
+    _chk(lib().cc_graph_copy_csr(g, int(reverse), _p(rp), _p(col), _p(w)),
+         "cc_graph_copy_csr")
+    return rp, col, w
+
+
+# ---------------------------------------------------------------- estimation
+
+def cc_sample_choose(g, k, seed):
+    out = np.empty(int(k), np.int32)
+    _chk(lib().cc_sample_choose(g, int(k), ctypes.c_uint64(seed & (2**64 - 1)),
+                                _p(out)), "cc_sample_choose")
+    return out
+
+
+def cc_opts_default(k):
+    o = cc_opts()
+    lib().cc_opts_default(ctypes.byref(o), int(k))
+    return o
+
+
+def cc_estimate(g, sample, opts=None, out=None):
+    """Low-level call: `out` is a filled cc_out (host or device pointers per
+    opts.device_outputs).  Without `out`, allocates host numpy outputs and
+    returns them as a dict."""
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    k = sample.size
+    if opts is None:
+        opts = cc_opts_default(k)
+    if out is not None:
+        _chk(lib().cc_estimate(g, _p(sample), k, ctypes.byref(opts), ctypes.byref(out)),
+             "cc_estimate")
+        return out
+    n = cc_graph_info(g)[0]
+    res = dict(s_hat=np.zeros((CC_NUM_EST, n)), closeness=np.zeros((CC_NUM_EST, n)),
+               pivot=np.empty(n, np.int32), delta=np.empty(n, np.uint32),
+               sum=np.empty(n, np.uint64), hyb=np.zeros((n, 6), np.uint64),
+               S_samp=np.empty(k, np.uint64), delta_cc=np.empty((k, k), np.uint32))
+    o = cc_out()
+    for e in range(CC_NUM_EST):
+        o.s_hat[e] = _p(res["s_hat"][e])
+        o.closeness[e] = _p(res["closeness"][e])
+    o.pivot, o.delta = _p(res["pivot"]), _p(res["delta"])
+    o.sample_sum, o.hyb_int = _p(res["sum"]), _p(res["hyb"])
+    o.S_sampled, o.delta_cc = _p(res["S_samp"]), _p(res["delta_cc"])
+    _chk(lib().cc_estimate(g, _p(sample), k, ctypes.byref(opts), ctypes.byref(o)),
+         "cc_estimate")
+    return res
+
+
+def cc_exact(g):
+    """(closeness, S) for every node."""
+    n = cc_graph_info(g)[0]
+    c = np.empty(n, np.float64)
+    S = np.empty(n, np.uint64)
+    _chk(lib().cc_exact(g, _p(c), _p(S)), "cc_exact")
+    return c, S
+
+
+def cc_sampling_sums_single(g, sample):
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    n = cc_graph_info(g)[0]
+    s = np.empty(n, np.uint64)
+    S = np.empty(sample.size, np.uint64)
+    _chk(lib().cc_sampling_sums_single(g, _p(sample), sample.size, _p(s), _p(S)),
+         "cc_sampling_sums_single")
+    return s, S
+
+
+def cc_last_pass_stats(g):
+    vals = [ctypes.c_int64() for _ in range(5)]
+    _chk(lib().cc_last_pass_stats(g, *[ctypes.byref(v) for v in vals]),
+         "cc_last_pass_stats")
+    return dict(zip(("levels", "td_levels", "bu_levels", "edges", "words"),
+                    [v.value for v in vals]))
+
+
+def cc_last_call_timing(g):
+    """(traversal launches, their kernel ms, alg bytes, all kernel launches)
+    of the last traversal call on g."""
+    n, a = ctypes.c_int32(), ctypes.c_int32()
+    ms, b = ctypes.c_double(), ctypes.c_double()
+    _chk(lib().cc_last_call_timing(g, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
+                                   ctypes.byref(a)), "cc_last_call_timing")
+    return n.value, ms.value, b.value, a.value
+
+
+def cc_selftest_barrier_timeout(timeout_ns):
+    return lib().cc_selftest_barrier_timeout(ctypes.c_uint64(int(timeout_ns)))

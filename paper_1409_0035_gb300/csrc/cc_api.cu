@@ -1,0 +1,645 @@
+// C ABI and host runtime: graph residency, workspace, the traversal passes
+// and the estimator pipeline (section 3, Algorithm 1: a pivot/sum pass over
+// all k sources, then the hybrid pass when eq. (4) needs per-node L(v)).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cc_internal.h"
+#include "estimate.h"
+
+using namespace ccg;
+
+namespace {
+
+constexpr uint64_t kTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
+constexpr int kAlpha = 14;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes)
+    {
+        if (bytes <= cap) return CC_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            return CC_ERR_OOM;
+        }
+        cap = bytes;
+        return CC_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Degree classes of one CSR for the bottom-up scan.
+struct Classes {
+    DevBuf L, M, H, Hn, Hb;
+    int64_t nL = 0, nM = 0, nH = 0, nHch = 0;
+};
+
+struct DevCSR {
+    DevBuf rp, col, w;
+    Classes cls;
+};
+
+}  // namespace
+
+struct cc_graph {
+    int64_t n = 0, arcs = 0;
+    bool directed = false, weighted = false;
+    DevCSR fw, rv;
+    // workspace
+    DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
+        dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum;
+    int hist_cap = 0;
+    Ctl last{};
+    // Traversal launches of the last API call: count, device time (CUDA
+    // events on the launching stream) and modelled algorithmic bytes.
+    int call_launches = 0, call_kernels = 0;
+    double call_ms = 0.0, call_bytes = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+#define CK(x)                                                   \
+    do {                                                        \
+        cudaError_t e_ = (x);                                   \
+        if (e_ != cudaSuccess) { cudaGetLastError(); return CC_ERR_CUDA; } \
+    } while (0)
+#define RC(x)                      \
+    do {                           \
+        int r_ = (x);              \
+        if (r_ != CC_OK) return r_; \
+    } while (0)
+
+int upload(DevBuf &b, const void *src, size_t bytes)
+{
+    RC(b.ensure(bytes));
+    if (bytes) CK(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+    return CC_OK;
+}
+
+int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c)
+{
+    std::vector<int32_t> L, M, H, Hn;
+    std::vector<int64_t> Hb;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = rp[v + 1] - rp[v];
+        if (d <= kLightMaxDeg) L.push_back((int32_t)v);
+        else if (d <= kMediumMaxDeg) M.push_back((int32_t)v);
+        else {
+            H.push_back((int32_t)v);
+            for (int64_t b = rp[v]; b < rp[v + 1]; b += kChunk) {
+                Hn.push_back((int32_t)v);
+                Hb.push_back(b);
+            }
+        }
+    }
+    c.nL = (int64_t)L.size(); c.nM = (int64_t)M.size(); c.nH = (int64_t)H.size();
+    c.nHch = (int64_t)Hn.size();
+    RC(upload(c.L, L.data(), L.size() * 4));
+    RC(upload(c.M, M.data(), M.size() * 4));
+    RC(upload(c.H, H.data(), H.size() * 4));
+    RC(upload(c.Hn, Hn.data(), Hn.size() * 4));
+    RC(upload(c.Hb, Hb.data(), Hb.size() * 8));
+    return CC_OK;
+}
+
+int upload_csr(DevCSR &d, int64_t n, const std::vector<int64_t> &rp,
+               const std::vector<int32_t> &col, const std::vector<uint32_t> &w)
+{
+    RC(upload(d.rp, rp.data(), rp.size() * 8));
+    RC(upload(d.col, col.data(), col.size() * 4));
+    if (!w.empty()) RC(upload(d.w, w.data(), w.size() * 4));
+    return build_classes(rp, n, d.cls);
+}
+
+int pow2_words(int k)
+{
+    const int need = (k + 63) / 64;
+    int W = 1;
+    while (W < need) W <<= 1;
+    return W;
+}
+
+int ensure_state(cc_graph *g, int W)
+{
+    const int64_t n = g->n;
+    const size_t nw = (size_t)n * W * 8;
+    RC(g->vis.ensure(nw));
+    RC(g->F0.ensure(nw));
+    RC(g->F1.ensure(nw));
+    RC(g->nxt.ensure(nw));
+    RC(g->Q0.ensure(n * 4));
+    RC(g->Q1.ensure(n * 4));
+    RC(g->T.ensure(n * 4));
+    RC(g->tflag.ensure(n * 4));
+    RC(g->sidx.ensure(n * 4));
+    RC(g->sum2.ensure(n * 16));
+    RC(g->ctl.ensure(sizeof(Ctl)));
+    return CC_OK;
+}
+
+BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
+{
+    BfsJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = g->n;
+    j.arcs = g->arcs;
+    j.rp = csr.rp.as<int64_t>();
+    j.col = csr.col.as<int32_t>();
+    j.Llist = csr.cls.L.as<int32_t>();
+    j.Mlist = csr.cls.M.as<int32_t>();
+    j.Hlist = csr.cls.H.as<int32_t>();
+    j.nL = csr.cls.nL;
+    j.nM = csr.cls.nM;
+    j.nH = csr.cls.nH;
+    j.Hch_node = csr.cls.Hn.as<int32_t>();
+    j.Hch_begin = csr.cls.Hb.as<int64_t>();
+    j.nHch = csr.cls.nHch;
+    j.vis = g->vis.as<uint64_t>();
+    j.F0 = g->F0.as<uint64_t>();
+    j.F1 = g->F1.as<uint64_t>();
+    j.nxt = g->nxt.as<uint64_t>();
+    j.Q0 = g->Q0.as<int32_t>();
+    j.Q1 = g->Q1.as<int32_t>();
+    j.T = g->T.as<int32_t>();
+    j.tflag = g->tflag.as<unsigned>();
+    j.sidx = g->sidx.as<int32_t>();
+    j.sum2 = g->sum2.as<uint64_t>();
+    j.ctl = g->ctl.as<Ctl>();
+    j.timeout_ns = kTimeoutNs;
+    j.alpha = kAlpha;
+    (void)W;
+    return j;
+}
+
+void reset_timing(cc_graph *g)
+{
+    g->call_launches = 0;
+    g->call_kernels = 0;
+    g->call_ms = 0.0;
+    g->call_bytes = 0.0;
+}
+
+// Algorithmic bytes of one traversal pass (the roofline model of the design
+// notes): every frontier word gathered (8 B) with its CSR entry (4 B, one per
+// W words), three word arrays (visited, frontier in, frontier out) per node
+// and level, the row offsets of top-down levels and R bytes of per-node
+// results.
+double pass_bytes(const Ctl &c, int64_t n, int W, uint32_t red)
+{
+    const double words = (double)c.words;
+    const double R = (red & RED_LC) ? 16.0 : ((red & RED_PIVOT) ? 24.0 : 16.0);
+    return words * 8.0 + words / W * 4.0 + (double)c.levels * n * 8.0 * W * 3.0 +
+           (double)c.td_levels * (n + 1) * 8.0 + (double)n * R;
+}
+
+// Launch one pass and wait for it; copies the control block to g->last.
+int run_pass(cc_graph *g, int W, const BfsJob &j, cudaStream_t st)
+{
+    if (!g->ev0) {
+        CK(cudaEventCreate(&g->ev0));
+        CK(cudaEventCreate(&g->ev1));
+    }
+    CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), st));
+    CK(cudaEventRecord(g->ev0, st));
+    RC(launch_msbfs(W, j, st, nullptr));
+    CK(cudaEventRecord(g->ev1, st));
+    CK(cudaMemcpyAsync(&g->last, g->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    g->call_launches += 1;
+    g->call_kernels += 1;
+    g->call_ms += ms;
+    g->call_bytes += pass_bytes(g->last, g->n, W, j.red);
+    if (g->last.err < 0) return g->last.err;
+    return CC_OK;
+}
+
+int validate_sample(const cc_graph *g, const int32_t *sample, int32_t k)
+{
+    if (!sample || k < 1 || k > CC_MAX_K || k > g->n) return CC_ERR_ARG;
+    std::vector<char> seen((size_t)g->n, 0);
+    for (int i = 0; i < k; ++i) {
+        const int32_t c = sample[i];
+        if (c < 0 || c >= g->n || seen[c]) return CC_ERR_ARG;
+        seen[c] = 1;
+    }
+    return CC_OK;
+}
+
+int finish_graph(cc_graph *g, HostCSR &h)
+{
+    g->n = h.n;
+    g->arcs = (int64_t)h.col.size();
+    g->weighted = !h.w.empty();
+    RC(upload_csr(g->fw, h.n, h.rp, h.col, h.w));
+    if (h.has_rev) RC(upload_csr(g->rv, h.n, h.rrp, h.rcol, h.rw));
+    return CC_OK;
+}
+
+void free_graph(cc_graph *g)
+{
+    DevBuf *all[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
+                     &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->rv.rp, &g->rv.col,
+                     &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
+                     &g->rv.cls.Hb, &g->vis, &g->F0, &g->F1, &g->nxt, &g->Q0, &g->Q1,
+                     &g->T, &g->tflag, &g->sidx, &g->sum2, &g->pivot, &g->delta, &g->lc2,
+                     &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
+                     &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
+                     &g->hyb, &g->ssum};
+    for (DevBuf *b : all) b->release();
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    g->ev0 = g->ev1 = nullptr;
+}
+
+int device_ok()
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return CC_ERR_NO_DEVICE;
+    }
+    return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cc_strerror(int code)
+{
+    switch (code) {
+    case CC_OK: return "ok";
+    case CC_ERR_ARG: return "invalid argument";
+    case CC_ERR_GRAPH: return "malformed graph";
+    case CC_ERR_DISCONNECTED: return "graph not (strongly) connected: closeness undefined";
+    case CC_ERR_OOM: return "out of memory";
+    case CC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case CC_ERR_CUDA: return "CUDA runtime error";
+    case CC_ERR_TOO_LARGE: return "size beyond a documented limit";
+    case CC_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+    }
+}
+
+void cc_opts_default(cc_opts *o, int32_t k)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->eps_num = 1;
+    o->eps_den = (uint32_t)std::max(1L, std::lround(std::sqrt((double)std::max(k, 1))));
+    o->want_hybrid = 1;
+}
+
+int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_t *dst,
+                        const uint32_t *w, int directed, int keep_component,
+                        cc_graph_t *out, int32_t *old_id_out)
+{
+    if (!out) return CC_ERR_ARG;
+    *out = nullptr;
+    RC(device_ok());
+    HostCSR h;
+    RC(build_host_csr(n, m, src, dst, w, directed != 0, keep_component != 0, h));
+    cc_graph *g = new (std::nothrow) cc_graph();
+    if (!g) return CC_ERR_OOM;
+    g->directed = directed != 0;
+    const int rc = finish_graph(g, h);
+    if (rc != CC_OK) {
+        free_graph(g);
+        delete g;
+        return rc;
+    }
+    if (old_id_out) std::memcpy(old_id_out, h.old_id.data(), h.old_id.size() * 4);
+    *out = g;
+    return CC_OK;
+}
+
+int cc_graph_load_csr(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                      const uint32_t *w, int directed, int keep_component,
+                      cc_graph_t *out, int32_t *old_id_out)
+{
+    if (!row_ptr || n < 2) return CC_ERR_ARG;
+    const int64_t m = row_ptr[n];
+    if (m > 0 && !col) return CC_ERR_ARG;
+    std::vector<uint32_t> s((size_t)m), d((size_t)m);
+    for (int64_t u = 0; u < n; ++u) {
+        if (row_ptr[u + 1] < row_ptr[u]) return CC_ERR_GRAPH;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            if (col[e] < 0) return CC_ERR_GRAPH;
+            s[e] = (uint32_t)u;
+            d[e] = (uint32_t)col[e];
+        }
+    }
+    return cc_graph_from_edges(n, m, s.data(), d.data(), w, directed, keep_component, out,
+                               old_id_out);
+}
+
+int cc_graph_free(cc_graph_t g)
+{
+    if (!g) return CC_ERR_ARG;
+    free_graph(g);
+    delete g;
+    return CC_OK;
+}
+
+int cc_graph_info(cc_graph_t g, int64_t *n, int64_t *arcs, int *directed, int *weighted)
+{
+    if (!g) return CC_ERR_ARG;
+    if (n) *n = g->n;
+    if (arcs) *arcs = g->arcs;
+    if (directed) *directed = g->directed;
+    if (weighted) *weighted = g->weighted;
+    return CC_OK;
+}
+
+int cc_graph_copy_csr(cc_graph_t g, int reverse, int64_t *row_ptr, int32_t *col,
+                      uint32_t *w)
+{
+    if (!g || (reverse && !g->directed)) return CC_ERR_ARG;
+    const DevCSR &c = reverse ? g->rv : g->fw;
+    if (row_ptr) CK(cudaMemcpy(row_ptr, c.rp.p, (g->n + 1) * 8, cudaMemcpyDeviceToHost));
+    if (col) CK(cudaMemcpy(col, c.col.p, g->arcs * 4, cudaMemcpyDeviceToHost));
+    if (w && g->weighted) CK(cudaMemcpy(w, c.w.p, g->arcs * 4, cudaMemcpyDeviceToHost));
+    return CC_OK;
+}
+
+int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td, int64_t *bu,
+                       int64_t *edges, int64_t *words)
+{
+    if (!g) return CC_ERR_ARG;
+    if (levels) *levels = g->last.levels;
+    if (td) *td = (int64_t)g->last.td_levels;
+    if (bu) *bu = (int64_t)g->last.bu_levels;
+    if (edges) *edges = (int64_t)g->last.edges;
+    if (words) *words = (int64_t)g->last.words;
+    return CC_OK;
+}
+
+int cc_last_call_timing(cc_graph_t g, int32_t *launches, double *kernel_ms,
+                        double *alg_bytes, int32_t *all_kernels)
+{
+    if (!g) return CC_ERR_ARG;
+    if (all_kernels) *all_kernels = g->call_kernels;
+    if (launches) *launches = g->call_launches;
+    if (kernel_ms) *kernel_ms = g->call_ms;
+    if (alg_bytes) *alg_bytes = g->call_bytes;
+    return CC_OK;
+}
+
+int cc_selftest_barrier_timeout(uint64_t timeout_ns)
+{
+    RC(device_ok());
+    int err = 0;
+    RC(launch_barrier_selftest(timeout_ns, &err));
+    return err;
+}
+
+int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *opts,
+                cc_out *out)
+{
+    if (!g || !opts || !out) return CC_ERR_ARG;
+    if (opts->eps_num == 0 || opts->eps_num > opts->eps_den) return CC_ERR_ARG;
+    if (g->directed || opts->roundtrip || g->weighted) return CC_ERR_ARG;  // later passes
+    RC(validate_sample(g, sample, k));
+    reset_timing(g);
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const int64_t n = g->n;
+    const int W = pow2_words(k);
+    RC(ensure_state(g, W));
+    RC(g->pivot.ensure(n * 4));
+    RC(g->delta.ensure(n * 4));
+    RC(g->dcc.ensure((size_t)k * k * 4));
+    RC(g->Ssamp.ensure((size_t)k * 8));
+    RC(g->sources.ensure((size_t)k * 4));
+    if (g->hist_cap == 0) g->hist_cap = (int)std::min<int64_t>(n + 1, 4096);
+    CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
+    run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
+    g->call_kernels += 2;
+
+    BfsJob j = base_job(g, W, g->fw);
+    j.k = k;
+    j.sources = g->sources.as<int32_t>();
+    j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
+    j.pivot = g->pivot.as<int32_t>();
+    j.delta = g->delta.as<uint32_t>();
+    j.dcc = g->dcc.as<uint32_t>();
+    j.dcc_k = k;
+    for (;;) {
+        RC(g->hist.ensure((size_t)g->hist_cap * k * 4));
+        j.hist = g->hist.as<uint32_t>();
+        j.hist_cap = g->hist_cap;
+        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+        CK(cudaMemsetAsync(g->hist.p, 0, (size_t)g->hist_cap * k * 4, st));
+        CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
+        RC(run_pass(g, W, j, st));
+        if (g->last.err == 1) {  // histogram too short: grow and rerun
+            if (g->hist_cap > n) return CC_ERR_TOO_LARGE;
+            g->hist_cap = (int)std::min<int64_t>(n + 1, (int64_t)g->hist_cap * 4);
+            continue;
+        }
+        break;
+    }
+    if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+    const int D = g->last.levels;
+    run_S_sampled(g->hist.as<uint32_t>(), D, k, g->dcc.as<uint32_t>(),
+                  g->Ssamp.as<uint64_t>(), st);
+    g->call_kernels += 1;
+
+    const bool hyb = opts->want_hybrid != 0;
+    if (hyb) {
+        RC(g->TN.ensure((size_t)k * (D + 1) * 8));
+        RC(g->TS.ensure((size_t)k * (D + 1) * 8));
+        RC(g->maxd.ensure((size_t)k * 4));
+        RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
+        RC(g->npartial.ensure(4));
+        CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
+        run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
+                 st);
+        run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
+        run_hyb_prep(n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+                     g->pivot.as<int32_t>(), g->delta.as<uint32_t>(),
+                     g->dcc.as<uint32_t>(), g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(),
+                     g->TS.as<uint64_t>(), g->hp.as<HybPrep>(),
+                     g->npartial.as<unsigned>(), st);
+        g->call_kernels += 3;
+        unsigned npart = 0;
+        CK(cudaMemcpyAsync(&npart, g->npartial.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        RC(g->lc2.ensure(n * 16));
+        if (npart > 0) {
+            RC(g->Lmask.ensure((size_t)n * W * 8));
+            run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(),
+                      g->dcc.as<uint32_t>(), g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(),
+                      st);
+            g->call_kernels += 1;
+            CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
+            BfsJob j2 = base_job(g, W, g->fw);
+            j2.k = k;
+            j2.sources = g->sources.as<int32_t>();
+            j2.red = RED_LC;
+            j2.Lmask = g->Lmask.as<uint64_t>();
+            j2.lc2 = g->lc2.as<uint64_t>();
+            RC(run_pass(g, W, j2, st));
+        }
+    }
+
+    // Finalise into device buffers (or straight into device outputs).
+    const bool dev_out = opts->device_outputs != 0;
+    FinalizeArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    fa.n = n;
+    fa.k = k;
+    fa.hybrid = hyb;
+    fa.sidx = g->sidx.as<int32_t>();
+    fa.pivot = g->pivot.as<int32_t>();
+    fa.delta = g->delta.as<uint32_t>();
+    fa.sum2 = g->sum2.as<uint64_t>();
+    fa.S_samp = g->Ssamp.as<uint64_t>();
+    fa.lc2 = g->lc2.as<uint64_t>();
+    fa.hp = g->hp.as<HybPrep>();
+    if (dev_out) {
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            fa.s_hat[e] = out->s_hat[e];
+            fa.clo[e] = out->closeness[e];
+        }
+        fa.hyb_int = out->hyb_int;
+        fa.sample_sum = out->sample_sum;
+    } else {
+        RC(g->shat.ensure((size_t)n * 8 * CC_NUM_EST));
+        RC(g->clo.ensure((size_t)n * 8 * CC_NUM_EST));
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            fa.s_hat[e] = out->s_hat[e] ? g->shat.as<double>() + (size_t)e * n : nullptr;
+            fa.clo[e] = out->closeness[e] ? g->clo.as<double>() + (size_t)e * n : nullptr;
+        }
+        if (out->hyb_int) {
+            RC(g->hyb.ensure((size_t)n * 48));
+            fa.hyb_int = g->hyb.as<uint64_t>();
+        }
+        if (out->sample_sum) {
+            RC(g->ssum.ensure((size_t)n * 8));
+            fa.sample_sum = g->ssum.as<uint64_t>();
+        }
+    }
+    run_finalize(fa, st);
+    g->call_kernels += 1;
+    const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!dev_out) {
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            if (e == CC_EST_HYBRID && !hyb) continue;
+            if (out->s_hat[e])
+                CK(cudaMemcpyAsync(out->s_hat[e], fa.s_hat[e], n * 8, kind, st));
+            if (out->closeness[e])
+                CK(cudaMemcpyAsync(out->closeness[e], fa.clo[e], n * 8, kind, st));
+        }
+        if (out->hyb_int && hyb)
+            CK(cudaMemcpyAsync(out->hyb_int, fa.hyb_int, n * 48, kind, st));
+        if (out->sample_sum)
+            CK(cudaMemcpyAsync(out->sample_sum, fa.sample_sum, n * 8, kind, st));
+    }
+    if (out->pivot) CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
+    if (out->delta) CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
+    if (out->S_sampled)
+        CK(cudaMemcpyAsync(out->S_sampled, g->Ssamp.p, (size_t)k * 8, kind, st));
+    if (out->delta_cc)
+        CK(cudaMemcpyAsync(out->delta_cc, g->dcc.p, (size_t)k * k * 4, kind, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return CC_OK;
+}
+
+int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
+{
+    if (!g) return CC_ERR_ARG;
+    if (g->directed || g->weighted) return CC_ERR_ARG;
+    const int64_t n = g->n;
+    const int kc = (int)std::min<int64_t>(n, CC_MAX_K);
+    const int W = pow2_words(kc);
+    cudaStream_t st = 0;
+    reset_timing(g);
+    RC(ensure_state(g, W));
+    RC(g->sources.ensure((size_t)kc * 4));
+    CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+    std::vector<int32_t> src(kc);
+    for (int64_t base = 0; base < n; base += kc) {
+        const int kk = (int)std::min<int64_t>(kc, n - base);
+        for (int i = 0; i < kk; ++i) src[i] = (int32_t)(base + i);
+        CK(cudaMemcpyAsync(g->sources.p, src.data(), (size_t)kk * 4, cudaMemcpyHostToDevice,
+                           st));
+        BfsJob j = base_job(g, W, g->fw);
+        j.k = kk;
+        j.sources = g->sources.as<int32_t>();
+        j.red = RED_SUM;
+        RC(run_pass(g, W, j, st));
+        if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+    }
+    std::vector<uint64_t> s2((size_t)n * 2);
+    CK(cudaMemcpy(s2.data(), g->sum2.p, n * 16, cudaMemcpyDeviceToHost));
+    for (int64_t v = 0; v < n; ++v) {
+        if (S) S[v] = s2[2 * v];
+        if (closeness) closeness[v] = (double)(n - 1) / (double)s2[2 * v];
+    }
+    return CC_OK;
+}
+
+int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k, uint64_t *sum,
+                            uint64_t *S_sampled)
+{
+    if (!g || !sum) return CC_ERR_ARG;
+    if (g->directed || g->weighted) return CC_ERR_ARG;
+    RC(validate_sample(g, sample, k));
+    const int64_t n = g->n;
+    cudaStream_t st = 0;
+    reset_timing(g);
+    RC(ensure_state(g, 1));
+    RC(g->sources.ensure((size_t)k * 4));
+    RC(g->hist.ensure((size_t)(n + 1) * 4));
+    RC(g->Ssamp.ensure((size_t)k * 8));
+    CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);  // every node counted in hist
+    CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+    std::vector<uint64_t> Sh(k, 0);
+    std::vector<uint32_t> hist;
+    for (int i = 0; i < k; ++i) {
+        BfsJob j = base_job(g, 1, g->fw);
+        j.k = 1;
+        j.sources = g->sources.as<int32_t>() + i;
+        j.red = RED_SUM | (S_sampled ? RED_HIST : 0u);
+        j.hist = g->hist.as<uint32_t>();
+        j.hist_cap = (int)(n + 1);
+        if (S_sampled) CK(cudaMemsetAsync(g->hist.p, 0, (size_t)(n + 1) * 4, st));
+        RC(run_pass(g, 1, j, st));
+        if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+        if (S_sampled) {
+            const int D = g->last.levels;
+            hist.resize(D + 1);
+            CK(cudaMemcpy(hist.data(), g->hist.p, (size_t)(D + 1) * 4, cudaMemcpyDeviceToHost));
+            uint64_t s = 0;
+            for (int l = 1; l <= D; ++l) s += (uint64_t)l * hist[l];
+            Sh[i] = s;
+        }
+    }
+    std::vector<uint64_t> s2((size_t)n * 2);
+    CK(cudaMemcpy(s2.data(), g->sum2.p, n * 16, cudaMemcpyDeviceToHost));
+    for (int64_t v = 0; v < n; ++v) sum[v] = s2[2 * v];
+    if (S_sampled) std::memcpy(S_sampled, Sh.data(), (size_t)k * 8);
+    return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cc.h"
+
+namespace ccg {
+
+constexpr int kBlock = 256;          // threads per CTA of the traversal kernel
+constexpr int kLightMaxDeg = 32;     // thread-per-(node, word) scan
+constexpr int kMediumMaxDeg = 256;   // warp-per-node scan
+constexpr int kChunk = 256;          // CSR entries per heavy-node warp task
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+// Reductions a traversal pass performs (bit set).
+enum : uint32_t {
+    RED_SUM = 1u,    // sum[v] += d, sumsq[v] += d^2
+    RED_PIVOT = 2u,  // first arrival: pivot[v], delta[v]
+    RED_DCC = 4u,    // delta_cc[i][j] for sampled nodes
+    RED_HIST = 8u,   // per-source level histogram over V \ C
+    RED_LC = 16u,    // hybrid pass: lc[v] += d, d^2 over sources in Lmask(v)
+};
+
+// Per-level statistics, indexed by level mod 4 (written during level l,
+// read during l+1 and l+2, cleared during l+3).
+struct LevelCtl {
+    unsigned int qlen;          // nodes with new bits this level (queue length)
+    unsigned int tlen;          // touched nodes (top-down)
+    unsigned int ninc_dec;      // nodes that became complete this level
+    unsigned int pad_;
+    unsigned long long ef;      // sum of degrees of the frontier nodes
+    unsigned long long eu_dec;  // sum of degrees of nodes completed
+};
+
+struct Ctl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;                // 0 or a CC_ERR_* code
+    int levels;             // last level that produced new bits
+    long long ninc_final;   // nodes never completed (non-zero: disconnected)
+    unsigned long long td_levels, bu_levels;
+    unsigned long long edges, words;  // CSR entries examined, words gathered
+    LevelCtl lev[4];
+};
+
+// One traversal pass over one graph.
+struct BfsJob {
+    int64_t n, arcs;
+    const int64_t *rp;
+    const int32_t *col;
+    int k;                  // sources in this pass
+    const int32_t *sources; // k node ids
+    const int32_t *sidx;    // n: sample index or -1 (pass-level sample)
+    const int32_t *Llist, *Mlist, *Hlist;
+    int64_t nL, nM, nH;
+    const int32_t *Hch_node;
+    const int64_t *Hch_begin;
+    int64_t nHch;
+    uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
+    int32_t *Q0, *Q1, *T;           // n each
+    unsigned int *tflag;            // n
+    uint32_t red;
+    uint64_t *sum2;      // n x 2: {sum, sumsq}
+    int32_t *pivot;      // n
+    uint32_t *delta;     // n
+    uint32_t *dcc;       // dcc_k x dcc_k (row = source index)
+    int dcc_k;
+    uint32_t *hist;      // hist_cap x k (level-major)
+    int hist_cap;
+    const uint64_t *Lmask;  // n*W
+    uint64_t *lc2;          // n x 2: {LCsum, LCsumSq}
+    Ctl *ctl;
+    uint64_t timeout_ns;
+    int alpha;              // top-down while ef * alpha < eu
+};
+
+// Launch one cooperative traversal pass (W = words per node, power of two
+// in [1, 32]).  Returns a CC_* status of the launch itself.
+int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used);
+
+int launch_barrier_selftest(uint64_t timeout_ns, int *err_out);
+
+// Host-built CSR (the "graph to CSR" step).
+struct HostCSR {
+    int64_t n = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> col;
+    std::vector<uint32_t> w;
+    std::vector<int32_t> old_id;
+    bool has_rev = false;
+    std::vector<int64_t> rrp;
+    std::vector<int32_t> rcol;
+    std::vector<uint32_t> rw;
+};
+
+int build_host_csr(int64_t n, int64_t m, const uint32_t *src,
+                   const uint32_t *dst, const uint32_t *w, bool directed,
+                   bool keep_component, HostCSR &out);
+
+}  // namespace ccg

@@ -1,0 +1,48 @@
+// Host launchers of the estimator kernels (estimate.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cc.h"
+
+namespace ccg {
+
+// LCnum carries this bit when L(v) misses some sampled node (second pass
+// needed for LCsum).
+constexpr uint64_t kPartialBit = 1ull << 63;
+
+struct HybPrep {
+    uint64_t Hsum, Hnum, thr, LCnum;
+};
+
+struct FinalizeArgs {
+    int64_t n;
+    int k;
+    int hybrid;
+    const int32_t *sidx, *pivot;
+    const uint32_t *delta;
+    const uint64_t *sum2, *S_samp, *lc2;
+    const HybPrep *hp;
+    double *s_hat[CC_NUM_EST];
+    double *clo[CC_NUM_EST];
+    uint64_t *hyb_int;
+    uint64_t *sample_sum;
+};
+
+void run_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
+void run_scatter_sidx(int32_t *sidx, const int32_t *src, int k, cudaStream_t st);
+void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint64_t *S,
+                   cudaStream_t st);
+void run_tail(const uint32_t *hist, int D, int k, uint64_t *TN, uint64_t *TS,
+              cudaStream_t st);
+void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st);
+void run_hyb_prep(int64_t n, int k, int D, uint32_t a, uint32_t b, const int32_t *sidx,
+                  const int32_t *pivot, const uint32_t *delta, const uint32_t *dcc,
+                  const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
+                  HybPrep *hp, unsigned *npartial, cudaStream_t st);
+void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
+               const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st);
+void run_finalize(const FinalizeArgs &a, cudaStream_t st);
+
+}  // namespace ccg

@@ -1,0 +1,589 @@
+// Bit-packed multi-source BFS with fused per-node reductions (sm_103a).
+//
+// One persistent cooperative kernel runs every level of one traversal pass.
+// k sources are packed 64 per uint64 word, W words per node (W a power of
+// two).  Per level l every node v gets new = (OR of its neighbours' frontier
+// words) & ~visited(v) -- the nodes at distance exactly l from the sources
+// whose bits are set -- and the pass reduces it on the fly (section 3: the
+// per-node running sums, the running minimum Delta(v) and pivot c(v)):
+//   RED_SUM    sum[v] += l * popc(new), sumsq[v] += l^2 * popc(new)
+//   RED_PIVOT  on the first level with new bits: Delta(v) = l and c(v) =
+//              the lowest set bit (smallest sample index among the nearest)
+//   RED_DCC    v sampled with index j: dcc[i][j] = l for each new bit i
+//   RED_HIST   v not sampled: hist[l][i] += 1 for each new bit i
+//   RED_LC     v not sampled: lc[v] += l, l^2 times popc(new & Lmask(v))
+// so the k x n distance matrix never exists.
+//
+// Direction per level (same decision in every CTA, from the previous level's
+// counters): top-down pushes the frontier words of the queued frontier nodes
+// into their neighbours with atomicOr; bottom-up pulls, per node and word,
+// the OR of the neighbours' frontier words with early exit once every
+// missing bit has arrived.  Bottom-up splits nodes by degree: <= 32 a thread
+// per (node, word), <= 256 a warp per node, larger nodes in 256-entry warp
+// tasks that OR into a scratch word finalised after the barrier.
+//
+// Every wait is bounded: the grid barrier gives up after timeout_ns, records
+// CC_ERR_TIMEOUT and every CTA returns.
+#include <cstdint>
+
+#include "cc_internal.h"
+
+namespace ccg {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bits of word w that do not correspond to a source (index >= k): preset in
+// visited so that "all bits set" means "reached by every source".
+__device__ __forceinline__ uint64_t pad_mask(int k, int w)
+{
+    const int lo = w * 64;
+    if (k <= lo) return ~0ull;
+    if (k >= lo + 64) return 0ull;
+    return ~0ull << (k - lo);
+}
+
+// Grid-wide barrier over `nblocks` CTAs with a bounded wait.  Returns false
+// (in every thread of the CTA) when the wait ran out or another CTA reported
+// an error.  Same arrival/generation scheme as a cooperative-groups grid
+// sync, with a time limit.
+__device__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = &ctl->bar_gen;
+        volatile int *verr = &ctl->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const uint64_t t0 = gtimer();
+            unsigned ns = 8;
+            while (*vgen == g) {
+                if (*verr != 0) { ok = 0; break; }
+                if (gtimer() - t0 > timeout_ns) {
+                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        __threadfence();
+        if (*verr != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// 32 x 32 bit-matrix transpose across a warp: on return lane c holds, in
+// bit r, bit c of the value lane r passed in.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000FFFFu
+                         : j == 8  ? 0x00FF00FFu
+                         : j == 4  ? 0x0F0F0F0Fu
+                         : j == 2  ? 0x33333333u
+                                   : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(FULL, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j))
+                       : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+template <int W>
+struct LaneAcc {
+    // Per-lane histogram counts (W <= 8): hc[2s+h] counts source
+    // s*64 + h*32 + lane.
+    uint32_t hc[W <= 8 ? 2 * W : 1];
+    unsigned long long ef, eu_dec, words, edges;
+    unsigned int ninc_dec;
+};
+
+// Update, reduce and enqueue one warp tile.  Lanes form groups of W; group
+// g = lane / W is one node (valid or not), lane % W its word.  Must be
+// called by all 32 lanes together.
+template <int W>
+__device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
+                                            int v, uint64_t vis, uint64_t nw,
+                                            int64_t deg, uint64_t *Fout,
+                                            int32_t *Qout, LevelCtl *C,
+                                            LaneAcc<W> &A, unsigned *s_hist,
+                                            bool clear_tflag)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = lane & (W - 1);
+    const int64_t vw = (int64_t)v * W + w;
+    if (valid) {
+        Fout[vw] = nw;
+        if (nw) J.vis[vw] = vis | nw;
+    }
+    int sx = -1;
+    if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC))) sx = J.sidx[v];
+    int c = __popcll(nw);
+    int cL = 0;
+    if ((J.red & RED_LC) && valid && sx < 0 && nw) cL = __popcll(nw & J.Lmask[vw]);
+    int had = (vis & ~pad_mask(J.k, w)) != 0;
+    int done_before = vis == ~0ull;
+    int done_after = (vis | nw) == ~0ull;
+    int pv = nw ? (w * 64 + __ffsll((long long)nw) - 1) : 0x7FFFFFFF;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        c += __shfl_xor_sync(FULL, c, o);
+        cL += __shfl_xor_sync(FULL, cL, o);
+        had |= __shfl_xor_sync(FULL, had, o);
+        done_before &= __shfl_xor_sync(FULL, done_before, o);
+        done_after &= __shfl_xor_sync(FULL, done_after, o);
+        pv = min(pv, __shfl_xor_sync(FULL, pv, o));
+    }
+    const bool leader = valid && w == 0;
+    if (leader && c > 0) {
+        const uint64_t ul = (uint64_t)l;
+        if (J.red & RED_SUM) {
+            J.sum2[2 * (int64_t)v] += ul * (uint64_t)c;
+            J.sum2[2 * (int64_t)v + 1] += ul * ul * (uint64_t)c;
+        }
+        if (cL > 0) {
+            J.lc2[2 * (int64_t)v] += ul * (uint64_t)cL;
+            J.lc2[2 * (int64_t)v + 1] += ul * ul * (uint64_t)cL;
+        }
+        if ((J.red & RED_PIVOT) && !had) {
+            J.pivot[v] = pv;
+            J.delta[v] = (uint32_t)l;
+        }
+    }
+    if (leader && clear_tflag) J.tflag[v] = 0u;
+    if ((J.red & RED_DCC) && sx >= 0 && nw) {
+        uint64_t b = nw;
+        while (b) {
+            const int i = w * 64 + __ffsll((long long)b) - 1;
+            b &= b - 1;
+            J.dcc[(int64_t)i * J.dcc_k + sx] = (uint32_t)l;
+        }
+    }
+    if (J.red & RED_HIST) {
+        const uint64_t x = (valid && sx < 0) ? nw : 0ull;
+        if constexpr (W <= 8) {
+            if (__ballot_sync(FULL, x != 0ull)) {
+                const uint32_t lo = warp_transpose32((uint32_t)x, lane);
+                const uint32_t hi = warp_transpose32((uint32_t)(x >> 32), lane);
+                constexpr uint32_t M0 = W == 1 ? 0xFFFFFFFFu
+                                      : W == 2 ? 0x55555555u
+                                      : W == 4 ? 0x11111111u
+                                               : 0x01010101u;
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    A.hc[2 * s] += __popc(lo & (M0 << s));
+                    A.hc[2 * s + 1] += __popc(hi & (M0 << s));
+                }
+            }
+        } else {
+            uint64_t b = x;
+            while (b) {
+                const int i = w * 64 + __ffsll((long long)b) - 1;
+                b &= b - 1;
+                atomicAdd(&s_hist[i], 1u);
+            }
+        }
+    }
+    // Enqueue frontier nodes (warp-aggregated) and count level statistics.
+    const bool fr = leader && c > 0;
+    const unsigned bal = __ballot_sync(FULL, fr);
+    if (bal) {
+        const int first = __ffs(bal) - 1;
+        unsigned base = 0;
+        if (lane == first) base = atomicAdd(&C->qlen, (unsigned)__popc(bal));
+        base = __shfl_sync(FULL, base, first);
+        if (fr) Qout[base + __popc(bal & ((1u << lane) - 1u))] = v;
+    }
+    if (fr) A.ef += (unsigned long long)deg;
+    if (leader && done_after && !done_before) {
+        A.eu_dec += (unsigned long long)deg;
+        A.ninc_dec += 1;
+    }
+}
+
+// OR of `x` over the lanes holding the same word slot (lane % W).
+template <int W>
+__device__ __forceinline__ uint64_t or_same_word(uint64_t x)
+{
+#pragma unroll
+    for (int o = W; o < 32; o <<= 1) x |= __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long block_sum64(unsigned long long x,
+                                                          unsigned long long *s)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s[wid] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
+    return t;  // valid in thread 0
+}
+
+// Flush per-lane counters of one level phase to the level control block and
+// (when asked) the CTA histogram to the global histogram of level l.
+template <int W>
+__device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
+                            unsigned *s_hist, bool flush_hist)
+{
+    __shared__ unsigned long long s_red[kBlock / 32];
+    const unsigned long long ef = block_sum64(A.ef, s_red);
+    const unsigned long long eu = block_sum64(A.eu_dec, s_red);
+    const unsigned long long ni = block_sum64(A.ninc_dec, s_red);
+    if (threadIdx.x == 0) {
+        if (ef) atomicAdd(&C->ef, ef);
+        if (eu) atomicAdd(&C->eu_dec, eu);
+        if (ni) atomicAdd(&C->ninc_dec, (unsigned)ni);
+    }
+    A.ef = A.eu_dec = 0;
+    A.ninc_dec = 0;
+    if (!flush_hist) return;
+    const int lane = threadIdx.x & 31;
+    if constexpr (W <= 8) {
+#pragma unroll
+        for (int s = 0; s < W; ++s)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = s * 64 + h * 32 + lane;
+                if (A.hc[2 * s + h]) atomicAdd(&s_hist[i], A.hc[2 * s + h]);
+                A.hc[2 * s + h] = 0;
+            }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < J.k; i += blockDim.x) {
+        const unsigned c = s_hist[i];
+        if (c) {
+            atomicAdd(&J.hist[(int64_t)l * J.k + i], c);
+            s_hist[i] = 0;
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
+{
+    extern __shared__ unsigned s_hist[];  // W * 64 counters
+    constexpr int NPW = 32 / W;           // nodes (or entries) per warp step
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t gthreads = (int64_t)gridDim.x * kBlock;
+    const int64_t gtid = (int64_t)blockIdx.x * kBlock + tid;
+    const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+    const int w = lane & (W - 1);
+    const int grp = lane / W;
+    const int64_t n = J.n;
+    const int64_t *rp = J.rp;
+    const int32_t *col = J.col;
+    Ctl *ctl = J.ctl;
+    const unsigned nb = gridDim.x;
+    const bool doHist = (J.red & RED_HIST) != 0;
+
+    LaneAcc<W> A;
+#pragma unroll
+    for (int i = 0; i < (W <= 8 ? 2 * W : 1); ++i) A.hc[i] = 0;
+    A.ef = A.eu_dec = A.words = A.edges = 0;
+    A.ninc_dec = 0;
+
+    // ---- level 0: clear the state, seed the sources -----------------------
+    for (int64_t i = gtid; i < n * W; i += gthreads) {
+        J.vis[i] = pad_mask(J.k, (int)(i & (W - 1)));
+        J.F0[i] = 0;
+        J.F1[i] = 0;
+        J.nxt[i] = 0;
+    }
+    for (int64_t v = gtid; v < n; v += gthreads) J.tflag[v] = 0;
+    for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
+    if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+    for (int64_t i = gtid; i < J.k; i += gthreads) {
+        const int v = J.sources[i];
+        const uint64_t bit = 1ull << (i & 63);
+        const int64_t vw = (int64_t)v * W + (i >> 6);
+        atomicOr((unsigned long long *)&J.vis[vw], bit);
+        atomicOr((unsigned long long *)&J.F0[vw], bit);
+        J.Q0[i] = v;
+        if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
+        if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
+        const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
+        atomicAdd(&ctl->lev[0].ef, d);
+        if (J.k == 1) {
+            atomicAdd(&ctl->lev[0].eu_dec, d);
+            atomicAdd(&ctl->lev[0].ninc_dec, 1u);
+        }
+    }
+    if (gtid == 0) ctl->lev[0].qlen = (unsigned)J.k;
+    if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+
+    long long eu = J.arcs, ninc = n;
+    int last = 0;
+    int l = 1;
+    for (;; ++l) {
+        volatile LevelCtl *P = &ctl->lev[(l - 1) & 3];
+        const unsigned qprev = P->qlen;
+        const unsigned long long ef = P->ef;
+        eu -= (long long)P->eu_dec;
+        ninc -= (long long)P->ninc_dec;
+        if (qprev > 0) last = l - 1;
+        if (qprev == 0 || ninc == 0) break;
+        if (doHist && l >= J.hist_cap) {
+            if (gtid == 0) atomicCAS(&ctl->err, 0, 1);  // histogram too short
+            break;
+        }
+        const bool td = ef * (unsigned long long)J.alpha < (unsigned long long)eu;
+        if (gtid == 0) {
+            LevelCtl *Z = &ctl->lev[(l + 1) & 3];
+            Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
+        }
+        uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
+        uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
+        const int32_t *Qin = (l & 1) ? J.Q0 : J.Q1;
+        int32_t *Qout = (l & 1) ? J.Q1 : J.Q0;
+        LevelCtl *C = &ctl->lev[l & 3];
+
+        if (td) {
+            // P1a: clear the stale frontier of level l-2 held in Fout.
+            if (l >= 2) {
+                const unsigned q2 = ((volatile LevelCtl *)&ctl->lev[(l - 2) & 3])->qlen;
+                for (int64_t i = gtid; i < (int64_t)q2 * W; i += gthreads)
+                    Fout[(int64_t)Qout[i / W] * W + (i & (W - 1))] = 0;
+            }
+            // P1b: push the frontier words of the queued nodes.
+            for (int64_t t = gwarp; t < (int64_t)qprev; t += nwarps) {
+                const int u = Qin[t];
+                const uint64_t f = Fin[(int64_t)u * W + w];
+                const int64_t b = rp[u], e = rp[u + 1];
+                for (int64_t base = b; base < e; base += NPW) {
+                    const int64_t ee = base + grp;
+                    if (ee < e && f) {
+                        const int v = col[ee];
+                        const int64_t vw = (int64_t)v * W + w;
+                        A.edges += 1;
+                        A.words += 1;
+                        const uint64_t nbits = f & ~J.vis[vw];
+                        if (nbits) {
+                            const uint64_t old = atomicOr((unsigned long long *)&J.nxt[vw], nbits);
+                            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u) {
+                                const unsigned m = __activemask();
+                                const int first = __ffs(m) - 1;
+                                unsigned pos = 0;
+                                if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
+                                pos = __shfl_sync(m, pos, first);
+                                J.T[pos + __popc(m & ((1u << lane) - 1u))] = v;
+                            }
+                        }
+                    }
+                }
+            }
+            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+            // P2: finalise the touched nodes.
+            const int64_t tl = ((volatile LevelCtl *)C)->tlen;
+            for (int64_t t = gwarp; t * NPW < tl; t += nwarps) {
+                const int64_t li = t * NPW + grp;
+                const bool valid = li < tl;
+                const int v = valid ? J.T[li] : 0;
+                const int64_t vw = (int64_t)v * W + w;
+                uint64_t vis = ~0ull, acc = 0;
+                int64_t deg = 0;
+                if (valid) {
+                    vis = J.vis[vw];
+                    acc = J.nxt[vw];
+                    if (acc) J.nxt[vw] = 0;
+                    deg = rp[v + 1] - rp[v];
+                }
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
+                               A, s_hist, true);
+            }
+            flush_level<W>(J, l, C, A, s_hist, doHist);
+            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+            if (gtid == 0) ctl->td_levels += 1;
+        } else {
+            // A1: light nodes, one thread per (node, word).
+            for (int64_t t = gwarp; t * NPW < J.nL; t += nwarps) {
+                const int64_t li = t * NPW + grp;
+                const bool valid = li < J.nL;
+                const int v = valid ? J.Llist[li] : 0;
+                const int64_t vw = (int64_t)v * W + w;
+                uint64_t vis = valid ? J.vis[vw] : ~0ull;
+                int64_t b = 0, e = 0;
+                if (valid) { b = rp[v]; e = rp[v + 1]; }
+                uint64_t acc = 0;
+                if (vis != ~0ull) {
+                    for (int64_t ee = b; ee < e; ++ee) {
+                        acc |= Fin[(int64_t)col[ee] * W + w];
+                        A.words += 1;
+                        if ((acc | vis) == ~0ull) break;
+                    }
+                }
+                __syncwarp();
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, Qout, C,
+                               A, s_hist, false);
+            }
+            // A2: medium nodes, one warp per node.
+            for (int64_t t = gwarp; t < J.nM; t += nwarps) {
+                const int v = J.Mlist[t];
+                const uint64_t visw = J.vis[(int64_t)v * W + w];
+                const int64_t b = rp[v], e = rp[v + 1];
+                uint64_t acc = 0;
+                if (!__all_sync(FULL, visw == ~0ull)) {
+                    for (int64_t base = b; base < e; base += NPW) {
+                        const int64_t ee = base + grp;
+                        if (ee < e) {
+                            acc |= Fin[(int64_t)col[ee] * W + w];
+                            A.words += 1;
+                        }
+                        const uint64_t r = or_same_word<W>(acc);
+                        if (__all_sync(FULL, (r | visw) == ~0ull)) break;
+                    }
+                }
+                const uint64_t r = or_same_word<W>(acc);
+                tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, Qout,
+                               C, A, s_hist, false);
+            }
+            // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
+            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
+                const int v = J.Hch_node[t];
+                const int64_t vw = (int64_t)v * W + w;
+                const int64_t b = J.Hch_begin[t];
+                const int64_t e = min(b + (int64_t)kChunk, rp[v + 1]);
+                const uint64_t visw = J.vis[vw];
+                const uint64_t cur = J.nxt[vw];
+                if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
+                uint64_t acc = 0;
+                for (int64_t base = b; base < e; base += NPW) {
+                    const int64_t ee = base + grp;
+                    if (ee < e) {
+                        acc |= Fin[(int64_t)col[ee] * W + w];
+                        A.words += 1;
+                    }
+                    const uint64_t r = or_same_word<W>(acc);
+                    if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
+                }
+                const uint64_t r = or_same_word<W>(acc);
+                const uint64_t nbits = r & ~visw & ~cur;
+                if (lane < W && nbits)
+                    atomicOr((unsigned long long *)&J.nxt[vw], nbits);
+            }
+            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+            // B: finalise the heavy nodes.
+            for (int64_t t = gwarp; t * NPW < J.nH; t += nwarps) {
+                const int64_t li = t * NPW + grp;
+                const bool valid = li < J.nH;
+                const int v = valid ? J.Hlist[li] : 0;
+                const int64_t vw = (int64_t)v * W + w;
+                uint64_t vis = ~0ull, acc = 0;
+                int64_t deg = 0;
+                if (valid) {
+                    vis = J.vis[vw];
+                    acc = J.nxt[vw];
+                    if (acc) J.nxt[vw] = 0;
+                    deg = rp[v + 1] - rp[v];
+                }
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
+                               A, s_hist, false);
+            }
+            flush_level<W>(J, l, C, A, s_hist, doHist);
+            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+            if (gtid == 0) ctl->bu_levels += 1;
+        }
+    }
+    // Pass statistics.
+    __shared__ unsigned long long s_red[kBlock / 32];
+    const unsigned long long words = block_sum64(A.words, s_red);
+    const unsigned long long edges = block_sum64(A.edges, s_red);
+    if (tid == 0) {
+        atomicAdd(&ctl->words, words);
+        atomicAdd(&ctl->edges, edges);
+    }
+    if (gtid == 0) {
+        ctl->levels = last;
+        ctl->ninc_final = ninc;
+    }
+}
+
+__global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t timeout_ns)
+{
+    // A team of two CTAs of which only one is launched: the barrier cannot
+    // complete and must give up after timeout_ns.
+    grid_sync(ctl, 2u, timeout_ns);
+}
+
+template <int W>
+int launch_w(const BfsJob &job, cudaStream_t st, int *grid_used)
+{
+    static int blocks_per_sm = -1, sms = 0;
+    const size_t smem = (size_t)W * 64 * sizeof(unsigned);
+    if (blocks_per_sm < 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return CC_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return CC_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm,
+                                                          msbfs_kernel<W>, kBlock,
+                                                          smem) != cudaSuccess)
+            return CC_ERR_CUDA;
+        if (blocks_per_sm < 1) return CC_ERR_CUDA;
+    }
+    const int grid = blocks_per_sm * sms;
+    if (grid_used) *grid_used = grid;
+    BfsJob j = job;
+    void *args[] = {&j};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)msbfs_kernel<W>,
+                                                      dim3(grid), dim3(kBlock), args,
+                                                      smem, st);
+    return e == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used)
+{
+    switch (W) {
+    case 1: return launch_w<1>(job, st, grid_used);
+    case 2: return launch_w<2>(job, st, grid_used);
+    case 4: return launch_w<4>(job, st, grid_used);
+    case 8: return launch_w<8>(job, st, grid_used);
+    case 16: return launch_w<16>(job, st, grid_used);
+    case 32: return launch_w<32>(job, st, grid_used);
+    default: return CC_ERR_ARG;
+    }
+}
+
+int launch_barrier_selftest(uint64_t timeout_ns, int *err_out)
+{
+    Ctl *d = nullptr;
+    if (cudaMalloc(&d, sizeof(Ctl)) != cudaSuccess) return CC_ERR_OOM;
+    cudaMemset(d, 0, sizeof(Ctl));
+    barrier_selftest_kernel<<<1, 32>>>(d, timeout_ns);
+    Ctl h;
+    cudaError_t e = cudaMemcpy(&h, d, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return CC_ERR_CUDA;
+    *err_out = h.err;
+    return CC_OK;
+}
+
+}  // namespace ccg

@@ -1,0 +1,212 @@
+"""GPU parity: every output of the sm_103a library against the CPU oracle
+on the same seeded inputs.  Integers bit-exact; FP64 within 1e-12 relative
+(the arithmetic is the same integer numerator, one conversion and one IEEE
+division on both sides)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def cc():
+    from paper_1409_0035_gb300 import build
+    build.build()
+    import paper_1409_0035_gb300 as m
+    return m
+
+
+def both(cc, n, s, d, w=None, directed=False, keep=True):
+    g, old = cc.cc_graph_from_edges(n, s, d, w, directed=directed, keep_component=keep)
+    og = orc.csr_from_edges(n, s, d, w=w, directed=directed, keep_component=keep)
+    return g, old, og
+
+
+def assert_close(a, b, what):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+    assert rel.max(initial=0.0) <= RTOL, f"{what}: max rel {rel.max()}"
+
+
+def check_estimate(cc, g, og, C, eps, hybrid=True):
+    o = cc.cc_opts_default(len(C))
+    o.eps_num, o.eps_den, o.want_hybrid = eps[0], eps[1], int(hybrid)
+    r = cc.cc_estimate(g, C, o)
+    want = orc.estimate(og, C, eps=eps)
+    assert (r["pivot"] == want["pivot"]).all()
+    assert (r["delta"] == want["delta"]).all()
+    assert (r["sum"] == want["sum"]).all()
+    assert (r["S_samp"] == want["S_samp"]).all()
+    assert (r["delta_cc"] == want["delta_cc"]).all()
+    nest = 4 if hybrid else 3
+    for e in range(nest):
+        assert_close(r["s_hat"][e], want["s_hat"][e], f"s_hat[{e}]")
+        assert_close(r["closeness"][e], want["closeness"][e], f"closeness[{e}]")
+    if hybrid:
+        assert (r["hyb"] == want["hyb"]).all()
+    return r, want
+
+
+GRAPHS = {
+    "rmat9": lambda: synth.rmat_edges(9, 8, seed=3),
+    "grid": lambda: synth.grid_edges(23, 17),
+    "ws": lambda: synth.watts_strogatz_edges(700, 10, 0.05, seed=4),
+    "path": lambda: synth.path_edges(300),
+    "star": lambda: synth.star_edges(1500),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_graph_build_matches_oracle(cc, name):
+    n, s, d = GRAPHS[name]()
+    g, old, og = both(cc, n, s, d)
+    try:
+        rp, col, _ = cc.cc_graph_copy_csr(g)
+        assert (rp == og.row_ptr).all() and (col == og.col).all()
+        assert (old == og.old_id).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_graph_build_weighted_directed(cc):
+    n, s, d = synth.rmat_edges(9, 6, seed=8)
+    w = synth.random_weights(s.size, 1, 30, seed=9)
+    for directed in (False, True):
+        g, old, og = both(cc, n, s, d, w, directed=directed)
+        try:
+            rp, col, ww = cc.cc_graph_copy_csr(g)
+            assert (rp == og.row_ptr).all() and (col == og.col).all()
+            assert (ww == og.w).all() and (old == og.old_id).all()
+            if directed:
+                rp, col, ww = cc.cc_graph_copy_csr(g, reverse=True)
+                assert (rp == og.rrow_ptr).all() and (col == og.rcol).all()
+                assert (ww == og.rw).all()
+        finally:
+            cc.cc_graph_free(g)
+
+
+@pytest.mark.parametrize("n,k,seed", [(10, 3, 0), (1000, 64, 2), (5000, 1, 7),
+                                      (3000, 2048, 5), (70000, 256, 11), (300, 300, 1)])
+def test_sample_choose_matches_oracle(cc, n, k, seed):
+    g, _ = cc.cc_graph_from_edges(*synth.path_edges(n))
+    try:
+        assert (cc.cc_sample_choose(g, k, seed) == orc.choose_sample(n, k, seed)).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("k", [1, 5, 64, 100, 256, 300])
+def test_estimate_parity(cc, name, k):
+    n, s, d = GRAPHS[name]()
+    g, old, og = both(cc, n, s, d)
+    try:
+        k = min(k, og.n)
+        C = orc.choose_sample(og.n, k, 17 + k)
+        for eps in [(1, 1), (1, 3), orc.default_eps(k)]:
+            check_estimate(cc, g, og, C, eps)
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_word_boundaries_and_large_k(cc):
+    n, s, d = synth.rmat_edges(10, 8, seed=12)
+    g, old, og = both(cc, n, s, d)
+    try:
+        for k in (63, 64, 65, 127, 128, 129, 511, 512, 513, 1024, 2048):
+            C = orc.choose_sample(og.n, min(k, og.n), k)
+            check_estimate(cc, g, og, C, (1, 2))
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_full_sample_is_exact(cc):
+    n, s, d = synth.grid_edges(12, 9)
+    g, old, og = both(cc, n, s, d)
+    try:
+        C = orc.choose_sample(og.n, og.n, 3)
+        r, _ = check_estimate(cc, g, og, C, (1, 2))
+        S = orc.exact_S(og).astype(np.float64)
+        for e in range(4):
+            assert (r["s_hat"][e] == S).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_exact_all_pairs_config1(cc):
+    """R-MAT scale 12, edge factor 8, seed 1, LCC: exact closeness of every
+    node against the oracle's n BFS."""
+    n, s, d = synth.rmat_edges(12, 8, seed=1)
+    g, old, og = both(cc, n, s, d)
+    try:
+        c, S = cc.cc_exact(g)
+        want = orc.exact_S(og)
+        assert (S == want).all()
+        assert_close(c, orc.exact_closeness(want), "exact closeness")
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_estimate_config1(cc):
+    """R-MAT scale 12 / edge factor 8 / seed 1, k = 64 (sample seed 2),
+    eps = 1/8: every output."""
+    n, s, d = synth.rmat_edges(12, 8, seed=1)
+    g, old, og = both(cc, n, s, d)
+    try:
+        C = cc.cc_sample_choose(g, 64, 2)
+        assert (C == orc.choose_sample(og.n, 64, 2)).all()
+        check_estimate(cc, g, og, C, (1, 8))
+        s_single, S_single = cc.cc_sampling_sums_single(g, C)
+        want = orc.streaming_pass(og, C)
+        assert (s_single == want["sum"]).all() and (S_single == want["S_samp"]).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_errors(cc):
+    n, s, d = synth.path_edges(50)
+    g, _ = cc.cc_graph_from_edges(n, s, d)
+    try:
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_estimate(g, [1, 1, 2])
+        assert e.value.code == cc.CC_ERR_ARG
+        with pytest.raises(cc.CCError):
+            cc.cc_estimate(g, [0, 60])
+        o = cc.cc_opts_default(2)
+        o.eps_num, o.eps_den = 3, 2  # eps > 1
+        with pytest.raises(cc.CCError):
+            cc.cc_estimate(g, [0, 1], o)
+    finally:
+        cc.cc_graph_free(g)
+    # two components kept: closeness undefined
+    src = np.array([0, 1, 3, 4], np.uint32)
+    dst = np.array([1, 2, 4, 5], np.uint32)
+    g, _ = cc.cc_graph_from_edges(6, src, dst, keep_component=False)
+    try:
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_estimate(g, [0, 4])
+        assert e.value.code == cc.CC_ERR_DISCONNECTED
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_bounded_barrier_wait_reports_timeout(cc):
+    assert cc.cc_selftest_barrier_timeout(50_000_000) == cc.CC_ERR_TIMEOUT
+
+
+def test_repeatable(cc):
+    n, s, d = synth.rmat_edges(11, 16, seed=21)
+    g, _ = cc.cc_graph_from_edges(n, s, d)
+    try:
+        C = cc.cc_sample_choose(g, 200, 4)
+        a = cc.cc_estimate(g, C)
+        for _ in range(3):
+            b = cc.cc_estimate(g, C)
+            for key in a:
+                assert (a[key] == b[key]).all(), key
+    finally:
+        cc.cc_graph_free(g)
