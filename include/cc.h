@@ -191,6 +191,39 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S);
 int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k,
                             uint64_t *sum, uint64_t *S_sampled);
 
+/*
+ * cc_sampling_pivots_noalloc -- the first traversal pass of cc_estimate
+ * (per-node sum of distances to the sample, pivot, Delta, and the exact S of
+ * every sampled node) for callers that cannot allocate device memory, e.g.
+ * code running inside a framework whose memory pool owns the device, or under
+ * a memory budget where an allocation could fail or synchronise the device at
+ * the wrong moment.  The paper has no counterpart: it is a deployment variant
+ * of the same computation.
+ *   n            nodes; d_row_ptr int64[n+1] and d_col int32[row_ptr[n]] are
+ *                a connected undirected graph in device memory (each edge
+ *                listed both ways, e.g. as returned by cc_graph_copy_csr);
+ *                checked on the device (CC_ERR_GRAPH when malformed)
+ *   sample, k    host int32[k], distinct node ids (CC_ERR_ARG otherwise)
+ *   outputs      device memory owned by the caller: d_sample_sum uint64[n],
+ *                d_pivot int32[n], d_delta uint32[n], d_S_sampled uint64[k]
+ *   stream       cudaStream_t or NULL
+ * Allocates nothing: all working memory lives in one fixed 32 MiB device
+ * array inside the library, present on every GPU that loads the library until
+ * the process exits.  Calls that need more -- about 4*n*W*8 + 40*n + 4*k*k +
+ * 8192*k bytes with W = ceil(k/64) rounded up to a power of two, or more than
+ * 2047 BFS levels -- return CC_ERR_TOO_LARGE before touching the device.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  Every call reuses the array and clears what it needs; calls that
+ * overlap on the GPU race on it and must not be issued.  Synchronous on
+ * `stream`.
+ */
+int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
+                               const int32_t *d_col, const int32_t *sample,
+                               int32_t k, uint64_t *d_sample_sum,
+                               int32_t *d_pivot, uint32_t *d_delta,
+                               uint64_t *d_S_sampled, void *stream);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Counters of the last traversal pass run on g: levels, top-down and
  * bottom-up levels, CSR entries examined and frontier words gathered.

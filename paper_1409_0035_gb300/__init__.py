@@ -33,7 +33,7 @@ EXPORTS = (
     "cc_graph_from_edges", "cc_graph_load_csr", "cc_graph_free", "cc_graph_info",
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
-    "cc_last_call_timing",
+    "cc_last_call_timing", "cc_sampling_pivots_noalloc",
     "cc_selftest_barrier_timeout", "cc_strerror",
 )
 
@@ -84,6 +84,7 @@ def lib():
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
+        L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
         L.cc_strerror.restype = ctypes.c_char_p
@@ -239,6 +240,16 @@ def cc_last_call_timing(g):
     _chk(lib().cc_last_call_timing(g, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
                                    ctypes.byref(a)), "cc_last_call_timing")
     return n.value, ms.value, b.value, a.value
+
+
+def cc_sampling_pivots_noalloc(n, d_row_ptr, d_col, sample, d_sample_sum, d_pivot,
+                               d_delta, d_S_sampled, stream=None):
+    """Device pointers (ints) in, device pointers out; returns the status
+    code (see include/cc.h: this call allocates nothing)."""
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    return lib().cc_sampling_pivots_noalloc(int(n), d_row_ptr, d_col, _p(sample),
+                                            sample.size, d_sample_sum, d_pivot, d_delta,
+                                            d_S_sampled, stream)
 
 
 def cc_selftest_barrier_timeout(timeout_ns):
