@@ -225,8 +225,8 @@ def run_ours(args):
 
     for _ in range(max(3, args.warmup)):
         step()
-    _ = cc.cc_last_call_timing(g)
     stats = cc.cc_last_pass_stats(g)
+    trace = cc.cc_last_pass_trace(g)
 
     if ws > 1:
         torch.distributed.barrier()
@@ -328,6 +328,8 @@ def run_ours(args):
                                          "sources": nsingle,
                                          "speedup": value / single_gteps},
             "pass_stats": stats,
+            "level_trace": [{"level": l, "us": ns / 1e3, "top_down": td, "frontier": fr}
+                            for (l, ns, td, fr) in trace],
             "estimates_per_s": n / (ms_step / 1e3)}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -33,7 +33,7 @@ EXPORTS = (
     "cc_graph_from_edges", "cc_graph_load_csr", "cc_graph_free", "cc_graph_info",
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
-    "cc_last_call_timing", "cc_sampling_pivots_noalloc",
+    "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
     "cc_selftest_barrier_timeout", "cc_strerror",
 )
 
@@ -84,6 +84,7 @@ def lib():
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
+        L.cc_last_pass_trace.argtypes = [P, i32, P, P, P]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
@@ -230,6 +231,17 @@ def cc_last_pass_stats(g):
          "cc_last_pass_stats")
     return dict(zip(("levels", "td_levels", "bu_levels", "edges", "words"),
                     [v.value for v in vals]))
+
+
+def cc_last_pass_trace(g, max_levels=64):
+    """List of (level, ns, top_down, frontier) of the last traversal pass."""
+    t = np.zeros(max_levels, np.int64)
+    d = np.zeros(max_levels, np.int32)
+    f = np.zeros(max_levels, np.int64)
+    L = lib().cc_last_pass_trace(g, max_levels, _p(t), _p(d), _p(f))
+    if L < 0:
+        raise CCError(L, "cc_last_pass_trace")
+    return [(l, int(t[l]), int(d[l]), int(f[l])) for l in range(1, L)]
 
 
 def cc_last_call_timing(g):

@@ -222,6 +222,7 @@ int run_pass(cc_graph *g, int W, const BfsJob &j, cudaStream_t st)
     CK(cudaStreamSynchronize(st));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    g->last.edges = g->last.words / (unsigned long long)W;
     g->call_launches += 1;
     g->call_kernels += 1;
     g->call_ms += ms;
@@ -389,6 +390,25 @@ int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td, int64_t *bu,
     if (edges) *edges = (int64_t)g->last.edges;
     if (words) *words = (int64_t)g->last.words;
     return CC_OK;
+}
+
+int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
+                       int32_t *top_down, int64_t *frontier)
+{
+    if (!g || max_levels < 0) return CC_ERR_ARG;
+    const int L = std::min<int>(g->last.levels + 1, std::min<int>(max_levels, kTraceLevels));
+    for (int l = 1; l < L; ++l) {
+        const unsigned long long t1 = (l + 1 < kTraceLevels + 1) ? g->last.lvl_ns[l + 1] : 0;
+        if (level_ns) level_ns[l] = t1 > g->last.lvl_ns[l] ? (int64_t)(t1 - g->last.lvl_ns[l]) : 0;
+        if (top_down) top_down[l] = (int32_t)g->last.lvl_td[l];
+        if (frontier) frontier[l] = (int64_t)g->last.lvl_front[l];
+    }
+    if (L > 0) {
+        if (level_ns) level_ns[0] = 0;
+        if (top_down) top_down[0] = 0;
+        if (frontier) frontier[0] = 0;
+    }
+    return L;
 }
 
 int cc_last_call_timing(cc_graph_t g, int32_t *launches, double *kernel_ms,

@@ -36,6 +36,8 @@ struct LevelCtl {
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
 
+constexpr int kTraceLevels = 64;
+
 struct Ctl {
     unsigned int bar_count;
     unsigned int bar_gen;
@@ -45,6 +47,11 @@ struct Ctl {
     unsigned long long td_levels, bu_levels;
     unsigned long long edges, words;  // CSR entries examined, words gathered
     LevelCtl lev[4];
+    // Trace of the first kTraceLevels levels: global timer at the start of
+    // each level (and at the end of the pass), direction and frontier size.
+    unsigned long long lvl_ns[kTraceLevels + 1];
+    unsigned int lvl_td[kTraceLevels];
+    unsigned int lvl_front[kTraceLevels];
 };
 
 // One traversal pass over one graph.

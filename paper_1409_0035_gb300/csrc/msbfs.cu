@@ -33,6 +33,7 @@ namespace ccg {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int kUnroll = 4;  // independent gathers in flight per lane and step
 
 __device__ __forceinline__ uint64_t gtimer()
 {
@@ -115,7 +116,7 @@ struct LaneAcc {
     // Per-lane histogram counts (W <= 8): hc[2s+h] counts source
     // s*64 + h*32 + lane.
     uint32_t hc[W <= 8 ? 2 * W : 1];
-    unsigned long long ef, eu_dec, words, edges;
+    unsigned long long ef, eu_dec, words;
     unsigned int ninc_dec;
 };
 
@@ -231,6 +232,30 @@ __device__ __forceinline__ uint64_t or_same_word(uint64_t x)
     return x;
 }
 
+// OR of the frontier words (slot w) of up to U CSR entries x, x+stride, ...
+// below e.  The U column loads and the U gathers are independent, so they
+// are all in flight together.
+template <int W, int U>
+__device__ __forceinline__ uint64_t gather_or(const int32_t *__restrict__ col,
+                                              const uint64_t *Fin, int64_t x, int64_t e,
+                                              int stride, int w, unsigned long long &words)
+{
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t ee = x + (int64_t)u * stride;
+        c[u] = ee < e ? __ldg(col + ee) : -1;
+    }
+    uint64_t f = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (c[u] >= 0) {
+            f |= Fin[(int64_t)c[u] * W + w];
+            words += 1;
+        }
+    return f;
+}
+
 __device__ __forceinline__ unsigned long long block_sum64(unsigned long long x,
                                                           unsigned long long *s)
 {
@@ -285,8 +310,55 @@ __device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
     }
 }
 
+// Top-down push of one frontier node's words f (slot w per lane) to the
+// CSR entries [b, e): new bits are OR-ed into nxt and each node reached for
+// the first time this level is appended (once) to the touched list.  Called
+// by a whole warp; lane groups of W take NPW entries per step, kUnroll steps
+// at a time.
 template <int W>
-__global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
+__device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restrict__ col,
+                                        uint64_t f, int64_t b, int64_t e, LevelCtl *C,
+                                        LaneAcc<W> &A)
+{
+    constexpr int NPW = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int w = lane & (W - 1);
+    const int grp = lane / W;
+    if (f == 0ull) return;
+    for (int64_t base = b + grp; base < e; base += NPW * kUnroll) {
+        int vv[kUnroll];
+        uint64_t vs[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            const int64_t ee = base + (int64_t)q * NPW;
+            vv[q] = ee < e ? __ldg(col + ee) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q)
+            vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + w] : ~0ull;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            if (vv[q] < 0) continue;
+            const int v = vv[q];
+            A.words += 1;
+            const uint64_t nbits = f & ~vs[q];
+            if (!nbits) continue;
+            const uint64_t old =
+                atomicOr((unsigned long long *)&J.nxt[(int64_t)v * W + w], nbits);
+            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u) {
+                const unsigned m = __activemask();
+                const int first = __ffs(m) - 1;
+                unsigned pos = 0;
+                if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
+                pos = __shfl_sync(m, pos, first);
+                J.T[pos + __popc(m & ((1u << lane) - 1u))] = v;
+            }
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
 {
     extern __shared__ unsigned s_hist[];  // W * 64 counters
     constexpr int NPW = 32 / W;           // nodes (or entries) per warp step
@@ -306,7 +378,7 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
     LaneAcc<W> A;
 #pragma unroll
     for (int i = 0; i < (W <= 8 ? 2 * W : 1); ++i) A.hc[i] = 0;
-    A.ef = A.eu_dec = A.words = A.edges = 0;
+    A.ef = A.eu_dec = A.words = 0;
     A.ninc_dec = 0;
 
     // ---- level 0: clear the state, seed the sources -----------------------
@@ -354,6 +426,11 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
             break;
         }
         const bool td = ef * (unsigned long long)J.alpha < (unsigned long long)eu;
+        if (gtid == 0 && l < kTraceLevels) {
+            ctl->lvl_ns[l] = gtimer();
+            ctl->lvl_td[l] = td;
+            ctl->lvl_front[l] = qprev;
+        }
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
             Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
@@ -371,32 +448,21 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
                 for (int64_t i = gtid; i < (int64_t)q2 * W; i += gthreads)
                     Fout[(int64_t)Qout[i / W] * W + (i & (W - 1))] = 0;
             }
-            // P1b: push the frontier words of the queued nodes.
+            // P1b: push the frontier words of the queued nodes; a heavy
+            // node's list is pushed by its 256-entry chunk tasks instead.
             for (int64_t t = gwarp; t < (int64_t)qprev; t += nwarps) {
                 const int u = Qin[t];
-                const uint64_t f = Fin[(int64_t)u * W + w];
                 const int64_t b = rp[u], e = rp[u + 1];
-                for (int64_t base = b; base < e; base += NPW) {
-                    const int64_t ee = base + grp;
-                    if (ee < e && f) {
-                        const int v = col[ee];
-                        const int64_t vw = (int64_t)v * W + w;
-                        A.edges += 1;
-                        A.words += 1;
-                        const uint64_t nbits = f & ~J.vis[vw];
-                        if (nbits) {
-                            const uint64_t old = atomicOr((unsigned long long *)&J.nxt[vw], nbits);
-                            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u) {
-                                const unsigned m = __activemask();
-                                const int first = __ffs(m) - 1;
-                                unsigned pos = 0;
-                                if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
-                                pos = __shfl_sync(m, pos, first);
-                                J.T[pos + __popc(m & ((1u << lane) - 1u))] = v;
-                            }
-                        }
-                    }
-                }
+                if (e - b > kMediumMaxDeg) continue;
+                const uint64_t f = Fin[(int64_t)u * W + w];
+                td_push<W>(J, col, f, b, e, C, A);
+            }
+            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
+                const int u = J.Hch_node[t];
+                const uint64_t f = Fin[(int64_t)u * W + w];
+                if (__all_sync(FULL, f == 0ull)) continue;
+                const int64_t b = J.Hch_begin[t];
+                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, A);
             }
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             // P2: finalise the touched nodes.
@@ -432,9 +498,8 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
                 if (valid) { b = rp[v]; e = rp[v + 1]; }
                 uint64_t acc = 0;
                 if (vis != ~0ull) {
-                    for (int64_t ee = b; ee < e; ++ee) {
-                        acc |= Fin[(int64_t)col[ee] * W + w];
-                        A.words += 1;
+                    for (int64_t x = b; x < e; x += kUnroll) {
+                        acc |= gather_or<W, kUnroll>(col, Fin, x, e, 1, w, A.words);
                         if ((acc | vis) == ~0ull) break;
                     }
                 }
@@ -449,12 +514,9 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
                 const int64_t b = rp[v], e = rp[v + 1];
                 uint64_t acc = 0;
                 if (!__all_sync(FULL, visw == ~0ull)) {
-                    for (int64_t base = b; base < e; base += NPW) {
-                        const int64_t ee = base + grp;
-                        if (ee < e) {
-                            acc |= Fin[(int64_t)col[ee] * W + w];
-                            A.words += 1;
-                        }
+                    for (int64_t base = b; base < e; base += NPW * kUnroll) {
+                        acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w,
+                                                     A.words);
                         const uint64_t r = or_same_word<W>(acc);
                         if (__all_sync(FULL, (r | visw) == ~0ull)) break;
                     }
@@ -473,12 +535,8 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
                 uint64_t acc = 0;
-                for (int64_t base = b; base < e; base += NPW) {
-                    const int64_t ee = base + grp;
-                    if (ee < e) {
-                        acc |= Fin[(int64_t)col[ee] * W + w];
-                        A.words += 1;
-                    }
+                for (int64_t base = b; base < e; base += NPW * kUnroll) {
+                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
                     const uint64_t r = or_same_word<W>(acc);
                     if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
                 }
@@ -513,14 +571,11 @@ __global__ void __launch_bounds__(kBlock) msbfs_kernel(BfsJob J)
     // Pass statistics.
     __shared__ unsigned long long s_red[kBlock / 32];
     const unsigned long long words = block_sum64(A.words, s_red);
-    const unsigned long long edges = block_sum64(A.edges, s_red);
-    if (tid == 0) {
-        atomicAdd(&ctl->words, words);
-        atomicAdd(&ctl->edges, edges);
-    }
+    if (tid == 0) atomicAdd(&ctl->words, words);
     if (gtid == 0) {
         ctl->levels = last;
         ctl->ninc_final = ninc;
+        ctl->lvl_ns[l < kTraceLevels ? l : kTraceLevels] = gtimer();
     }
 }
 
