@@ -448,12 +448,12 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 for (int64_t i = gtid; i < (int64_t)q2 * W; i += gthreads)
                     Fout[(int64_t)Qout[i / W] * W + (i & (W - 1))] = 0;
             }
-            // P1b: push the frontier words of the queued nodes; a heavy
-            // node's list is pushed by its 256-entry chunk tasks instead.
+            // P1b: push the frontier words of the queued nodes; when the
+            // graph has chunk tasks, a heavy node's list is pushed by them.
             for (int64_t t = gwarp; t < (int64_t)qprev; t += nwarps) {
                 const int u = Qin[t];
                 const int64_t b = rp[u], e = rp[u + 1];
-                if (e - b > kMediumMaxDeg) continue;
+                if (J.nHch > 0 && e - b > kMediumMaxDeg) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
                 td_push<W>(J, col, f, b, e, C, A);
             }
