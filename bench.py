@@ -328,8 +328,9 @@ def run_ours(args):
                                          "sources": nsingle,
                                          "speedup": value / single_gteps},
             "pass_stats": stats,
-            "level_trace": [{"level": l, "us": ns / 1e3, "top_down": td, "frontier": fr}
-                            for (l, ns, td, fr) in trace],
+            "level_trace": [{"level": l, "us": ns / 1e3, "top_down": td, "frontier": fr,
+                             "frontier_arcs": fa, "words": wd}
+                            for (l, ns, td, fr, fa, wd) in trace],
             "estimates_per_s": n / (ms_step / 1e3)}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

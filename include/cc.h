@@ -234,11 +234,13 @@ int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td_levels,
 
 /* Per-level trace of the last traversal pass on g (levels 1 .. D, at most
  * max_levels and at most 64): device time of each level in ns (global timer
- * on the device), whether it ran top-down (1) or bottom-up (0), and the
- * frontier size it started from.  Entry 0 is zero.  Returns the number of
- * entries written (D + 1, capped) or a negative CC_ERR_* code. */
+ * on the device), whether it ran top-down (1) or bottom-up (0), the frontier
+ * size it started from, the CSR entries of that frontier and the frontier
+ * words it gathered.  Entry 0 is zero; any pointer may be NULL.  Returns the
+ * number of entries written (D + 1, capped) or a negative CC_ERR_* code. */
 int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
-                       int32_t *top_down, int64_t *frontier);
+                       int32_t *top_down, int64_t *frontier,
+                       int64_t *frontier_arcs, int64_t *words);
 
 /* Traversal kernel launches of the last cc_estimate / cc_exact /
  * cc_sampling_sums_single call on g: their number, their summed device time

@@ -84,7 +84,7 @@ def lib():
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
-        L.cc_last_pass_trace.argtypes = [P, i32, P, P, P]
+        L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
@@ -234,14 +234,18 @@ def cc_last_pass_stats(g):
 
 
 def cc_last_pass_trace(g, max_levels=64):
-    """List of (level, ns, top_down, frontier) of the last traversal pass."""
+    """List of (level, ns, top_down, frontier, frontier_arcs, words) of the
+    last traversal pass."""
     t = np.zeros(max_levels, np.int64)
     d = np.zeros(max_levels, np.int32)
     f = np.zeros(max_levels, np.int64)
-    L = lib().cc_last_pass_trace(g, max_levels, _p(t), _p(d), _p(f))
+    fa = np.zeros(max_levels, np.int64)
+    wd = np.zeros(max_levels, np.int64)
+    L = lib().cc_last_pass_trace(g, max_levels, _p(t), _p(d), _p(f), _p(fa), _p(wd))
     if L < 0:
         raise CCError(L, "cc_last_pass_trace")
-    return [(l, int(t[l]), int(d[l]), int(f[l])) for l in range(1, L)]
+    return [(l, int(t[l]), int(d[l]), int(f[l]), int(fa[l]), int(wd[l]))
+            for l in range(1, L)]
 
 
 def cc_last_call_timing(g):

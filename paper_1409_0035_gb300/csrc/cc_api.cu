@@ -9,6 +9,7 @@
 
 #include "cc_internal.h"
 #include "estimate.h"
+#include "sssp.h"
 
 using namespace ccg;
 
@@ -16,6 +17,7 @@ namespace {
 
 constexpr uint64_t kTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
 constexpr int kAlpha = 14;
+constexpr double kMaxHistBytes = 4.0 * (1ull << 30);  // distance histogram cap
 
 struct DevBuf {
     void *p = nullptr;
@@ -61,7 +63,9 @@ struct cc_graph {
     DevCSR fw, rv;
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
-        dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum;
+        dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
+        distF, distR, mask, best, dmax, errflag, fbm;
+    int64_t dist_max = 0;  // largest distance seen by the last estimate
     int hist_cap = 0;
     Ctl last{};
     // Traversal launches of the last API call: count, device time (CUDA
@@ -149,6 +153,7 @@ int ensure_state(cc_graph *g, int W)
     RC(g->sidx.ensure(n * 4));
     RC(g->sum2.ensure(n * 16));
     RC(g->ctl.ensure(sizeof(Ctl)));
+    RC(g->fbm.ensure((size_t)3 * ((n + 31) / 32) * 4));
     return CC_OK;
 }
 
@@ -173,6 +178,7 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
     j.F0 = g->F0.as<uint64_t>();
     j.F1 = g->F1.as<uint64_t>();
     j.nxt = g->nxt.as<uint64_t>();
+    j.fbm = g->fbm.as<unsigned>();
     j.Q0 = g->Q0.as<int32_t>();
     j.Q1 = g->Q1.as<int32_t>();
     j.T = g->T.as<int32_t>();
@@ -262,11 +268,298 @@ void free_graph(cc_graph *g)
                      &g->T, &g->tflag, &g->sidx, &g->sum2, &g->pivot, &g->delta, &g->lc2,
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
-                     &g->hyb, &g->ssum};
+                     &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
+                     &g->dmax, &g->errflag, &g->fbm};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     g->ev0 = g->ev1 = nullptr;
+}
+
+
+// Unweighted undirected graphs: one bit-packed multi-source pass for sums,
+// pivots, Delta, delta_cc and the per-level histogram, and a second pass
+// with the L(v) masks only when some node's L(v) misses a sampled node.
+int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const int W = pow2_words(k);
+    RC(ensure_state(g, W));
+    if (g->hist_cap == 0) g->hist_cap = (int)std::min<int64_t>(n + 1, 4096);
+    BfsJob j = base_job(g, W, g->fw);
+    j.k = k;
+    j.sources = g->sources.as<int32_t>();
+    j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
+    j.pivot = g->pivot.as<int32_t>();
+    j.delta = g->delta.as<uint32_t>();
+    j.dcc = g->dcc.as<uint32_t>();
+    j.dcc_k = k;
+    for (;;) {
+        RC(g->hist.ensure((size_t)g->hist_cap * k * 4));
+        j.hist = g->hist.as<uint32_t>();
+        j.hist_cap = g->hist_cap;
+        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+        CK(cudaMemsetAsync(g->hist.p, 0, (size_t)g->hist_cap * k * 4, st));
+        CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
+        RC(run_pass(g, W, j, st));
+        if (g->last.err == 1) {  // histogram too short: grow and rerun
+            if (g->hist_cap > n) return CC_ERR_TOO_LARGE;
+            g->hist_cap = (int)std::min<int64_t>(n + 1, (int64_t)g->hist_cap * 4);
+            continue;
+        }
+        break;
+    }
+    if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+    const int D = g->last.levels;
+    g->dist_max = D;
+    run_S_sampled(g->hist.as<uint32_t>(), D, k, g->dcc.as<uint32_t>(),
+                  g->Ssamp.as<uint64_t>(), st);
+    g->call_kernels += 1;
+    if (!opts->want_hybrid) return CC_OK;
+    RC(g->TN.ensure((size_t)k * (D + 1) * 8));
+    RC(g->TS.ensure((size_t)k * (D + 1) * 8));
+    RC(g->maxd.ensure((size_t)k * 4));
+    RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
+    RC(g->npartial.ensure(4));
+    CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
+    run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
+    run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
+    run_hyb_prep(3, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+                 g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
+                 g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
+                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), st);
+    g->call_kernels += 3;
+    unsigned npart = 0;
+    CK(cudaMemcpyAsync(&npart, g->npartial.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    RC(g->lc2.ensure(n * 16));
+    if (npart == 0) return CC_OK;
+    RC(g->Lmask.ensure((size_t)n * W * 8));
+    run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
+              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
+    g->call_kernels += 1;
+    CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
+    BfsJob j2 = base_job(g, W, g->fw);
+    j2.k = k;
+    j2.sources = g->sources.as<int32_t>();
+    j2.red = RED_LC;
+    j2.Lmask = g->Lmask.as<uint64_t>();
+    j2.lc2 = g->lc2.as<uint64_t>();
+    return run_pass(g, W, j2, st);
+}
+
+// One 32-source chunk of shortest paths (forward, and reversed for round
+// trips) into g->distF / g->distR.
+int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
+        const DevCSR &c = dir ? g->rv : g->fw;
+        SsspJob j;
+        std::memset(&j, 0, sizeof(j));
+        j.n = n;
+        j.rp = c.rp.as<int64_t>();
+        j.col = c.col.as<int32_t>();
+        j.w = g->weighted ? c.w.as<uint32_t>() : nullptr;
+        j.kc = kc;
+        j.sources = d_sources;
+        j.dist = (dir ? g->distR : g->distF).as<uint32_t>();
+        j.mask = g->mask.as<unsigned>();
+        j.Q0 = g->Q0.as<int32_t>();
+        j.Q1 = g->Q1.as<int32_t>();
+        j.ctl = g->ctl.as<Ctl>();
+        j.timeout_ns = kTimeoutNs;
+        if (!g->ev0) {
+            CK(cudaEventCreate(&g->ev0));
+            CK(cudaEventCreate(&g->ev1));
+        }
+        CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), st));
+        CK(cudaEventRecord(g->ev0, st));
+        RC(launch_mssp(j, st));
+        CK(cudaEventRecord(g->ev1, st));
+        CK(cudaMemcpyAsync(&g->last, g->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+        g->call_launches += 1;
+        g->call_kernels += 1;
+        g->call_ms += ms;
+        // relaxations x (row read 4 B + arc 8 B) + the n x 32 rows written once
+        g->call_bytes += (double)g->last.words * 12.0 + (double)n * kChunkSrc * 4.0;
+        if (g->last.err < 0) return g->last.err;
+    }
+    return CC_OK;
+}
+
+ReduceJob base_reduce(cc_graph *g, int k, int W)
+{
+    ReduceJob r;
+    std::memset(&r, 0, sizeof(r));
+    r.n = g->n;
+    r.k = k;
+    r.W = W;
+    r.distF = g->distF.as<uint32_t>();
+    r.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+    r.sidx = g->sidx.as<int32_t>();
+    r.sum2 = g->sum2.as<uint64_t>();
+    r.best = g->best.as<unsigned long long>();
+    r.dcc = g->dcc.as<uint32_t>();
+    r.S_samp = g->Ssamp.as<unsigned long long>();
+    r.dmax = g->dmax.as<unsigned long long>();
+    r.err = g->errflag.as<int>();
+    return r;
+}
+
+// Weighted or directed (round-trip) graphs: the k sources in 32-source
+// chunks of shortest paths, each reduced into the same per-node statistics;
+// the hybrid needs a second sweep (histogram of distances and L(v) sums).
+int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const int W = pow2_words(k);
+    RC(g->distF.ensure((size_t)n * kChunkSrc * 4));
+    if (g->directed) RC(g->distR.ensure((size_t)n * kChunkSrc * 4));
+    RC(g->mask.ensure(n * 4));
+    RC(g->Q0.ensure(n * 4));
+    RC(g->Q1.ensure(n * 4));
+    RC(g->best.ensure(n * 8));
+    RC(g->dmax.ensure(8));
+    RC(g->errflag.ensure(4));
+    CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+    CK(cudaMemsetAsync(g->best.p, 0xFF, n * 8, st));
+    CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
+    CK(cudaMemsetAsync(g->Ssamp.p, 0, (size_t)k * 8, st));
+    CK(cudaMemsetAsync(g->dmax.p, 0, 8, st));
+    CK(cudaMemsetAsync(g->errflag.p, 0, 4, st));
+    const int32_t *src = g->sources.as<int32_t>();
+    ReduceJob r = base_reduce(g, k, W);
+    for (int base = 0; base < k; base += kChunkSrc) {
+        const int kc = std::min(kChunkSrc, k - base);
+        RC(run_chunk(g, src + base, kc, st));
+        r.base = base;
+        r.kc = kc;
+        run_reduce1(r, st);
+        g->call_kernels += 1;
+    }
+    unsigned long long dmax = 0;
+    int err = 0;
+    CK(cudaMemcpyAsync(&dmax, g->dmax.p, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&err, g->errflag.p, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (err) return err;
+    run_unpack_pivot(n, g->best.as<unsigned long long>(), g->pivot.as<int32_t>(),
+                     g->delta.as<uint32_t>(), st);
+    g->call_kernels += 1;
+    g->dist_max = (int64_t)dmax;
+    if (!opts->want_hybrid) return CC_OK;
+
+    const int64_t D = (int64_t)dmax;
+    if ((double)(D + 1) * k * 4.0 > (double)kMaxHistBytes) return CC_ERR_TOO_LARGE;
+    RC(g->hist.ensure((size_t)(D + 1) * k * 4));
+    RC(g->TN.ensure((size_t)k * (D + 1) * 8));
+    RC(g->TS.ensure((size_t)k * (D + 1) * 8));
+    RC(g->maxd.ensure((size_t)k * 4));
+    RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
+    RC(g->npartial.ensure(4));
+    RC(g->Lmask.ensure((size_t)n * W * 8));
+    RC(g->lc2.ensure(n * 16));
+    CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
+    CK(cudaMemsetAsync(g->hist.p, 0, (size_t)(D + 1) * k * 4, st));
+    CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
+    run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
+    run_hyb_prep(1, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+                 g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
+                 g->maxd.as<uint32_t>(), nullptr, nullptr, g->hp.as<HybPrep>(),
+                 g->npartial.as<unsigned>(), st);
+    run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
+              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
+    g->call_kernels += 3;
+    r.hist = g->hist.as<uint32_t>();
+    r.Lmask = g->Lmask.as<uint64_t>();
+    r.lc2 = g->lc2.as<uint64_t>();
+    for (int base = 0; base < k; base += kChunkSrc) {
+        const int kc = std::min(kChunkSrc, k - base);
+        RC(run_chunk(g, src + base, kc, st));
+        r.base = base;
+        r.kc = kc;
+        run_reduce2(r, st);
+        g->call_kernels += 1;
+    }
+    run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
+    run_hyb_prep(2, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+                 g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
+                 g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
+                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), st);
+    g->call_kernels += 2;
+    return CC_OK;
+}
+
+// Finalise into device buffers (or straight into device outputs) and copy.
+int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
+                   cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const bool dev_out = opts->device_outputs != 0;
+    FinalizeArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    fa.n = n;
+    fa.k = k;
+    fa.hybrid = hyb;
+    fa.sidx = g->sidx.as<int32_t>();
+    fa.pivot = g->pivot.as<int32_t>();
+    fa.delta = g->delta.as<uint32_t>();
+    fa.sum2 = g->sum2.as<uint64_t>();
+    fa.S_samp = g->Ssamp.as<uint64_t>();
+    fa.lc2 = g->lc2.as<uint64_t>();
+    fa.hp = g->hp.as<HybPrep>();
+    if (dev_out) {
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            fa.s_hat[e] = out->s_hat[e];
+            fa.clo[e] = out->closeness[e];
+        }
+        fa.hyb_int = out->hyb_int;
+        fa.sample_sum = out->sample_sum;
+    } else {
+        RC(g->shat.ensure((size_t)n * 8 * CC_NUM_EST));
+        RC(g->clo.ensure((size_t)n * 8 * CC_NUM_EST));
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            fa.s_hat[e] = out->s_hat[e] ? g->shat.as<double>() + (size_t)e * n : nullptr;
+            fa.clo[e] = out->closeness[e] ? g->clo.as<double>() + (size_t)e * n : nullptr;
+        }
+        if (out->hyb_int) {
+            RC(g->hyb.ensure((size_t)n * 48));
+            fa.hyb_int = g->hyb.as<uint64_t>();
+        }
+        if (out->sample_sum) {
+            RC(g->ssum.ensure((size_t)n * 8));
+            fa.sample_sum = g->ssum.as<uint64_t>();
+        }
+    }
+    run_finalize(fa, st);
+    g->call_kernels += 1;
+    const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!dev_out) {
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            if (e == CC_EST_HYBRID && !hyb) continue;
+            if (out->s_hat[e])
+                CK(cudaMemcpyAsync(out->s_hat[e], fa.s_hat[e], n * 8, kind, st));
+            if (out->closeness[e])
+                CK(cudaMemcpyAsync(out->closeness[e], fa.clo[e], n * 8, kind, st));
+        }
+        if (out->hyb_int && hyb)
+            CK(cudaMemcpyAsync(out->hyb_int, fa.hyb_int, n * 48, kind, st));
+        if (out->sample_sum)
+            CK(cudaMemcpyAsync(out->sample_sum, fa.sample_sum, n * 8, kind, st));
+    }
+    if (out->pivot) CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
+    if (out->delta) CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
+    if (out->S_sampled)
+        CK(cudaMemcpyAsync(out->S_sampled, g->Ssamp.p, (size_t)k * 8, kind, st));
+    if (out->delta_cc)
+        CK(cudaMemcpyAsync(out->delta_cc, g->dcc.p, (size_t)k * k * 4, kind, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return CC_OK;
 }
 
 int device_ok()
@@ -393,7 +686,8 @@ int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td, int64_t *bu,
 }
 
 int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
-                       int32_t *top_down, int64_t *frontier)
+                       int32_t *top_down, int64_t *frontier, int64_t *frontier_arcs,
+                       int64_t *words)
 {
     if (!g || max_levels < 0) return CC_ERR_ARG;
     const int L = std::min<int>(g->last.levels + 1, std::min<int>(max_levels, kTraceLevels));
@@ -402,11 +696,15 @@ int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
         if (level_ns) level_ns[l] = t1 > g->last.lvl_ns[l] ? (int64_t)(t1 - g->last.lvl_ns[l]) : 0;
         if (top_down) top_down[l] = (int32_t)g->last.lvl_td[l];
         if (frontier) frontier[l] = (int64_t)g->last.lvl_front[l];
+        if (frontier_arcs) frontier_arcs[l] = (int64_t)g->last.lvl_ef[l];
+        if (words) words[l] = (int64_t)g->last.lvl_words[l];
     }
     if (L > 0) {
         if (level_ns) level_ns[0] = 0;
         if (top_down) top_down[0] = 0;
         if (frontier) frontier[0] = 0;
+        if (frontier_arcs) frontier_arcs[0] = 0;
+        if (words) words[0] = 0;
     }
     return L;
 }
@@ -435,179 +733,94 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *o
 {
     if (!g || !opts || !out) return CC_ERR_ARG;
     if (opts->eps_num == 0 || opts->eps_num > opts->eps_den) return CC_ERR_ARG;
-    if (g->directed || opts->roundtrip || g->weighted) return CC_ERR_ARG;  // later passes
+    if ((opts->roundtrip != 0) != g->directed) return CC_ERR_ARG;
     RC(validate_sample(g, sample, k));
     reset_timing(g);
     cudaStream_t st = (cudaStream_t)opts->stream;
     const int64_t n = g->n;
-    const int W = pow2_words(k);
-    RC(ensure_state(g, W));
+    RC(g->sidx.ensure(n * 4));
+    RC(g->sum2.ensure(n * 16));
     RC(g->pivot.ensure(n * 4));
     RC(g->delta.ensure(n * 4));
     RC(g->dcc.ensure((size_t)k * k * 4));
     RC(g->Ssamp.ensure((size_t)k * 8));
     RC(g->sources.ensure((size_t)k * 4));
-    if (g->hist_cap == 0) g->hist_cap = (int)std::min<int64_t>(n + 1, 4096);
+    RC(g->ctl.ensure(sizeof(Ctl)));
     CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
     run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
     run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
     g->call_kernels += 2;
-
-    BfsJob j = base_job(g, W, g->fw);
-    j.k = k;
-    j.sources = g->sources.as<int32_t>();
-    j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
-    j.pivot = g->pivot.as<int32_t>();
-    j.delta = g->delta.as<uint32_t>();
-    j.dcc = g->dcc.as<uint32_t>();
-    j.dcc_k = k;
-    for (;;) {
-        RC(g->hist.ensure((size_t)g->hist_cap * k * 4));
-        j.hist = g->hist.as<uint32_t>();
-        j.hist_cap = g->hist_cap;
-        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
-        CK(cudaMemsetAsync(g->hist.p, 0, (size_t)g->hist_cap * k * 4, st));
-        CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
-        RC(run_pass(g, W, j, st));
-        if (g->last.err == 1) {  // histogram too short: grow and rerun
-            if (g->hist_cap > n) return CC_ERR_TOO_LARGE;
-            g->hist_cap = (int)std::min<int64_t>(n + 1, (int64_t)g->hist_cap * 4);
-            continue;
-        }
-        break;
-    }
-    if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
-    const int D = g->last.levels;
-    run_S_sampled(g->hist.as<uint32_t>(), D, k, g->dcc.as<uint32_t>(),
-                  g->Ssamp.as<uint64_t>(), st);
-    g->call_kernels += 1;
-
     const bool hyb = opts->want_hybrid != 0;
-    if (hyb) {
-        RC(g->TN.ensure((size_t)k * (D + 1) * 8));
-        RC(g->TS.ensure((size_t)k * (D + 1) * 8));
-        RC(g->maxd.ensure((size_t)k * 4));
-        RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
-        RC(g->npartial.ensure(4));
-        CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
-        run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
-                 st);
-        run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
-        run_hyb_prep(n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
-                     g->pivot.as<int32_t>(), g->delta.as<uint32_t>(),
-                     g->dcc.as<uint32_t>(), g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(),
-                     g->TS.as<uint64_t>(), g->hp.as<HybPrep>(),
-                     g->npartial.as<unsigned>(), st);
-        g->call_kernels += 3;
-        unsigned npart = 0;
-        CK(cudaMemcpyAsync(&npart, g->npartial.p, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        RC(g->lc2.ensure(n * 16));
-        if (npart > 0) {
-            RC(g->Lmask.ensure((size_t)n * W * 8));
-            run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(),
-                      g->dcc.as<uint32_t>(), g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(),
-                      st);
-            g->call_kernels += 1;
-            CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
-            BfsJob j2 = base_job(g, W, g->fw);
-            j2.k = k;
-            j2.sources = g->sources.as<int32_t>();
-            j2.red = RED_LC;
-            j2.Lmask = g->Lmask.as<uint64_t>();
-            j2.lc2 = g->lc2.as<uint64_t>();
-            RC(run_pass(g, W, j2, st));
-        }
-    }
-
-    // Finalise into device buffers (or straight into device outputs).
-    const bool dev_out = opts->device_outputs != 0;
-    FinalizeArgs fa;
-    std::memset(&fa, 0, sizeof(fa));
-    fa.n = n;
-    fa.k = k;
-    fa.hybrid = hyb;
-    fa.sidx = g->sidx.as<int32_t>();
-    fa.pivot = g->pivot.as<int32_t>();
-    fa.delta = g->delta.as<uint32_t>();
-    fa.sum2 = g->sum2.as<uint64_t>();
-    fa.S_samp = g->Ssamp.as<uint64_t>();
-    fa.lc2 = g->lc2.as<uint64_t>();
-    fa.hp = g->hp.as<HybPrep>();
-    if (dev_out) {
-        for (int e = 0; e < CC_NUM_EST; ++e) {
-            fa.s_hat[e] = out->s_hat[e];
-            fa.clo[e] = out->closeness[e];
-        }
-        fa.hyb_int = out->hyb_int;
-        fa.sample_sum = out->sample_sum;
-    } else {
-        RC(g->shat.ensure((size_t)n * 8 * CC_NUM_EST));
-        RC(g->clo.ensure((size_t)n * 8 * CC_NUM_EST));
-        for (int e = 0; e < CC_NUM_EST; ++e) {
-            fa.s_hat[e] = out->s_hat[e] ? g->shat.as<double>() + (size_t)e * n : nullptr;
-            fa.clo[e] = out->closeness[e] ? g->clo.as<double>() + (size_t)e * n : nullptr;
-        }
-        if (out->hyb_int) {
-            RC(g->hyb.ensure((size_t)n * 48));
-            fa.hyb_int = g->hyb.as<uint64_t>();
-        }
-        if (out->sample_sum) {
-            RC(g->ssum.ensure((size_t)n * 8));
-            fa.sample_sum = g->ssum.as<uint64_t>();
-        }
-    }
-    run_finalize(fa, st);
-    g->call_kernels += 1;
-    const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (!dev_out) {
-        for (int e = 0; e < CC_NUM_EST; ++e) {
-            if (e == CC_EST_HYBRID && !hyb) continue;
-            if (out->s_hat[e])
-                CK(cudaMemcpyAsync(out->s_hat[e], fa.s_hat[e], n * 8, kind, st));
-            if (out->closeness[e])
-                CK(cudaMemcpyAsync(out->closeness[e], fa.clo[e], n * 8, kind, st));
-        }
-        if (out->hyb_int && hyb)
-            CK(cudaMemcpyAsync(out->hyb_int, fa.hyb_int, n * 48, kind, st));
-        if (out->sample_sum)
-            CK(cudaMemcpyAsync(out->sample_sum, fa.sample_sum, n * 8, kind, st));
-    }
-    if (out->pivot) CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
-    if (out->delta) CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
-    if (out->S_sampled)
-        CK(cudaMemcpyAsync(out->S_sampled, g->Ssamp.p, (size_t)k * 8, kind, st));
-    if (out->delta_cc)
-        CK(cudaMemcpyAsync(out->delta_cc, g->dcc.p, (size_t)k * k * 4, kind, st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
-    return CC_OK;
+    const int rc = (g->weighted || g->directed) ? estimate_chunked(g, k, opts, st)
+                                                : estimate_bfs(g, k, opts, st);
+    if (rc != CC_OK) return rc;
+    return finish_outputs(g, k, hyb, opts, out, st);
 }
 
 int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
 {
     if (!g) return CC_ERR_ARG;
-    if (g->directed || g->weighted) return CC_ERR_ARG;
     const int64_t n = g->n;
-    const int kc = (int)std::min<int64_t>(n, CC_MAX_K);
-    const int W = pow2_words(kc);
     cudaStream_t st = 0;
     reset_timing(g);
-    RC(ensure_state(g, W));
-    RC(g->sources.ensure((size_t)kc * 4));
-    CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
-    std::vector<int32_t> src(kc);
-    for (int64_t base = 0; base < n; base += kc) {
-        const int kk = (int)std::min<int64_t>(kc, n - base);
-        for (int i = 0; i < kk; ++i) src[i] = (int32_t)(base + i);
-        CK(cudaMemcpyAsync(g->sources.p, src.data(), (size_t)kk * 4, cudaMemcpyHostToDevice,
-                           st));
-        BfsJob j = base_job(g, W, g->fw);
-        j.k = kk;
-        j.sources = g->sources.as<int32_t>();
-        j.red = RED_SUM;
-        RC(run_pass(g, W, j, st));
-        if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+    std::vector<int32_t> src;
+    if (g->weighted || g->directed) {
+        // Every node as a source, 32 per chunk of shortest paths; S(v) is the
+        // sum of the chunk distances (round trips on directed graphs).
+        RC(g->sum2.ensure(n * 16));
+        RC(g->ctl.ensure(sizeof(Ctl)));
+        RC(g->sources.ensure((size_t)n * 4));
+        RC(g->distF.ensure((size_t)n * kChunkSrc * 4));
+        if (g->directed) RC(g->distR.ensure((size_t)n * kChunkSrc * 4));
+        RC(g->mask.ensure(n * 4));
+        RC(g->Q0.ensure(n * 4));
+        RC(g->Q1.ensure(n * 4));
+        RC(g->errflag.ensure(4));
+        RC(g->sidx.ensure(n * 4));
+        src.resize(n);
+        for (int64_t v = 0; v < n; ++v) src[v] = (int32_t)v;
+        CK(cudaMemcpy(g->sources.p, src.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+        CK(cudaMemsetAsync(g->errflag.p, 0, 4, st));
+        ReduceJob r;
+        std::memset(&r, 0, sizeof(r));
+        r.n = n;
+        r.k = (int)std::min<int64_t>(n, 0x7FFFFFFF);
+        r.distF = g->distF.as<uint32_t>();
+        r.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+        r.sidx = g->sidx.as<int32_t>();
+        r.sum2 = g->sum2.as<uint64_t>();
+        r.err = g->errflag.as<int>();
+        r.sum_only = 1;
+        for (int64_t base = 0; base < n; base += kChunkSrc) {
+            const int kc = (int)std::min<int64_t>(kChunkSrc, n - base);
+            RC(run_chunk(g, g->sources.as<int32_t>() + base, kc, st));
+            r.base = (int)base;
+            r.kc = kc;
+            run_reduce1(r, st);
+        }
+        int err = 0;
+        CK(cudaMemcpy(&err, g->errflag.p, 4, cudaMemcpyDeviceToHost));
+        if (err) return err;
+    } else {
+        const int kc = (int)std::min<int64_t>(n, CC_MAX_K);
+        const int W = pow2_words(kc);
+        RC(ensure_state(g, W));
+        RC(g->sources.ensure((size_t)kc * 4));
+        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+        src.resize(kc);
+        for (int64_t base = 0; base < n; base += kc) {
+            const int kk = (int)std::min<int64_t>(kc, n - base);
+            for (int i = 0; i < kk; ++i) src[i] = (int32_t)(base + i);
+            CK(cudaMemcpyAsync(g->sources.p, src.data(), (size_t)kk * 4,
+                               cudaMemcpyHostToDevice, st));
+            BfsJob j = base_job(g, W, g->fw);
+            j.k = kk;
+            j.sources = g->sources.as<int32_t>();
+            j.red = RED_SUM;
+            RC(run_pass(g, W, j, st));
+            if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+        }
     }
     std::vector<uint64_t> s2((size_t)n * 2);
     CK(cudaMemcpy(s2.data(), g->sum2.p, n * 16, cudaMemcpyDeviceToHost));

@@ -52,6 +52,8 @@ struct Ctl {
     unsigned long long lvl_ns[kTraceLevels + 1];
     unsigned int lvl_td[kTraceLevels];
     unsigned int lvl_front[kTraceLevels];
+    unsigned long long lvl_ef[kTraceLevels];
+    unsigned long long lvl_words[kTraceLevels];
 };
 
 // One traversal pass over one graph.
@@ -68,6 +70,7 @@ struct BfsJob {
     const int64_t *Hch_begin;
     int64_t nHch;
     uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
+    unsigned *fbm;                  // 3 x ceil(n/32): frontier-presence bitmaps
     int32_t *Q0, *Q1, *T;           // n each
     unsigned int *tflag;            // n
     uint32_t red;

@@ -12,6 +12,7 @@ namespace ccg {
 namespace {
 
 typedef unsigned __int128 u128;
+constexpr int kTailThreads = 256;
 
 // Round-to-nearest-even conversion of an unsigned 128-bit integer: the top
 // 64 significant bits with every lower bit folded into a sticky bit are
@@ -54,20 +55,38 @@ __global__ void k_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *
     S[i] = s;
 }
 
-// Tail tables of the per-source level histogram: TN[i][t] = number of nodes
-// of V \ C farther than t from c_i, TS[i][t] = the sum of their distances,
-// t = 0..D.  (Role of Algorithm 1's reverse scan of the bin/count arrays.)
-__global__ void k_tail(const uint32_t *hist, int D, int k, uint64_t *TN, uint64_t *TS)
+// Tail tables of the per-source distance histogram: TN[i][t] = number of
+// nodes of V \ C farther than t from c_i, TS[i][t] = the sum of their
+// distances, t = 0..D.  (Role of Algorithm 1's reverse scan of the
+// bin/count arrays.)  One CTA per source scans the histogram downwards in
+// tiles with a shared-memory suffix scan.
+__global__ void k_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-    uint64_t cn = 0, cs = 0;
-    for (int t = D; t >= 0; --t) {
-        TN[(int64_t)i * (D + 1) + t] = cn;
-        TS[(int64_t)i * (D + 1) + t] = cs;
-        const uint64_t h = hist[(int64_t)t * k + i];
-        cn += h;
-        cs += (uint64_t)t * h;
+    __shared__ unsigned long long sN[kTailThreads], sS[kTailThreads];
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x;
+    unsigned long long cn = 0, cs = 0;
+    for (int64_t top = D; top >= 0; top -= kTailThreads) {
+        const int64_t t = top - tid;
+        const unsigned long long h = t >= 0 ? hist[t * k + i] : 0ull;
+        sN[tid] = h;
+        sS[tid] = t >= 0 ? (unsigned long long)t * h : 0ull;
+        __syncthreads();
+        for (int o = 1; o < kTailThreads; o <<= 1) {
+            unsigned long long a = 0, b = 0;
+            if (tid >= o) { a = sN[tid - o]; b = sS[tid - o]; }
+            __syncthreads();
+            sN[tid] += a;
+            sS[tid] += b;
+            __syncthreads();
+        }
+        if (t >= 0) {
+            TN[(int64_t)i * (D + 1) + t] = cn + sN[tid] - h;
+            TS[(int64_t)i * (D + 1) + t] = cs + sS[tid] - (unsigned long long)t * h;
+        }
+        cn += sN[kTailThreads - 1];
+        cs += sS[kTailThreads - 1];
+        __syncthreads();
     }
 }
 
@@ -84,7 +103,10 @@ __global__ void k_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd)
 // Delta/eps" is "d > t" for integer d), H statistics from the tail tables of
 // the pivot, |L cap C| and whether L(v) misses some sampled node (then the
 // hybrid needs the second pass).
-__global__ void k_hyb_prep(int64_t n, int k, int D, uint32_t a, uint32_t b,
+// mode & 1: thresholds and |L cap C| (needs delta_cc); mode & 2: H
+// statistics from the tail tables (needs the histogram of the pass that
+// produced it).
+__global__ void k_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                            const int32_t *sidx, const int32_t *pivot,
                            const uint32_t *delta, const uint32_t *dcc,
                            const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
@@ -92,21 +114,25 @@ __global__ void k_hyb_prep(int64_t n, int k, int D, uint32_t a, uint32_t b,
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        HybPrep h = {0, 0, 0, 0};
+        HybPrep h = (mode & 1) ? HybPrep{0, 0, 0, 0} : hp[v];
         if (sidx[v] < 0) {
             const int p = pivot[v];
             const uint64_t t = (uint64_t)delta[v] * b / a;
-            const int64_t tt = t < (uint64_t)D ? (int64_t)t : D;
-            h.Hnum = TN[(int64_t)p * (D + 1) + tt];
-            h.Hsum = TS[(int64_t)p * (D + 1) + tt];
-            h.thr = t;
-            if (t >= maxd[p]) {
-                h.LCnum = (uint64_t)k;
-            } else {
-                uint64_t c = 0;
-                for (int i = 0; i < k; ++i) c += dcc[(int64_t)p * k + i] <= t;
-                h.LCnum = c | kPartialBit;
-                atomicAdd(npartial, 1u);
+            if (mode & 2) {
+                const int64_t tt = t < (uint64_t)D ? (int64_t)t : D;
+                h.Hnum = TN[(int64_t)p * (D + 1) + tt];
+                h.Hsum = TS[(int64_t)p * (D + 1) + tt];
+            }
+            if (mode & 1) {
+                h.thr = t;
+                if (t >= maxd[p]) {
+                    h.LCnum = (uint64_t)k;
+                } else {
+                    uint64_t c = 0;
+                    for (int i = 0; i < k; ++i) c += dcc[(int64_t)p * k + i] <= t;
+                    h.LCnum = c | kPartialBit;
+                    atomicAdd(npartial, 1u);
+                }
             }
         }
         hp[v] = h;
@@ -206,10 +232,10 @@ void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint
     k_S_sampled<<<(k + 127) / 128, 128, 0, st>>>(hist, D, k, dcc, S);
 }
 
-void run_tail(const uint32_t *hist, int D, int k, uint64_t *TN, uint64_t *TS,
+void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS,
               cudaStream_t st)
 {
-    k_tail<<<(k + 127) / 128, 128, 0, st>>>(hist, D, k, TN, TS);
+    k_tail<<<k, kTailThreads, 0, st>>>(hist, D, k, TN, TS);
 }
 
 void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
@@ -217,13 +243,13 @@ void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
     k_maxdelta<<<(k + 127) / 128, 128, 0, st>>>(dcc, k, maxd);
 }
 
-void run_hyb_prep(int64_t n, int k, int D, uint32_t a, uint32_t b, const int32_t *sidx,
-                  const int32_t *pivot, const uint32_t *delta, const uint32_t *dcc,
-                  const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
-                  HybPrep *hp, unsigned *npartial, cudaStream_t st)
+void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
+                  const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
+                  const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
+                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, cudaStream_t st)
 {
-    k_hyb_prep<<<grid_for(n, 256), 256, 0, st>>>(n, k, D, a, b, sidx, pivot, delta, dcc,
-                                                 maxd, TN, TS, hp, npartial);
+    k_hyb_prep<<<grid_for(n, 256), 256, 0, st>>>(mode, n, k, D, a, b, sidx, pivot, delta,
+                                                 dcc, maxd, TN, TS, hp, npartial);
 }
 
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,

@@ -34,13 +34,13 @@ void run_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
 void run_scatter_sidx(int32_t *sidx, const int32_t *src, int k, cudaStream_t st);
 void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint64_t *S,
                    cudaStream_t st);
-void run_tail(const uint32_t *hist, int D, int k, uint64_t *TN, uint64_t *TS,
+void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS,
               cudaStream_t st);
 void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st);
-void run_hyb_prep(int64_t n, int k, int D, uint32_t a, uint32_t b, const int32_t *sidx,
-                  const int32_t *pivot, const uint32_t *delta, const uint32_t *dcc,
-                  const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
-                  HybPrep *hp, unsigned *npartial, cudaStream_t st);
+void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
+                  const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
+                  const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
+                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, cudaStream_t st);
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
                const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st);
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);

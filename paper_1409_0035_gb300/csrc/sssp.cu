@@ -1,0 +1,293 @@
+// Multi-source shortest paths with uint32 arc lengths, 32 sources at a time
+// (sections 3 and 7: one Dijkstra per sampled node, 32-bit integer arc
+// lengths), and the per-chunk reductions that feed the same estimators as the
+// breadth-first path.
+//
+// A chunk holds the tentative distances of up to 32 sources as one 128-byte
+// row per node (dist[v][lane], lane = source within the chunk), so a warp
+// owns a node and each lane one source: every row read or atomicMin is one
+// coalesced line.  The chunk is solved by label-correcting relaxation in
+// rounds (Bellman-Ford over an active-node queue): a node is queued when
+// some source's distance to it drops, with a per-node bit mask of the
+// sources whose distance dropped; a round relaxes the out-arcs of every
+// queued node for exactly those sources.  Rounds run inside one persistent
+// cooperative kernel separated by a bounded grid barrier.
+//
+// Directed round-trip distances (section 6.1) are the sum of a chunk solved
+// on G and the same chunk solved on the reversed graph; the reductions take
+// either one distance matrix or the pair.
+#include <cstdint>
+
+#include "cc_internal.h"
+#include "sssp.h"
+
+namespace ccg {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded grid barrier (same scheme as the traversal kernel's).
+__device__ bool grid_sync2(Ctl *ctl, unsigned nblocks, uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = &ctl->bar_gen;
+        volatile int *verr = &ctl->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const uint64_t t0 = gtimer();
+            unsigned ns = 8;
+            while (*vgen == g) {
+                if (*verr < 0) { ok = 0; break; }
+                if (gtimer() - t0 > timeout_ns) {
+                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        __threadfence();
+        if (*verr < 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gthreads = (int64_t)gridDim.x * kBlock;
+    const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+    const int64_t n = J.n;
+    Ctl *ctl = J.ctl;
+    const unsigned nb = gridDim.x;
+    unsigned long long relax = 0;
+
+    for (int64_t i = gtid; i < n * kChunkSrc; i += gthreads) J.dist[i] = kInf;
+    for (int64_t v = gtid; v < n; v += gthreads) J.mask[v] = 0u;
+    if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+    if (gtid < J.kc) {
+        const int v = J.sources[gtid];
+        J.dist[(int64_t)v * kChunkSrc + gtid] = 0u;
+        if (atomicOr(&J.mask[v], 1u << gtid) == 0u) {
+            const unsigned p = atomicAdd(&ctl->lev[0].qlen, 1u);
+            J.Q0[p] = v;
+        }
+    }
+    if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+
+    int r = 0;
+    for (;; ++r) {
+        const unsigned qn = ((volatile LevelCtl *)&ctl->lev[r & 3])->qlen;
+        if (qn == 0) break;
+        if (gtid == 0) ((LevelCtl *)&ctl->lev[(r + 2) & 3])->qlen = 0;
+        const int32_t *Qin = (r & 1) ? J.Q1 : J.Q0;
+        int32_t *Qout = (r & 1) ? J.Q0 : J.Q1;
+        unsigned *qout_len = &ctl->lev[(r + 1) & 3].qlen;
+        for (int64_t t = gwarp; t < (int64_t)qn; t += nwarps) {
+            const int u = Qin[t];
+            unsigned m = 0;
+            if (lane == 0) m = atomicExch(&J.mask[u], 0u);
+            m = __shfl_sync(FULL, m, 0);
+            const bool active = (m >> lane) & 1u;
+            const uint64_t du = active ? J.dist[(int64_t)u * kChunkSrc + lane] : 0ull;
+            const int64_t b = J.rp[u], e = J.rp[u + 1];
+            for (int64_t x = b; x < e; ++x) {
+                const int v = __ldg(J.col + x);
+                const uint64_t wt = J.w ? (uint64_t)__ldg(J.w + x) : 1ull;
+                bool imp = false;
+                if (active) {
+                    const uint64_t nd = du + wt;
+                    relax += 1;
+                    if (nd >= (uint64_t)kInf) {
+                        atomicCAS(&ctl->err, 0, CC_ERR_TOO_LARGE);
+                    } else {
+                        unsigned *slot = &J.dist[(int64_t)v * kChunkSrc + lane];
+                        if ((unsigned)nd < *slot) imp = (unsigned)nd < atomicMin(slot, (unsigned)nd);
+                    }
+                }
+                const unsigned bits = __ballot_sync(FULL, imp);
+                if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u) {
+                    const unsigned p = atomicAdd(qout_len, 1u);
+                    Qout[p] = v;
+                }
+            }
+        }
+        if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+    }
+    __shared__ unsigned long long s_rel[kBlock / 32];
+    for (int o = 16; o >= 1; o >>= 1) relax += __shfl_xor_sync(FULL, relax, o);
+    if (lane == 0) s_rel[threadIdx.x >> 5] = relax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kBlock / 32; ++i) t += s_rel[i];
+        atomicAdd(&ctl->words, t);
+    }
+    if (gtid == 0) ctl->levels = r;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+// Distance of the lane's source to v in this chunk (round trip when a
+// reverse matrix is given); kInf when unreachable or not a source lane.
+__device__ __forceinline__ uint64_t chunk_dist(const ReduceJob &R, int64_t v, int lane)
+{
+    if (lane >= R.kc) return (uint64_t)kInf;
+    const uint64_t a = R.distF[v * kChunkSrc + lane];
+    if (!R.distR) return a;
+    const uint64_t b = R.distR[v * kChunkSrc + lane];
+    if (a == kInf || b == kInf) return (uint64_t)kInf;
+    return a + b;
+}
+
+// Pass-1 reduction of one chunk: sums, running (distance, index) minimum
+// for the pivot, distances between sampled nodes, exact S of the chunk's
+// sources and the largest distance.
+__global__ void k_reduce1(ReduceJob R)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int gi = R.base + lane;
+    unsigned long long Sl = 0, dmax = 0;
+    int bad = 0;
+    for (int64_t v = gwarp; v < R.n; v += nwarps) {
+        const uint64_t d = chunk_dist(R, v, lane);
+        const bool valid = lane < R.kc;
+        if (valid && d >= (uint64_t)kInf) bad = 1;
+        const uint64_t dd = valid && d < kInf ? d : 0;
+        Sl += dd;
+        dmax = dd > dmax ? dd : dmax;
+        const unsigned long long s = warp_sum(dd), s2 = warp_sum(dd * dd);
+        unsigned long long key = valid ? ((d << 32) | (uint64_t)gi) : ~0ull;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(FULL, key, o);
+            key = y < key ? y : key;
+        }
+        if (lane == 0) {
+            R.sum2[2 * v] += s;
+            R.sum2[2 * v + 1] += s2;
+            if (!R.sum_only && key < R.best[v]) R.best[v] = key;
+        }
+        if (R.sum_only) continue;
+        const int j = R.sidx[v];
+        if (j >= 0 && valid) R.dcc[(int64_t)gi * R.k + j] = (uint32_t)dd;
+    }
+    if (lane < R.kc && !R.sum_only) {
+        atomicAdd(&R.S_samp[gi], Sl);
+        atomicMax(R.dmax, dmax);
+    }
+    if (bad) atomicExch(R.err, CC_ERR_DISCONNECTED);
+}
+
+// Pass-2 reduction of one chunk for the hybrid estimator: per-source
+// distance histogram over V \ C and the sums over the sources in L(v).
+__global__ void k_reduce2(ReduceJob R)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int gi = R.base + lane;
+    for (int64_t v = gwarp; v < R.n; v += nwarps) {
+        if (R.sidx[v] >= 0) continue;
+        const bool valid = lane < R.kc;
+        const uint64_t d = valid ? chunk_dist(R, v, lane) : 0;
+        if (valid) atomicAdd(&R.hist[(int64_t)d * R.k + gi], 1u);
+        bool inL = false;
+        if (valid) {
+            const uint64_t m = R.Lmask[v * R.W + (gi >> 6)];
+            inL = (m >> (gi & 63)) & 1ull;
+        }
+        const unsigned long long s = warp_sum(inL ? d : 0), s2 = warp_sum(inL ? d * d : 0);
+        if (lane == 0 && s) {
+            R.lc2[2 * v] += s;
+            R.lc2[2 * v + 1] += s2;
+        }
+    }
+}
+
+// best[v] = (Delta << 32 | pivot index)  ->  pivot[v], delta[v]
+__global__ void k_unpack_pivot(int64_t n, const unsigned long long *best, int32_t *pivot,
+                               uint32_t *delta)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        pivot[v] = (int32_t)(best[v] & 0xFFFFFFFFull);
+        delta[v] = (uint32_t)(best[v] >> 32);
+    }
+}
+
+int grid_of(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int launch_mssp(const SsspJob &job, cudaStream_t st)
+{
+    static int blocks_per_sm = -1, sms = 0;
+    if (blocks_per_sm < 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return CC_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return CC_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, mssp_kernel, kBlock,
+                                                          0) != cudaSuccess ||
+            blocks_per_sm < 1)
+            return CC_ERR_CUDA;
+    }
+    SsspJob j = job;
+    void *args[] = {&j};
+    return cudaLaunchCooperativeKernel((const void *)mssp_kernel, dim3(blocks_per_sm * sms),
+                                       dim3(kBlock), args, 0, st) == cudaSuccess
+               ? CC_OK
+               : CC_ERR_CUDA;
+}
+
+void run_reduce1(const ReduceJob &r, cudaStream_t st)
+{
+    k_reduce1<<<grid_of(r.n * 32), 256, 0, st>>>(r);
+}
+
+void run_reduce2(const ReduceJob &r, cudaStream_t st)
+{
+    k_reduce2<<<grid_of(r.n * 32), 256, 0, st>>>(r);
+}
+
+void run_unpack_pivot(int64_t n, const unsigned long long *best, int32_t *pivot,
+                      uint32_t *delta, cudaStream_t st)
+{
+    k_unpack_pivot<<<grid_of(n), 256, 0, st>>>(n, best, pivot, delta);
+}
+
+}  // namespace ccg

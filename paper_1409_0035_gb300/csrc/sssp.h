@@ -1,0 +1,50 @@
+// Multi-source shortest paths in 32-source chunks (sssp.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "cc_internal.h"
+
+namespace ccg {
+
+constexpr int kChunkSrc = 32;  // sources per chunk: one 128-byte row per node
+
+struct SsspJob {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *col;
+    const uint32_t *w;      // arc lengths (NULL: unit lengths)
+    int kc;                 // sources in this chunk (<= 32)
+    const int32_t *sources; // kc node ids
+    uint32_t *dist;         // n x 32
+    unsigned *mask;         // n
+    int32_t *Q0, *Q1;       // n each
+    Ctl *ctl;
+    uint64_t timeout_ns;
+};
+
+struct ReduceJob {
+    int64_t n;
+    int k, kc, base, W;
+    int sum_only;                   // exact mode: only sum2 and the reachability check
+    const uint32_t *distF, *distR;  // n x 32 each (distR NULL unless round trip)
+    const int32_t *sidx;
+    uint64_t *sum2;                 // n x 2
+    unsigned long long *best;       // n: (distance << 32 | sample index) minimum
+    uint32_t *dcc;                  // k x k
+    unsigned long long *S_samp;     // k
+    unsigned long long *dmax;       // 1
+    int *err;                       // 1
+    uint32_t *hist;                 // (D+1) x k
+    const uint64_t *Lmask;          // n x W
+    uint64_t *lc2;                  // n x 2
+};
+
+int launch_mssp(const SsspJob &job, cudaStream_t st);
+void run_reduce1(const ReduceJob &r, cudaStream_t st);
+void run_reduce2(const ReduceJob &r, cudaStream_t st);
+void run_unpack_pivot(int64_t n, const unsigned long long *best, int32_t *pivot,
+                      uint32_t *delta, cudaStream_t st);
+
+}  // namespace ccg

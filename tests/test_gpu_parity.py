@@ -210,3 +210,96 @@ def test_repeatable(cc):
                 assert (a[key] == b[key]).all(), key
     finally:
         cc.cc_graph_free(g)
+
+
+def check_chunked(cc, g, og, C, eps, roundtrip=False, hybrid=True):
+    o = cc.cc_opts_default(len(C))
+    o.eps_num, o.eps_den, o.want_hybrid, o.roundtrip = eps[0], eps[1], int(hybrid), int(roundtrip)
+    r = cc.cc_estimate(g, C, o)
+    want = orc.estimate(og, C, eps=eps, roundtrip=roundtrip)
+    for key in ("pivot", "delta", "sum", "S_samp", "delta_cc"):
+        assert (r[key] == want[key]).all(), key
+    for e in range(4 if hybrid else 3):
+        assert_close(r["s_hat"][e], want["s_hat"][e], f"s_hat[{e}]")
+        assert_close(r["closeness"][e], want["closeness"][e], f"closeness[{e}]")
+    if hybrid:
+        assert (r["hyb"] == want["hyb"]).all()
+
+
+WEIGHTED = {
+    "ws_w": lambda: (*synth.watts_strogatz_edges(600, 6, 0.1, seed=5),
+                     synth.random_weights(1800, 1, 40, seed=6)),
+    "rmat_w": lambda: (*synth.rmat_edges(9, 6, seed=7),
+                       synth.random_weights(6 * 512, 1, 1000, seed=8)),
+    "grid_w": lambda: (*synth.grid_edges(30, 20),
+                       synth.random_weights(29 * 20 + 30 * 19, 1, 3, seed=9)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WEIGHTED))
+@pytest.mark.parametrize("k", [1, 31, 32, 33, 64, 100])
+def test_weighted_estimate_parity(cc, name, k):
+    n, s, d, w = WEIGHTED[name]()
+    g, old, og = both(cc, n, s, d, w)
+    try:
+        k = min(k, og.n)
+        C = orc.choose_sample(og.n, k, 5 + k)
+        for eps in [(1, 1), (1, 4), orc.default_eps(k)]:
+            check_chunked(cc, g, og, C, eps)
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_rgg_road_like_weights(cc):
+    n, s, d, length = synth.rgg_edges(4000, 0.03, seed=3)
+    w = synth.edge_lengths_to_weights(length, 1000.0)
+    g, old, og = both(cc, n, s, d, w)
+    try:
+        C = orc.choose_sample(og.n, 64, 2)
+        check_chunked(cc, g, og, C, (1, 8))
+        c, S = cc.cc_exact(g)
+        assert (S == orc.exact_S(og)).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+DIRECTED = {
+    "rmat_d": lambda: (*synth.rmat_edges(9, 8, seed=11), None),
+    "rmat_dw": lambda: (*synth.rmat_edges(8, 8, seed=12),
+                        synth.random_weights(8 * 256, 1, 9, seed=13)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(DIRECTED))
+@pytest.mark.parametrize("k", [1, 32, 50])
+def test_roundtrip_estimate_parity(cc, name, k):
+    n, s, d, w = DIRECTED[name]()
+    g, old, og = both(cc, n, s, d, w, directed=True)
+    try:
+        k = min(k, og.n)
+        C = orc.choose_sample(og.n, k, 3 + k)
+        for eps in [(1, 1), (1, 3)]:
+            check_chunked(cc, g, og, C, eps, roundtrip=True)
+        with pytest.raises(cc.CCError):  # directed graphs need round trips
+            cc.cc_estimate(g, C)
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_exact_weighted_and_roundtrip(cc):
+    n, s, d, w = WEIGHTED["ws_w"]()
+    g, old, og = both(cc, n, s, d, w)
+    try:
+        c, S = cc.cc_exact(g)
+        want = orc.exact_S(og)
+        assert (S == want).all()
+        assert_close(c, orc.exact_closeness(want), "exact weighted closeness")
+    finally:
+        cc.cc_graph_free(g)
+    n, s, d, w = DIRECTED["rmat_d"]()
+    g, old, og = both(cc, n, s, d, w, directed=True)
+    try:
+        c, S = cc.cc_exact(g)
+        assert (S == orc.exact_S(og, roundtrip=True)).all()
+    finally:
+        cc.cc_graph_free(g)
