@@ -224,6 +224,13 @@ int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
                                int32_t *d_pivot, uint32_t *d_delta,
                                uint64_t *d_S_sampled, void *stream);
 
+/* ---- tuning ---------------------------------------------------------------- */
+/* Direction switch of the breadth-first traversal of one graph (0 restores
+ * the default 14): a level runs top-down while (CSR entries of the
+ * frontier) * alpha < (CSR entries of the nodes some source has not reached
+ * yet), bottom-up otherwise.  Results do not depend on it, only the time. */
+int cc_set_tuning(cc_graph_t g, int32_t alpha);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Counters of the last traversal pass run on g: levels, top-down and
  * bottom-up levels, CSR entries examined and frontier words gathered.

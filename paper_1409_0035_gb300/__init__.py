@@ -34,6 +34,7 @@ EXPORTS = (
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
+    "cc_set_tuning",
     "cc_selftest_barrier_timeout", "cc_strerror",
 )
 
@@ -85,6 +86,7 @@ def lib():
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
         L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
+        L.cc_set_tuning.argtypes = [P, i32]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
@@ -231,6 +233,10 @@ def cc_last_pass_stats(g):
          "cc_last_pass_stats")
     return dict(zip(("levels", "td_levels", "bu_levels", "edges", "words"),
                     [v.value for v in vals]))
+
+
+def cc_set_tuning(g, alpha=0):
+    _chk(lib().cc_set_tuning(g, int(alpha)), "cc_set_tuning")
 
 
 def cc_last_pass_trace(g, max_levels=64):

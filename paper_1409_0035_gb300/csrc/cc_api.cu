@@ -64,8 +64,9 @@ struct cc_graph {
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
-        distF, distR, mask, best, dmax, errflag, fbm;
+        distF, distR, mask, best, dmax, errflag;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
+    int alpha = kAlpha;  // traversal tuning
     int hist_cap = 0;
     Ctl last{};
     // Traversal launches of the last API call: count, device time (CUDA
@@ -153,7 +154,6 @@ int ensure_state(cc_graph *g, int W)
     RC(g->sidx.ensure(n * 4));
     RC(g->sum2.ensure(n * 16));
     RC(g->ctl.ensure(sizeof(Ctl)));
-    RC(g->fbm.ensure((size_t)3 * ((n + 31) / 32) * 4));
     return CC_OK;
 }
 
@@ -178,7 +178,6 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
     j.F0 = g->F0.as<uint64_t>();
     j.F1 = g->F1.as<uint64_t>();
     j.nxt = g->nxt.as<uint64_t>();
-    j.fbm = g->fbm.as<unsigned>();
     j.Q0 = g->Q0.as<int32_t>();
     j.Q1 = g->Q1.as<int32_t>();
     j.T = g->T.as<int32_t>();
@@ -187,7 +186,7 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
     j.sum2 = g->sum2.as<uint64_t>();
     j.ctl = g->ctl.as<Ctl>();
     j.timeout_ns = kTimeoutNs;
-    j.alpha = kAlpha;
+    j.alpha = g->alpha;
     (void)W;
     return j;
 }
@@ -269,7 +268,7 @@ void free_graph(cc_graph *g)
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag, &g->fbm};
+                     &g->dmax, &g->errflag};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -682,6 +681,13 @@ int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td, int64_t *bu,
     if (bu) *bu = (int64_t)g->last.bu_levels;
     if (edges) *edges = (int64_t)g->last.edges;
     if (words) *words = (int64_t)g->last.words;
+    return CC_OK;
+}
+
+int cc_set_tuning(cc_graph_t g, int32_t alpha)
+{
+    if (!g || alpha < 0) return CC_ERR_ARG;
+    g->alpha = alpha ? alpha : kAlpha;
     return CC_OK;
 }
 

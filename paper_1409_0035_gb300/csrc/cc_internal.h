@@ -70,7 +70,6 @@ struct BfsJob {
     const int64_t *Hch_begin;
     int64_t nHch;
     uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
-    unsigned *fbm;                  // 3 x ceil(n/32): frontier-presence bitmaps
     int32_t *Q0, *Q1, *T;           // n each
     unsigned int *tflag;            // n
     uint32_t red;

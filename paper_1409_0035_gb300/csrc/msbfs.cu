@@ -34,9 +34,6 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int kUnroll = 4;  // independent gathers in flight per lane and step
-// Bottom-up consults the frontier bitmap when fewer than n / kSparseFrontier
-// nodes are in the previous frontier.
-constexpr int kSparseFrontier = 8;
 
 __device__ __forceinline__ uint64_t gtimer()
 {
@@ -132,7 +129,7 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
                                             int64_t deg, uint64_t *Fout,
                                             int32_t *Qout, LevelCtl *C,
                                             LaneAcc<W> &A, unsigned *s_hist,
-                                            bool clear_tflag, unsigned *bmout)
+                                            bool clear_tflag)
 {
     const int lane = threadIdx.x & 31;
     const int w = lane & (W - 1);
@@ -219,10 +216,7 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         base = __shfl_sync(FULL, base, first);
         if (fr) Qout[base + __popc(bal & ((1u << lane) - 1u))] = v;
     }
-    if (fr) {
-        A.ef += (unsigned long long)deg;
-        atomicOr(&bmout[v >> 5], 1u << (v & 31));
-    }
+    if (fr) A.ef += (unsigned long long)deg;
     if (leader && done_after && !done_before) {
         A.eu_dec += (unsigned long long)deg;
         A.ninc_dec += 1;
@@ -250,24 +244,16 @@ __device__ __forceinline__ uint64_t or_same_word(uint64_t x)
 // OR of the frontier words (slot w) of up to U CSR entries x, x+stride, ...
 // below e.  The U column loads and the U gathers are independent, so they
 // are all in flight together.
-// On sparse levels `bm` (one bit per node: in the previous frontier) is
-// consulted first and only flagged neighbours are gathered.
 template <int W, int U>
 __device__ __forceinline__ uint64_t gather_or(const int32_t *__restrict__ col,
-                                              const uint64_t *Fin, const unsigned *bm,
-                                              int64_t x, int64_t e, int stride, int w,
-                                              unsigned long long &words)
+                                              const uint64_t *Fin, int64_t x, int64_t e,
+                                              int stride, int w, unsigned long long &words)
 {
     int c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t ee = x + (int64_t)u * stride;
         c[u] = ee < e ? __ldg(col + ee) : -1;
-    }
-    if (bm) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (c[u] >= 0 && !((bm[c[u] >> 5] >> (c[u] & 31)) & 1u)) c[u] = -1;
     }
     uint64_t f = 0;
 #pragma unroll
@@ -412,8 +398,6 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         J.nxt[i] = 0;
     }
     for (int64_t v = gtid; v < n; v += gthreads) J.tflag[v] = 0;
-    const int64_t nbm = (n + 31) >> 5;
-    for (int64_t i = gtid; i < 3 * nbm; i += gthreads) J.fbm[i] = 0u;
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
     if (!grid_sync(ctl, nb, J.timeout_ns)) return;
     for (int64_t i = gtid; i < J.k; i += gthreads) {
@@ -423,7 +407,6 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         atomicOr((unsigned long long *)&J.vis[vw], bit);
         atomicOr((unsigned long long *)&J.F0[vw], bit);
         J.Q0[i] = v;
-        atomicOr(&J.fbm[v >> 5], 1u << (v & 31));
         if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
         if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
         const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
@@ -458,13 +441,6 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
             ctl->lvl_front[l] = qprev;
             ctl->lvl_ef[l] = ef;
         }
-        // Frontier-presence bitmaps rotate over three buffers: read the
-        // previous level's, write this level's, clear the one for the next.
-        const unsigned *bmprev = J.fbm + ((l + 2) % 3) * nbm;
-        unsigned *bmout = J.fbm + (l % 3) * nbm;
-        unsigned *bmnext = J.fbm + ((l + 1) % 3) * nbm;
-        for (int64_t i = gtid; i < nbm; i += gthreads) bmnext[i] = 0u;
-        const unsigned *bmin = (int64_t)qprev * kSparseFrontier < n ? bmprev : nullptr;
         const unsigned long long words_before = A.words;
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
@@ -516,7 +492,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                     deg = rp[v + 1] - rp[v];
                 }
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
-                               A, s_hist, true, bmout);
+                               A, s_hist, true);
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
@@ -535,13 +511,13 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 uint64_t acc = 0;
                 if (vis != ~0ull) {
                     for (int64_t x = b; x < e; x += kUnroll) {
-                        acc |= gather_or<W, kUnroll>(col, Fin, bmin, x, e, 1, w, A.words);
+                        acc |= gather_or<W, kUnroll>(col, Fin, x, e, 1, w, A.words);
                         if ((acc | vis) == ~0ull) break;
                     }
                 }
                 __syncwarp();
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, Qout, C,
-                               A, s_hist, false, bmout);
+                               A, s_hist, false);
             }
             // A2: medium nodes, one warp per node.
             for (int64_t t = gwarp; t < J.nM; t += nwarps) {
@@ -551,15 +527,15 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 uint64_t acc = 0;
                 if (!__all_sync(FULL, visw == ~0ull)) {
                     for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                        acc |= gather_or<W, kUnroll>(col, Fin, bmin, base + grp, e, NPW,
-                                                     w, A.words);
+                        acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w,
+                                                     A.words);
                         const uint64_t r = or_same_word<W>(acc);
                         if (__all_sync(FULL, (r | visw) == ~0ull)) break;
                     }
                 }
                 const uint64_t r = or_same_word<W>(acc);
                 tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, Qout,
-                               C, A, s_hist, false, bmout);
+                               C, A, s_hist, false);
             }
             // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
             for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
@@ -572,7 +548,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
                 uint64_t acc = 0;
                 for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(col, Fin, bmin, base + grp, e, NPW, w, A.words);
+                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
                     const uint64_t r = or_same_word<W>(acc);
                     if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
                 }
@@ -597,7 +573,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                     deg = rp[v + 1] - rp[v];
                 }
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
-                               A, s_hist, false, bmout);
+                               A, s_hist, false);
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);

@@ -142,7 +142,6 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
         c.take<int32_t>((size_t)k);
         c.take<Ctl>(1);
         c.take<int>(1);
-        c.take<unsigned>((size_t)3 * ((n + 31) / 32));
         if (c.off > kNoAllocScratchBytes) return CC_ERR_TOO_LARGE;
     }
     unsigned char *base = nullptr;
@@ -167,7 +166,6 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     int32_t *src = c.take<int32_t>((size_t)k);
     Ctl *ctl = c.take<Ctl>(1);
     int *err = c.take<int>(1);
-    unsigned *fbm = c.take<unsigned>((size_t)3 * ((n + 31) / 32));
 
 #define NA_CK(x)                                     \
     do {                                             \
@@ -212,7 +210,6 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     j.nL = n;
     j.vis = vis; j.F0 = F0; j.F1 = F1; j.nxt = nxt;
     j.Q0 = Q0; j.Q1 = Q1; j.T = T; j.tflag = tflag;
-    j.fbm = fbm;
     j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
     j.sum2 = sum2;
     j.pivot = d_pivot;

@@ -110,7 +110,11 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
             if (lane == 0) m = atomicExch(&J.mask[u], 0u);
             m = __shfl_sync(FULL, m, 0);
             const bool active = (m >> lane) & 1u;
-            const uint64_t du = active ? J.dist[(int64_t)u * kChunkSrc + lane] : 0ull;
+            // The row may have been lowered by an atomicMin of another SM in
+            // this round (that is what set the mask bit): read it from L2,
+            // the point where those atomics are performed, not from a
+            // possibly stale L1 line.
+            const uint64_t du = active ? __ldcg(J.dist + (int64_t)u * kChunkSrc + lane) : 0ull;
             const int64_t b = J.rp[u], e = J.rp[u + 1];
             for (int64_t x = b; x < e; ++x) {
                 const int v = __ldg(J.col + x);
