@@ -64,7 +64,7 @@ struct cc_graph {
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
-        distF, distR, mask, best, dmax, errflag;
+        distF, distR, mask, best, dmax, errflag, AL0, AL1;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = kAlpha;  // traversal tuning
     int hist_cap = 0;
@@ -150,6 +150,8 @@ int ensure_state(cc_graph *g, int W)
     RC(g->Q0.ensure(n * 4));
     RC(g->Q1.ensure(n * 4));
     RC(g->T.ensure(n * 4));
+    RC(g->AL0.ensure(n * 4));
+    RC(g->AL1.ensure(n * 4));
     RC(g->tflag.ensure(n * 4));
     RC(g->sidx.ensure(n * 4));
     RC(g->sum2.ensure(n * 16));
@@ -181,6 +183,8 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
     j.Q0 = g->Q0.as<int32_t>();
     j.Q1 = g->Q1.as<int32_t>();
     j.T = g->T.as<int32_t>();
+    j.AL0 = g->AL0.as<int32_t>();
+    j.AL1 = g->AL1.as<int32_t>();
     j.tflag = g->tflag.as<unsigned>();
     j.sidx = g->sidx.as<int32_t>();
     j.sum2 = g->sum2.as<uint64_t>();
@@ -268,7 +272,7 @@ void free_graph(cc_graph *g)
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag};
+                     &g->dmax, &g->errflag, &g->AL0, &g->AL1};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);

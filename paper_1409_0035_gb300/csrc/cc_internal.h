@@ -31,7 +31,7 @@ struct LevelCtl {
     unsigned int qlen;          // nodes with new bits this level (queue length)
     unsigned int tlen;          // touched nodes (top-down)
     unsigned int ninc_dec;      // nodes that became complete this level
-    unsigned int pad_;
+    unsigned int alen;          // light nodes still incomplete (bottom-up)
     unsigned long long ef;      // sum of degrees of the frontier nodes
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
@@ -71,6 +71,7 @@ struct BfsJob {
     int64_t nHch;
     uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
     int32_t *Q0, *Q1, *T;           // n each
+    int32_t *AL0, *AL1;             // n each: active light-node lists
     unsigned int *tflag;            // n
     uint32_t red;
     uint64_t *sum2;      // n x 2: {sum, sumsq}

@@ -134,9 +134,14 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
     const int lane = threadIdx.x & 31;
     const int w = lane & (W - 1);
     const int64_t vw = (int64_t)v * W + w;
-    if (valid) {
+    // Frontier and visited words are written only when new bits arrive.  A
+    // frontier word left unwritten keeps bits of an older level of the same
+    // parity; each such source reached every neighbour one level after this
+    // node, so those bits are already in the neighbours' visited words and
+    // are masked off wherever the word is read.
+    if (valid && nw) {
         Fout[vw] = nw;
-        if (nw) J.vis[vw] = vis | nw;
+        J.vis[vw] = vis | nw;
     }
     int sx = -1;
     if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC))) sx = J.sidx[v];
@@ -421,6 +426,10 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
 
     long long eu = J.arcs, ninc = n;
     int last = 0;
+    // Active light-node list: Llist until the first bottom-up level, then
+    // alternately AL0 / AL1 (al_par 0 / 1).
+    int64_t al_len = J.nL;
+    int al_par = -1;
     int l = 1;
     for (;; ++l) {
         volatile LevelCtl *P = &ctl->lev[(l - 1) & 3];
@@ -445,6 +454,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
             Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
+            Z->alen = 0;
         }
         uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
         uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
@@ -453,13 +463,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         LevelCtl *C = &ctl->lev[l & 3];
 
         if (td) {
-            // P1a: clear the stale frontier of level l-2 held in Fout.
-            if (l >= 2) {
-                const unsigned q2 = ((volatile LevelCtl *)&ctl->lev[(l - 2) & 3])->qlen;
-                for (int64_t i = gtid; i < (int64_t)q2 * W; i += gthreads)
-                    Fout[(int64_t)Qout[i / W] * W + (i & (W - 1))] = 0;
-            }
-            // P1b: push the frontier words of the queued nodes; when the
+            // P1: push the frontier words of the queued nodes; when the
             // graph has chunk tasks, a heavy node's list is pushed by them.
             for (int64_t t = gwarp; t < (int64_t)qprev; t += nwarps) {
                 const int u = Qin[t];
@@ -499,11 +503,15 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->td_levels += 1;
         } else {
-            // A1: light nodes, one thread per (node, word).
-            for (int64_t t = gwarp; t * NPW < J.nL; t += nwarps) {
+            // A1: light nodes still missing some source, one thread per
+            // (node, word); those still incomplete afterwards form the next
+            // bottom-up level's list.
+            const int32_t *ALin = al_par < 0 ? J.Llist : (al_par ? J.AL1 : J.AL0);
+            int32_t *ALout = al_par == 0 ? J.AL1 : J.AL0;
+            for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
                 const int64_t li = t * NPW + grp;
-                const bool valid = li < J.nL;
-                const int v = valid ? J.Llist[li] : 0;
+                const bool valid = li < al_len;
+                const int v = valid ? ALin[li] : 0;
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = valid ? J.vis[vw] : ~0ull;
                 int64_t b = 0, e = 0;
@@ -518,6 +526,18 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 __syncwarp();
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, Qout, C,
                                A, s_hist, false);
+                int inc = valid && ((vis | acc) != ~0ull);
+#pragma unroll
+                for (int o = 1; o < W; o <<= 1) inc |= __shfl_xor_sync(FULL, inc, o);
+                const bool keep = inc && w == 0;
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (bal) {
+                    const int first = __ffs(bal) - 1;
+                    unsigned base = 0;
+                    if (lane == first) base = atomicAdd(&C->alen, (unsigned)__popc(bal));
+                    base = __shfl_sync(FULL, base, first);
+                    if (keep) ALout[base + __popc(bal & ((1u << lane) - 1u))] = v;
+                }
             }
             // A2: medium nodes, one warp per node.
             for (int64_t t = gwarp; t < J.nM; t += nwarps) {
@@ -525,7 +545,8 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
                 const int64_t b = rp[v], e = rp[v + 1];
                 uint64_t acc = 0;
-                if (!__all_sync(FULL, visw == ~0ull)) {
+                if (__all_sync(FULL, visw == ~0ull)) continue;
+                {
                     for (int64_t base = b; base < e; base += NPW * kUnroll) {
                         acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w,
                                                      A.words);
@@ -579,6 +600,8 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
             flush_level<W>(J, l, C, A, s_hist, doHist);
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->bu_levels += 1;
+            al_len = ((volatile LevelCtl *)C)->alen;
+            al_par = al_par == 0 ? 1 : 0;
         }
     }
     // Pass statistics.
