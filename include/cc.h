@@ -209,7 +209,7 @@ int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k,
  *   stream       cudaStream_t or NULL
  * Allocates nothing: all working memory lives in one fixed 32 MiB device
  * array inside the library, present on every GPU that loads the library until
- * the process exits.  Calls that need more -- about 4*n*W*8 + 48*n + 4*k*k +
+ * the process exits.  Calls that need more -- about 4*n*W*8 + 52*n + 4*k*k +
  * 8192*k bytes with W = ceil(k/64) rounded up to a power of two, or more than
  * 2047 BFS levels -- return CC_ERR_TOO_LARGE before touching the device.
  * The first call on a device looks up that array's device address (once per

@@ -64,7 +64,7 @@ struct cc_graph {
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
-        distF, distR, mask, best, dmax, errflag, AL0, AL1;
+        distF, distR, mask, best, dmax, errflag, AL0, AL1, fstamp;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = kAlpha;  // traversal tuning
     int hist_cap = 0;
@@ -152,6 +152,7 @@ int ensure_state(cc_graph *g, int W)
     RC(g->T.ensure(n * 4));
     RC(g->AL0.ensure(n * 4));
     RC(g->AL1.ensure(n * 4));
+    RC(g->fstamp.ensure(n * 4));
     RC(g->tflag.ensure(n * 4));
     RC(g->sidx.ensure(n * 4));
     RC(g->sum2.ensure(n * 16));
@@ -185,6 +186,7 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
     j.T = g->T.as<int32_t>();
     j.AL0 = g->AL0.as<int32_t>();
     j.AL1 = g->AL1.as<int32_t>();
+    j.fstamp = g->fstamp.as<uint32_t>();
     j.tflag = g->tflag.as<unsigned>();
     j.sidx = g->sidx.as<int32_t>();
     j.sum2 = g->sum2.as<uint64_t>();
@@ -272,7 +274,7 @@ void free_graph(cc_graph *g)
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag, &g->AL0, &g->AL1};
+                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->fstamp};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);

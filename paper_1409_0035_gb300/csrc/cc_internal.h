@@ -31,7 +31,9 @@ struct LevelCtl {
     unsigned int qlen;          // nodes with new bits this level (queue length)
     unsigned int tlen;          // touched nodes (top-down)
     unsigned int ninc_dec;      // nodes that became complete this level
-    unsigned int alen;          // light nodes still incomplete (bottom-up)
+    unsigned int alen;          // rebuilt light list length (bottom-up)
+    unsigned int qcnt;          // frontier queue built from the stamps (top-down)
+    unsigned int pad_[3];
     unsigned long long ef;      // sum of degrees of the frontier nodes
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
@@ -72,6 +74,7 @@ struct BfsJob {
     uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
     int32_t *Q0, *Q1, *T;           // n each
     int32_t *AL0, *AL1;             // n each: active light-node lists
+    uint32_t *fstamp;               // n: last level a node got new bits
     unsigned int *tflag;            // n
     uint32_t red;
     uint64_t *sum2;      // n x 2: {sum, sumsq}

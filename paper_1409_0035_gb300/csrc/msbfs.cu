@@ -117,7 +117,7 @@ struct LaneAcc {
     // s*64 + h*32 + lane.
     uint32_t hc[W <= 8 ? 2 * W : 1];
     unsigned long long ef, eu_dec, words;
-    unsigned int ninc_dec;
+    unsigned int ninc_dec, nfront;
 };
 
 // Update, reduce and enqueue one warp tile.  Lanes form groups of W; group
@@ -127,7 +127,6 @@ template <int W>
 __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
                                             int v, uint64_t vis, uint64_t nw,
                                             int64_t deg, uint64_t *Fout,
-                                            int32_t *Qout, LevelCtl *C,
                                             LaneAcc<W> &A, unsigned *s_hist,
                                             bool clear_tflag)
 {
@@ -211,17 +210,14 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
             }
         }
     }
-    // Enqueue frontier nodes (warp-aggregated) and count level statistics.
+    // Stamp frontier nodes with the level (a later top-down level builds its
+    // queue from the stamps) and count level statistics.
     const bool fr = leader && c > 0;
-    const unsigned bal = __ballot_sync(FULL, fr);
-    if (bal) {
-        const int first = __ffs(bal) - 1;
-        unsigned base = 0;
-        if (lane == first) base = atomicAdd(&C->qlen, (unsigned)__popc(bal));
-        base = __shfl_sync(FULL, base, first);
-        if (fr) Qout[base + __popc(bal & ((1u << lane) - 1u))] = v;
+    if (fr) {
+        J.fstamp[v] = (uint32_t)l;
+        A.ef += (unsigned long long)deg;
+        A.nfront += 1;
     }
-    if (fr) A.ef += (unsigned long long)deg;
     if (leader && done_after && !done_before) {
         A.eu_dec += (unsigned long long)deg;
         A.ninc_dec += 1;
@@ -291,19 +287,29 @@ template <int W>
 __device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
                             unsigned *s_hist, bool flush_hist)
 {
-    __shared__ unsigned long long s_red[kBlock / 32];
-    const unsigned long long ef = block_sum64(A.ef, s_red);
-    const unsigned long long eu = block_sum64(A.eu_dec, s_red);
-    const unsigned long long ni = block_sum64(A.ninc_dec, s_red);
-    if (threadIdx.x == 0) {
-        if (ef) atomicAdd(&C->ef, ef);
-        if (eu) atomicAdd(&C->eu_dec, eu);
-        if (ni) atomicAdd(&C->ninc_dec, (unsigned)ni);
+    __shared__ unsigned long long s_red[4][kBlock / 32];
+    unsigned long long x[4] = {A.ef, A.eu_dec, A.ninc_dec, A.nfront};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) x[q] += __shfl_xor_sync(FULL, x[q], o);
+        if (lane == 0) s_red[q][wid] = x[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kBlock / 32; ++i) t += s_red[threadIdx.x][i];
+        if (t) {
+            if (threadIdx.x == 0) atomicAdd(&C->ef, t);
+            if (threadIdx.x == 1) atomicAdd(&C->eu_dec, t);
+            if (threadIdx.x == 2) atomicAdd(&C->ninc_dec, (unsigned)t);
+            if (threadIdx.x == 3) atomicAdd(&C->qlen, (unsigned)t);
+        }
     }
     A.ef = A.eu_dec = 0;
-    A.ninc_dec = 0;
+    A.ninc_dec = A.nfront = 0;
     if (!flush_hist) return;
-    const int lane = threadIdx.x & 31;
     if constexpr (W <= 8) {
 #pragma unroll
         for (int s = 0; s < W; ++s)
@@ -324,6 +330,47 @@ __device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
     }
 }
 
+// Order-preserving stream compaction over [0, N) by all CTAs: each CTA
+// takes a contiguous slice, counts its keepers, reserves their slots with
+// one atomicAdd on *counter, then writes them in slice order.
+template <class Keep, class Get>
+__device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsigned *counter)
+{
+    __shared__ unsigned s_w[kBlock / 32];
+    __shared__ unsigned s_base;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(N, lo + per);
+    unsigned c = 0;
+    for (int64_t i = lo + tid; i < hi; i += kBlock) c += keep(i) ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if (lane == 0) s_w[wid] = c;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned t = 0;
+        for (int i = 0; i < kBlock / 32; ++i) t += s_w[i];
+        s_base = t ? atomicAdd(counter, t) : 0u;
+    }
+    __syncthreads();
+    unsigned base = s_base;
+    for (int64_t c0 = lo; c0 < hi; c0 += kBlock) {
+        const int64_t i = c0 + tid;
+        const bool k = i < hi && keep(i);
+        const unsigned bal = __ballot_sync(FULL, k);
+        if (lane == 0) s_w[wid] = __popc(bal);
+        __syncthreads();
+        unsigned off = 0, tot = 0;
+        for (int q = 0; q < kBlock / 32; ++q) {
+            if (q < wid) off += s_w[q];
+            tot += s_w[q];
+        }
+        if (k) out[base + off + __popc(bal & ((1u << lane) - 1u))] = get(i);
+        base += tot;
+        __syncthreads();
+    }
+}
+
 // Top-down push of one frontier node's words f (slot w per lane) to the
 // CSR entries [b, e): new bits are OR-ed into nxt and each node reached for
 // the first time this level is appended (once) to the touched list.  Called
@@ -332,7 +379,7 @@ __device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
 template <int W>
 __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restrict__ col,
                                         uint64_t f, int64_t b, int64_t e, LevelCtl *C,
-                                        LaneAcc<W> &A)
+                                        int32_t *Tout, LaneAcc<W> &A)
 {
     constexpr int NPW = 32 / W;
     const int lane = threadIdx.x & 31;
@@ -365,7 +412,7 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
                 unsigned pos = 0;
                 if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
                 pos = __shfl_sync(m, pos, first);
-                J.T[pos + __popc(m & ((1u << lane) - 1u))] = v;
+                Tout[pos + __popc(m & ((1u << lane) - 1u))] = v;
             }
         }
     }
@@ -393,7 +440,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
 #pragma unroll
     for (int i = 0; i < (W <= 8 ? 2 * W : 1); ++i) A.hc[i] = 0;
     A.ef = A.eu_dec = A.words = 0;
-    A.ninc_dec = 0;
+    A.ninc_dec = A.nfront = 0;
 
     // ---- level 0: clear the state, seed the sources -----------------------
     for (int64_t i = gtid; i < n * W; i += gthreads) {
@@ -402,7 +449,10 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         J.F1[i] = 0;
         J.nxt[i] = 0;
     }
-    for (int64_t v = gtid; v < n; v += gthreads) J.tflag[v] = 0;
+    for (int64_t v = gtid; v < n; v += gthreads) {
+        J.tflag[v] = 0;
+        J.fstamp[v] = kInf;
+    }
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
     if (!grid_sync(ctl, nb, J.timeout_ns)) return;
     for (int64_t i = gtid; i < J.k; i += gthreads) {
@@ -411,7 +461,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         const int64_t vw = (int64_t)v * W + (i >> 6);
         atomicOr((unsigned long long *)&J.vis[vw], bit);
         atomicOr((unsigned long long *)&J.F0[vw], bit);
-        J.Q0[i] = v;
+        J.fstamp[v] = 0u;
         if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
         if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
         const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
@@ -421,19 +471,29 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
             atomicAdd(&ctl->lev[0].ninc_dec, 1u);
         }
     }
-    if (gtid == 0) ctl->lev[0].qlen = (unsigned)J.k;
+    if (gtid == 0) {
+        ctl->lev[0].qlen = (unsigned)J.k;
+        ctl->lev[0].tlen = (unsigned)J.k;  // level 0 "touched" the sources
+    }
     if (!grid_sync(ctl, nb, J.timeout_ns)) return;
 
     long long eu = J.arcs, ninc = n;
     int last = 0;
-    // Active light-node list: Llist until the first bottom-up level, then
-    // alternately AL0 / AL1 (al_par 0 / 1).
+    // Active light-node list: Llist, later rebuilt (order-preserving) into
+    // AL0 / AL1 once the incomplete nodes fall below half of it.
+    const int32_t *ALcur = J.Llist;
     int64_t al_len = J.nL;
-    int al_par = -1;
+    int al_next = 0;
+    // Queue of a top-down level: the previous level's touched list when that
+    // level was top-down (level 0 "touched" the sources), else built from
+    // the frontier stamps.
+    bool prev_td = true;
+    const int32_t *prevT = J.sources;
     int l = 1;
     for (;; ++l) {
         volatile LevelCtl *P = &ctl->lev[(l - 1) & 3];
         const unsigned qprev = P->qlen;
+        const unsigned tprev = P->tlen;
         const unsigned long long ef = P->ef;
         eu -= (long long)P->eu_dec;
         ninc -= (long long)P->ninc_dec;
@@ -454,30 +514,41 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
             Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
-            Z->alen = 0;
+            Z->alen = 0; Z->qcnt = 0;
         }
         uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
         uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
-        const int32_t *Qin = (l & 1) ? J.Q0 : J.Q1;
-        int32_t *Qout = (l & 1) ? J.Q1 : J.Q0;
         LevelCtl *C = &ctl->lev[l & 3];
 
         if (td) {
+            const int32_t *Qin = prevT;
+            int64_t qn = tprev;
+            if (!prev_td) {
+                const unsigned want = (unsigned)(l - 1);
+                block_compact(
+                    n, [&](int64_t i) { return J.fstamp[i] == want; },
+                    [&](int64_t i) { return (int32_t)i; }, J.Q0, &C->qcnt);
+                if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+                Qin = J.Q0;
+                qn = ((volatile LevelCtl *)C)->qcnt;
+            }
+            int32_t *Tout = (Qin == J.T) ? J.Q1 : J.T;
             // P1: push the frontier words of the queued nodes; when the
             // graph has chunk tasks, a heavy node's list is pushed by them.
-            for (int64_t t = gwarp; t < (int64_t)qprev; t += nwarps) {
+            for (int64_t t = gwarp; t < qn; t += nwarps) {
                 const int u = Qin[t];
                 const int64_t b = rp[u], e = rp[u + 1];
                 if (J.nHch > 0 && e - b > kMediumMaxDeg) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
-                td_push<W>(J, col, f, b, e, C, A);
+                td_push<W>(J, col, f, b, e, C, Tout, A);
             }
             for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
                 const int u = J.Hch_node[t];
+                if (J.fstamp[u] != (unsigned)(l - 1)) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
                 if (__all_sync(FULL, f == 0ull)) continue;
                 const int64_t b = J.Hch_begin[t];
-                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, A);
+                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A);
             }
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             // P2: finalise the touched nodes.
@@ -485,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
             for (int64_t t = gwarp; t * NPW < tl; t += nwarps) {
                 const int64_t li = t * NPW + grp;
                 const bool valid = li < tl;
-                const int v = valid ? J.T[li] : 0;
+                const int v = valid ? Tout[li] : 0;
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = ~0ull, acc = 0;
                 int64_t deg = 0;
@@ -495,23 +566,39 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                     if (acc) J.nxt[vw] = 0;
                     deg = rp[v + 1] - rp[v];
                 }
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
-                               A, s_hist, true);
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, true);
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->td_levels += 1;
+            prev_td = true;
+            prevT = Tout;
         } else {
-            // A1: light nodes still missing some source, one thread per
-            // (node, word); those still incomplete afterwards form the next
-            // bottom-up level's list.
-            const int32_t *ALin = al_par < 0 ? J.Llist : (al_par ? J.AL1 : J.AL0);
-            int32_t *ALout = al_par == 0 ? J.AL1 : J.AL0;
+            // Rebuild the light list when fewer than half of it can still be
+            // incomplete (ninc bounds the incomplete light nodes).
+            if (2 * ninc < al_len) {
+                int32_t *ALout = al_next ? J.AL1 : J.AL0;
+                const int32_t *ALin = ALcur;
+                block_compact(
+                    al_len,
+                    [&](int64_t i) {
+                        const int64_t v = ALin[i];
+                        bool inc = false;
+                        for (int q = 0; q < W; ++q) inc |= J.vis[v * W + q] != ~0ull;
+                        return inc;
+                    },
+                    [&](int64_t i) { return ALin[i]; }, ALout, &C->alen);
+                if (!grid_sync(ctl, nb, J.timeout_ns)) return;
+                ALcur = ALout;
+                al_len = ((volatile LevelCtl *)C)->alen;
+                al_next ^= 1;
+            }
+            // A1: light nodes of the active list, one thread per (node, word).
             for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
                 const int64_t li = t * NPW + grp;
                 const bool valid = li < al_len;
-                const int v = valid ? ALin[li] : 0;
+                const int v = valid ? ALcur[li] : 0;
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = valid ? J.vis[vw] : ~0ull;
                 int64_t b = 0, e = 0;
@@ -524,39 +611,24 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                     }
                 }
                 __syncwarp();
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, Qout, C,
-                               A, s_hist, false);
-                int inc = valid && ((vis | acc) != ~0ull);
-#pragma unroll
-                for (int o = 1; o < W; o <<= 1) inc |= __shfl_xor_sync(FULL, inc, o);
-                const bool keep = inc && w == 0;
-                const unsigned bal = __ballot_sync(FULL, keep);
-                if (bal) {
-                    const int first = __ffs(bal) - 1;
-                    unsigned base = 0;
-                    if (lane == first) base = atomicAdd(&C->alen, (unsigned)__popc(bal));
-                    base = __shfl_sync(FULL, base, first);
-                    if (keep) ALout[base + __popc(bal & ((1u << lane) - 1u))] = v;
-                }
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, A, s_hist,
+                               false);
             }
             // A2: medium nodes, one warp per node.
             for (int64_t t = gwarp; t < J.nM; t += nwarps) {
                 const int v = J.Mlist[t];
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
+                if (__all_sync(FULL, visw == ~0ull)) continue;
                 const int64_t b = rp[v], e = rp[v + 1];
                 uint64_t acc = 0;
-                if (__all_sync(FULL, visw == ~0ull)) continue;
-                {
-                    for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                        acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w,
-                                                     A.words);
-                        const uint64_t r = or_same_word<W>(acc);
-                        if (__all_sync(FULL, (r | visw) == ~0ull)) break;
-                    }
+                for (int64_t base = b; base < e; base += NPW * kUnroll) {
+                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
+                    const uint64_t r = or_same_word<W>(acc);
+                    if (__all_sync(FULL, (r | visw) == ~0ull)) break;
                 }
                 const uint64_t r = or_same_word<W>(acc);
-                tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, Qout,
-                               C, A, s_hist, false);
+                tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, A, s_hist,
+                               false);
             }
             // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
             for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
@@ -593,15 +665,13 @@ __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
                     if (acc) J.nxt[vw] = 0;
                     deg = rp[v + 1] - rp[v];
                 }
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, Qout, C,
-                               A, s_hist, false);
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, false);
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
             if (!grid_sync(ctl, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->bu_levels += 1;
-            al_len = ((volatile LevelCtl *)C)->alen;
-            al_par = al_par == 0 ? 1 : 0;
+            prev_td = false;
         }
     }
     // Pass statistics.

@@ -135,7 +135,7 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     {
         Carve c{nullptr};
         for (int i = 0; i < 4; ++i) c.take<uint64_t>((size_t)n * W);
-        for (int i = 0; i < 8; ++i) c.take<int32_t>((size_t)n);
+        for (int i = 0; i < 9; ++i) c.take<int32_t>((size_t)n);
         c.take<uint64_t>((size_t)n * 2);
         c.take<uint32_t>((size_t)k * k);
         c.take<uint32_t>((size_t)hist_cap * k);
@@ -162,6 +162,7 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     int32_t *Llist = c.take<int32_t>((size_t)n);
     int32_t *AL0 = c.take<int32_t>((size_t)n);
     int32_t *AL1 = c.take<int32_t>((size_t)n);
+    uint32_t *fstamp = c.take<uint32_t>((size_t)n);
     uint64_t *sum2 = c.take<uint64_t>((size_t)n * 2);
     uint32_t *dcc = c.take<uint32_t>((size_t)k * k);
     uint32_t *hist = c.take<uint32_t>((size_t)hist_cap * k);
@@ -213,6 +214,7 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     j.vis = vis; j.F0 = F0; j.F1 = F1; j.nxt = nxt;
     j.Q0 = Q0; j.Q1 = Q1; j.T = T; j.tflag = tflag;
     j.AL0 = AL0; j.AL1 = AL1;
+    j.fstamp = fstamp;
     j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
     j.sum2 = sum2;
     j.pivot = d_pivot;
