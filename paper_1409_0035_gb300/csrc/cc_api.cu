@@ -9,6 +9,7 @@
 
 #include "cc_internal.h"
 #include "estimate.h"
+#include "graph_gpu.h"
 #include "sssp.h"
 
 using namespace ccg;
@@ -262,6 +263,24 @@ int finish_graph(cc_graph *g, HostCSR &h)
     RC(upload_csr(g->fw, h.n, h.rp, h.col, h.w));
     if (h.has_rev) RC(upload_csr(g->rv, h.n, h.rrp, h.rcol, h.rw));
     return CC_OK;
+}
+
+// Take ownership of a CSR built on the device.
+int adopt_device_csr(cc_graph *g, DeviceCSR &d)
+{
+    g->n = d.n;
+    g->arcs = d.arcs;
+    g->weighted = d.w != nullptr;
+    g->fw.rp.p = d.rp;
+    g->fw.rp.cap = (size_t)(d.n + 1) * 8;
+    g->fw.col.p = d.col;
+    g->fw.col.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
+    if (d.w) {
+        g->fw.w.p = d.w;
+        g->fw.w.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
+    }
+    d.rp = d.col = d.w = nullptr;
+    return build_classes(d.rp_host, d.n, g->fw.cls);
 }
 
 void free_graph(cc_graph *g)
@@ -613,18 +632,33 @@ int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_
     if (!out) return CC_ERR_ARG;
     *out = nullptr;
     RC(device_ok());
-    HostCSR h;
-    RC(build_host_csr(n, m, src, dst, w, directed != 0, keep_component != 0, h));
     cc_graph *g = new (std::nothrow) cc_graph();
     if (!g) return CC_ERR_OOM;
     g->directed = directed != 0;
-    const int rc = finish_graph(g, h);
+    int rc = CC_OK;
+    std::vector<int32_t> old_id;
+    if (!directed) {
+        // Undirected: sort, merge, components and renumbering on the device.
+        DeviceCSR d;
+        rc = build_csr_device(n, m, src, dst, w, keep_component != 0, d);
+        if (rc == CC_OK) rc = adopt_device_csr(g, d);
+        if (d.rp) cudaFree(d.rp);
+        if (d.col) cudaFree(d.col);
+        if (d.w) cudaFree(d.w);
+        old_id.swap(d.old_id);
+    } else {
+        // Directed: strongly connected components on the host (Tarjan).
+        HostCSR h;
+        rc = build_host_csr(n, m, src, dst, w, true, keep_component != 0, h);
+        if (rc == CC_OK) rc = finish_graph(g, h);
+        old_id.swap(h.old_id);
+    }
     if (rc != CC_OK) {
         free_graph(g);
         delete g;
         return rc;
     }
-    if (old_id_out) std::memcpy(old_id_out, h.old_id.data(), h.old_id.size() * 4);
+    if (old_id_out) std::memcpy(old_id_out, old_id.data(), old_id.size() * 4);
     *out = g;
     return CC_OK;
 }

@@ -1,0 +1,570 @@
+// Graph to CSR on the device (undirected graphs): the preprocessing step
+// that section 7 counts in its times.
+//
+//   1. arcs: each edge u-v gives the keys (u << 32 | v) and (v << 32 | u)
+//      with its length; self-loops dropped (stream compaction);
+//   2. stable LSD radix sort of the 64-bit keys (8-bit digits, only the
+//      2 * ceil(log2 n) significant bits), lengths carried along;
+//   3. parallel arcs merged keeping the smallest length (segmented minimum
+//      over equal keys), then compacted;
+//   4. row offsets from the sorted tails;
+//   5. connected components by lock-free union-find (roots hooked under the
+//      smaller root with atomicCAS, path halving), so a component's label
+//      is its smallest node id; the largest component wins, ties to the
+//      smallest label;
+//   6. kept nodes renumbered in increasing original id (exclusive scan) and
+//      the rows rewritten (monotone renumbering keeps them sorted).
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "cc_internal.h"
+#include "graph_gpu.h"
+
+namespace ccg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;                 // keys per thread per sort tile
+constexpr int kTile = kThreads * kItems;   // 4096 keys per tile
+constexpr int kRadix = 256;
+
+// ---------------------------------------------------------------- scan
+
+// Exclusive scan of uint64 values in tiles of kThreads*4: per-tile sums,
+// scan of the sums (recursively), then the in-tile scan plus offset.
+__global__ void k_tile_sums(const uint64_t *in, int64_t n, uint64_t *sums)
+{
+    __shared__ uint64_t s[kThreads];
+    const int64_t base = (int64_t)blockIdx.x * kThreads * 4;
+    uint64_t t = 0;
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+        if (i < n) t += in[i];
+    }
+    s[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = s[0];
+}
+
+__global__ void k_tile_scan(const uint64_t *in, int64_t n, const uint64_t *offs,
+                            uint64_t *out)
+{
+    __shared__ uint64_t s[kThreads * 4];
+    const int64_t base = (int64_t)blockIdx.x * kThreads * 4;
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+        s[j * kThreads + threadIdx.x] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    // each thread scans 4 consecutive values, then a Hillis-Steele scan of
+    // the thread totals
+    uint64_t v[4], tot = 0;
+    for (int j = 0; j < 4; ++j) {
+        v[j] = s[threadIdx.x * 4 + j];
+        tot += v[j];
+    }
+    __shared__ uint64_t t[kThreads];
+    t[threadIdx.x] = tot;
+    __syncthreads();
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const uint64_t a = threadIdx.x >= o ? t[threadIdx.x - o] : 0;
+        __syncthreads();
+        t[threadIdx.x] += a;
+        __syncthreads();
+    }
+    uint64_t run = t[threadIdx.x] - tot + offs[blockIdx.x];
+    __syncthreads();
+    for (int j = 0; j < 4; ++j) {
+        s[threadIdx.x * 4 + j] = run;
+        run += v[j];
+    }
+    __syncthreads();
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+        if (i < n) out[i] = s[j * kThreads + threadIdx.x];
+    }
+}
+
+// ---------------------------------------------------------------- sort
+
+__global__ void k_digit_hist(const uint64_t *keys, int64_t n, int shift, int nbits,
+                             uint32_t *counts, int ntiles)
+{
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const uint64_t mask = (1ull << nbits) - 1;
+    for (int j = 0; j < kItems; ++j) {
+        const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile: keys are taken in index order (iteration j
+// covers indices base + j*256 .. +255, warp-major), each key's rank among
+// the tile's earlier keys with the same digit is the running count of that
+// digit plus the counts of earlier warps plus the rank inside its warp.
+__global__ void k_digit_scatter(const uint64_t *keys, const uint32_t *vals, int64_t n,
+                                int shift, int nbits, const uint64_t *offs, int ntiles,
+                                uint64_t *okeys, uint32_t *ovals)
+{
+    constexpr int kWarps = kThreads / 32;
+    __shared__ uint32_t run[kRadix];
+    __shared__ uint32_t wcnt[kWarps][kRadix];
+    __shared__ uint64_t goff[kRadix];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    run[threadIdx.x] = 0;
+    goff[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const uint64_t mask = (1ull << nbits) - 1;
+    for (int j = 0; j < kItems; ++j) {
+        for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t i = base + (int64_t)j * kThreads + threadIdx.x;
+        const bool ok = i < n;
+        const uint64_t key = ok ? keys[i] : 0;
+        const uint32_t val = ok ? vals[i] : 0;
+        const int d = ok ? (int)((key >> shift) & mask) : kRadix;  // kRadix: none
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        // digit-major prefix over warps (thread = digit)
+        uint32_t acc = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = acc;
+            acc += c;
+        }
+        __syncthreads();
+        if (ok) {
+            const uint64_t pos = goff[d] + run[d] + wcnt[wid][d] + rank;
+            okeys[pos] = key;
+            ovals[pos] = val;
+        }
+        __syncthreads();
+        run[threadIdx.x] += acc;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- arcs
+
+__global__ void k_make_arcs(const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                            int64_t m, int64_t n, int b, uint64_t *keys, uint32_t *vals,
+                            uint64_t *flags, int *err)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t u = src[e], v = dst[e];
+        const uint32_t ww = w ? w[e] : 1u;
+        if ((int64_t)u >= n || (int64_t)v >= n) atomicExch(err, CC_ERR_GRAPH);
+        if (ww == 0) atomicExch(err, CC_ERR_ARG);
+        const uint64_t keep = u != v && (int64_t)u < n && (int64_t)v < n;
+        keys[2 * e] = (u << b) | v;
+        keys[2 * e + 1] = (v << b) | u;
+        vals[2 * e] = ww;
+        vals[2 * e + 1] = ww;
+        flags[2 * e] = keep;
+        flags[2 * e + 1] = keep;
+    }
+}
+
+__global__ void k_compact(const uint64_t *keys, const uint32_t *vals, const uint64_t *flags,
+                          const uint64_t *pos, int64_t n, uint64_t *okeys, uint32_t *ovals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i]) {
+            okeys[pos[i]] = keys[i];
+            ovals[pos[i]] = vals[i];
+        }
+}
+
+// flags[i] = 1 for the first arc of each run of equal keys; mins[run start]
+// = the smallest length of the run.
+__global__ void k_first_of_run(const uint64_t *keys, int64_t n, uint64_t *flags)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_run_min(const uint64_t *keys, uint32_t *vals, const uint64_t *flags,
+                          int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        uint32_t mn = vals[i];
+        for (int64_t j = i + 1; j < n && keys[j] == keys[i]; ++j) mn = min(mn, vals[j]);
+        vals[i] = mn;
+    }
+}
+
+// Row offsets from keys sorted by tail: rp[u] = first arc with tail >= u.
+__global__ void k_row_ptr(const uint64_t *keys, int64_t a, int64_t n, int b, int64_t *rp)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= a;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cur = i < a ? (int64_t)(keys[i] >> b) : n;
+        const int64_t prev = i > 0 ? (int64_t)(keys[i - 1] >> b) : -1;
+        for (int64_t u = prev + 1; u <= cur; ++u) rp[u] = i;
+    }
+}
+
+__global__ void k_heads(const uint64_t *keys, int64_t a, int b, int32_t *col)
+{
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a;
+         i += (int64_t)gridDim.x * blockDim.x)
+        col[i] = (int32_t)(keys[i] & mask);
+}
+
+// ---------------------------------------------------------------- components
+
+__device__ __forceinline__ int32_t find_root(int32_t *parent, int32_t x)
+{
+    int32_t p = parent[x];
+    while (p != x) {
+        const int32_t g = parent[p];
+        if (g != p) parent[x] = g;  // path halving (benign race)
+        x = p;
+        p = g;
+    }
+    return x;
+}
+
+__global__ void k_iota32(int32_t *p, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+
+// Union of the endpoints of every arc u -> v with u < v.
+__global__ void k_hook(const int64_t *rp, const int32_t *col, int64_t n, int32_t *parent)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            const int32_t v = col[e];
+            if (v <= u) continue;
+            int32_t a = find_root(parent, (int32_t)u), b = find_root(parent, v);
+            while (a != b) {
+                if (a < b) { const int32_t t = a; a = b; b = t; }  // hook larger under smaller
+                const int32_t old = atomicCAS(&parent[a], a, b);
+                if (old == a) break;
+                a = find_root(parent, old);
+                b = find_root(parent, b);
+            }
+        }
+    }
+}
+
+__global__ void k_flatten_count(int32_t *parent, int64_t n, uint32_t *size)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = find_root(parent, (int32_t)v);
+        parent[v] = r;
+        atomicAdd(&size[r], 1u);
+    }
+}
+
+// best = max over roots of (size << 32 | ~root): largest, ties to smallest id
+__global__ void k_pick(const uint32_t *size, int64_t n, unsigned long long *best)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (size[v])
+            atomicMax(best, ((unsigned long long)size[v] << 32) |
+                                (0xFFFFFFFFull - (unsigned long long)v));
+}
+
+__global__ void k_keep_flags(const int32_t *parent, int64_t n, int32_t root, uint64_t *flags)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        flags[v] = parent[v] == root ? 1 : 0;
+}
+
+// Degrees of kept nodes (for the new row offsets) and the new id map.
+__global__ void k_kept_deg(const int64_t *rp, const uint64_t *flags, const uint64_t *pos,
+                           int64_t n, uint64_t *deg, int32_t *newid, int32_t *old_id)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        if (flags[v]) {
+            deg[pos[v]] = (uint64_t)(rp[v + 1] - rp[v]);
+            newid[v] = (int32_t)pos[v];
+            old_id[pos[v]] = (int32_t)v;
+        } else {
+            newid[v] = -1;
+        }
+    }
+}
+
+__global__ void k_rewrite_rows(const int64_t *rp, const int32_t *col, const uint32_t *w,
+                               const int32_t *old_id, const int32_t *newid,
+                               const uint64_t *nrp, int64_t nk, int32_t *ncol, uint32_t *nw)
+{
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nk;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = old_id[x];
+        int64_t o = (int64_t)nrp[x];
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e, ++o) {
+            ncol[o] = newid[col[e]];
+            if (w) nw[o] = w[e];
+        }
+    }
+}
+
+__global__ void k_u64_to_i64(const uint64_t *in, int64_t n, int64_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int64_t)in[i];
+}
+
+__global__ void k_widen(const uint32_t *in, int64_t n, uint64_t *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+int gsz(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 32); }
+
+struct Buf {
+    void *p = nullptr;
+    ~Buf() { if (p) cudaFree(p); }
+    template <class T> T *as() { return static_cast<T *>(p); }
+    int alloc(size_t bytes)
+    {
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return CC_ERR_OOM;
+        }
+        return CC_OK;
+    }
+};
+
+#define G_RC(x)                      \
+    do {                             \
+        int r_ = (x);                \
+        if (r_ != CC_OK) return r_;  \
+    } while (0)
+#define G_CK(x)                                          \
+    do {                                                 \
+        if ((x) != cudaSuccess) {                        \
+            cudaGetLastError();                          \
+            return CC_ERR_CUDA;                          \
+        }                                                \
+    } while (0)
+
+// Exclusive scan of n uint64 values (in -> out, may alias), returns the total.
+int scan_u64(const uint64_t *in, uint64_t *out, int64_t n, uint64_t *total, cudaStream_t st)
+{
+    const int per = kThreads * 4;
+    const int64_t nb = (n + per - 1) / per;
+    Buf sums, offs;
+    G_RC(sums.alloc((size_t)std::max<int64_t>(nb, 1) * 8));
+    G_RC(offs.alloc((size_t)std::max<int64_t>(nb, 1) * 8));
+    if (n > 0) k_tile_sums<<<(int)nb, kThreads, 0, st>>>(in, n, sums.as<uint64_t>());
+    uint64_t tot = 0;
+    if (nb <= 1) {
+        G_CK(cudaMemsetAsync(offs.p, 0, 8, st));
+        if (n > 0) G_CK(cudaMemcpyAsync(&tot, sums.p, 8, cudaMemcpyDeviceToHost, st));
+    } else {
+        G_RC(scan_u64(sums.as<uint64_t>(), offs.as<uint64_t>(), nb, &tot, st));
+    }
+    if (n > 0) k_tile_scan<<<(int)nb, kThreads, 0, st>>>(in, n, offs.as<uint64_t>(), out);
+    G_CK(cudaStreamSynchronize(st));
+    *total = tot;
+    return CC_OK;
+}
+
+// Stable LSD radix sort of (keys, vals) over the low `bits` bits.
+int radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bits, uint64_t *tk,
+               uint32_t *tv, cudaStream_t st, bool *in_tmp)
+{
+    const int ntiles = (int)((n + kTile - 1) / kTile);
+    Buf counts, offs;
+    G_RC(counts.alloc((size_t)kRadix * ntiles * 4));
+    G_RC(offs.alloc((size_t)kRadix * ntiles * 8));
+    Buf c64;
+    G_RC(c64.alloc((size_t)kRadix * ntiles * 8));
+    uint64_t *ka = keys, *kb = tk;
+    uint32_t *va = vals, *vb = tv;
+    for (int shift = 0; shift < bits; shift += 8) {
+        const int nb = std::min(8, bits - shift);
+        k_digit_hist<<<ntiles, kThreads, 0, st>>>(ka, n, shift, nb, counts.as<uint32_t>(),
+                                                  ntiles);
+        // widen to 64-bit for the scan
+        const int64_t nc = (int64_t)kRadix * ntiles;
+        k_widen<<<gsz(nc), 256, 0, st>>>(counts.as<uint32_t>(), nc, c64.as<uint64_t>());
+        uint64_t tot = 0;
+        G_RC(scan_u64(c64.as<uint64_t>(), offs.as<uint64_t>(), nc, &tot, st));
+        k_digit_scatter<<<ntiles, kThreads, 0, st>>>(ka, va, n, shift, nb,
+                                                     offs.as<uint64_t>(), ntiles, kb, vb);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    G_CK(cudaStreamSynchronize(st));
+    *in_tmp = ka != keys;
+    return CC_OK;
+}
+
+
+}  // namespace
+
+// Undirected graph to CSR on the device (see the top of this file).  On
+// success the device buffers rp / col / w (w only when lengths are given)
+// are owned by the caller (cudaFree), rp_host and old_id hold host copies.
+int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t *h_dst,
+                     const uint32_t *h_w, bool keep_component, DeviceCSR &out)
+{
+    if (n < 2 || m < 0 || (m > 0 && (!h_src || !h_dst))) return CC_ERR_ARG;
+    if (n > 0x7FFFFFFFLL || 2 * m > 0x7FFFFFFFLL) return CC_ERR_TOO_LARGE;
+    cudaStream_t st = 0;
+    int b = 1;
+    while ((1ll << b) < n) ++b;
+    const int64_t A0 = 2 * m;
+    Buf dsrc, ddst, dw, k0, v0, k1, v1, fl, pos, err;
+    G_RC(dsrc.alloc(m * 4));
+    G_RC(ddst.alloc(m * 4));
+    if (h_w) G_RC(dw.alloc(m * 4));
+    G_RC(k0.alloc(A0 * 8));
+    G_RC(v0.alloc(A0 * 4));
+    G_RC(k1.alloc(A0 * 8));
+    G_RC(v1.alloc(A0 * 4));
+    G_RC(fl.alloc(A0 * 8));
+    G_RC(pos.alloc((A0 + 1) * 8));
+    G_RC(err.alloc(4));
+    if (m > 0) {
+        G_CK(cudaMemcpy(dsrc.p, h_src, m * 4, cudaMemcpyHostToDevice));
+        G_CK(cudaMemcpy(ddst.p, h_dst, m * 4, cudaMemcpyHostToDevice));
+        if (h_w) G_CK(cudaMemcpy(dw.p, h_w, m * 4, cudaMemcpyHostToDevice));
+    }
+    G_CK(cudaMemset(err.p, 0, 4));
+    // 1. arcs both ways, self-loops dropped
+    if (m > 0)
+        k_make_arcs<<<gsz(m), 256, 0, st>>>(dsrc.as<uint32_t>(), ddst.as<uint32_t>(),
+                                            h_w ? dw.as<uint32_t>() : nullptr, m, n, b,
+                                            k0.as<uint64_t>(), v0.as<uint32_t>(),
+                                            fl.as<uint64_t>(), err.as<int>());
+    int herr = 0;
+    G_CK(cudaMemcpy(&herr, err.p, 4, cudaMemcpyDeviceToHost));
+    if (herr) return herr;
+    uint64_t A1 = 0;
+    G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), A0, &A1, st));
+    if (A0 > 0)
+        k_compact<<<gsz(A0), 256, 0, st>>>(k0.as<uint64_t>(), v0.as<uint32_t>(),
+                                           fl.as<uint64_t>(), pos.as<uint64_t>(), A0,
+                                           k1.as<uint64_t>(), v1.as<uint32_t>());
+    // 2. sort by (tail, head)
+    bool in_tmp = false;
+    if (A1 > 0)
+        G_RC(radix_sort(k1.as<uint64_t>(), v1.as<uint32_t>(), (int64_t)A1, 2 * b,
+                        k0.as<uint64_t>(), v0.as<uint32_t>(), st, &in_tmp));
+    uint64_t *ks = in_tmp ? k0.as<uint64_t>() : k1.as<uint64_t>();
+    uint32_t *vs = in_tmp ? v0.as<uint32_t>() : v1.as<uint32_t>();
+    uint64_t *ko = in_tmp ? k1.as<uint64_t>() : k0.as<uint64_t>();
+    uint32_t *vo = in_tmp ? v1.as<uint32_t>() : v0.as<uint32_t>();
+    // 3. merge parallel arcs (smallest length)
+    uint64_t A2 = 0;
+    if (A1 > 0) {
+        k_first_of_run<<<gsz(A1), 256, 0, st>>>(ks, (int64_t)A1, fl.as<uint64_t>());
+        k_run_min<<<gsz(A1), 256, 0, st>>>(ks, vs, fl.as<uint64_t>(), (int64_t)A1);
+        G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), (int64_t)A1, &A2, st));
+        k_compact<<<gsz(A1), 256, 0, st>>>(ks, vs, fl.as<uint64_t>(), pos.as<uint64_t>(),
+                                           (int64_t)A1, ko, vo);
+    }
+    // 4. CSR of all n nodes
+    Buf rp, col;
+    G_RC(rp.alloc((n + 1) * 8));
+    G_RC(col.alloc(std::max<uint64_t>(A2, 1) * 4));
+    k_row_ptr<<<gsz((int64_t)A2 + 1), 256, 0, st>>>(ko, (int64_t)A2, n, b, rp.as<int64_t>());
+    if (A2 > 0) k_heads<<<gsz(A2), 256, 0, st>>>(ko, (int64_t)A2, b, col.as<int32_t>());
+    uint32_t *wv = vo;  // merged lengths, in arc order
+    int64_t nk = n;
+    Buf nrp, ncol, nw, parent, size, newid, oldid, degs, best;
+    int64_t *frp = rp.as<int64_t>();
+    int32_t *fcol = col.as<int32_t>();
+    uint32_t *fw = h_w ? wv : nullptr;
+    if (keep_component) {
+        // 5. components
+        G_RC(parent.alloc(n * 4));
+        G_RC(size.alloc(n * 4));
+        G_RC(best.alloc(8));
+        G_CK(cudaMemset(size.p, 0, n * 4));
+        G_CK(cudaMemset(best.p, 0, 8));
+        k_iota32<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n);
+        k_hook<<<gsz(n), 256, 0, st>>>(frp, fcol, n, parent.as<int32_t>());
+        k_flatten_count<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, size.as<uint32_t>());
+        k_pick<<<gsz(n), 256, 0, st>>>(size.as<uint32_t>(), n,
+                                       best.as<unsigned long long>());
+        unsigned long long hb = 0;
+        G_CK(cudaMemcpy(&hb, best.p, 8, cudaMemcpyDeviceToHost));
+        const int32_t root = (int32_t)(0xFFFFFFFFull - (hb & 0xFFFFFFFFull));
+        // 6. renumber the kept nodes and rewrite their rows
+        k_keep_flags<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, root, fl.as<uint64_t>());
+        uint64_t kept = 0;
+        G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), n, &kept, st));
+        nk = (int64_t)kept;
+        if (nk < 2) return CC_ERR_GRAPH;
+        G_RC(newid.alloc(n * 4));
+        G_RC(oldid.alloc(nk * 4));
+        G_RC(degs.alloc((nk + 1) * 8));
+        k_kept_deg<<<gsz(n), 256, 0, st>>>(frp, fl.as<uint64_t>(), pos.as<uint64_t>(), n,
+                                           degs.as<uint64_t>(), newid.as<int32_t>(),
+                                           oldid.as<int32_t>());
+        uint64_t arcs = 0;
+        G_RC(scan_u64(degs.as<uint64_t>(), degs.as<uint64_t>(), nk, &arcs, st));
+        G_CK(cudaMemcpy(degs.as<uint64_t>() + nk, &arcs, 8, cudaMemcpyHostToDevice));
+        G_RC(nrp.alloc((nk + 1) * 8));
+        G_RC(ncol.alloc(std::max<uint64_t>(arcs, 1) * 4));
+        if (h_w) G_RC(nw.alloc(std::max<uint64_t>(arcs, 1) * 4));
+        k_u64_to_i64<<<gsz(nk + 1), 256, 0, st>>>(degs.as<uint64_t>(), nk + 1,
+                                                  nrp.as<int64_t>());
+        k_rewrite_rows<<<gsz(nk), 256, 0, st>>>(frp, fcol, fw, oldid.as<int32_t>(),
+                                                newid.as<int32_t>(), degs.as<uint64_t>(), nk,
+                                                ncol.as<int32_t>(),
+                                                h_w ? nw.as<uint32_t>() : nullptr);
+        out.arcs = (int64_t)arcs;
+        out.old_id.resize(nk);
+        G_CK(cudaMemcpy(out.old_id.data(), oldid.p, nk * 4, cudaMemcpyDeviceToHost));
+        std::swap(out.rp, nrp.p);
+        std::swap(out.col, ncol.p);
+        if (h_w) std::swap(out.w, nw.p);
+    } else {
+        out.arcs = (int64_t)A2;
+        out.old_id.resize(n);
+        for (int64_t v = 0; v < n; ++v) out.old_id[v] = (int32_t)v;
+        if (h_w) {
+            G_RC(nw.alloc(std::max<uint64_t>(A2, 1) * 4));
+            if (A2) G_CK(cudaMemcpy(nw.p, wv, A2 * 4, cudaMemcpyDeviceToDevice));
+            std::swap(out.w, nw.p);
+        }
+        std::swap(out.rp, rp.p);
+        std::swap(out.col, col.p);
+    }
+    out.n = nk;
+    out.rp_host.resize(nk + 1);
+    G_CK(cudaMemcpy(out.rp_host.data(), out.rp, (nk + 1) * 8, cudaMemcpyDeviceToHost));
+    G_CK(cudaDeviceSynchronize());
+    return CC_OK;
+}
+
+}  // namespace ccg

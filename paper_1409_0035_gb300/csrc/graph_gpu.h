@@ -1,0 +1,18 @@
+// Graph to CSR on the device (graph_gpu.cu).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace ccg {
+
+struct DeviceCSR {
+    int64_t n = 0, arcs = 0;
+    void *rp = nullptr, *col = nullptr, *w = nullptr;  // device, caller frees
+    std::vector<int64_t> rp_host;
+    std::vector<int32_t> old_id;
+};
+
+int build_csr_device(int64_t n, int64_t m, const uint32_t *src, const uint32_t *dst,
+                     const uint32_t *w, bool keep_component, DeviceCSR &out);
+
+}  // namespace ccg

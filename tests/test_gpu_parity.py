@@ -72,6 +72,31 @@ def test_graph_build_matches_oracle(cc, name):
         cc.cc_graph_free(g)
 
 
+@pytest.mark.parametrize("scale,ef,weighted", [(16, 16, False), (17, 8, True), (14, 4, False)])
+def test_graph_build_large_matches_oracle(cc, scale, ef, weighted):
+    """Device CSR build (radix sort over many tiles, multi-level scans,
+    union-find) against the oracle's numpy build."""
+    n, s, d = synth.rmat_edges(scale, ef, seed=scale)
+    w = synth.random_weights(s.size, 1, 7, seed=3) if weighted else None
+    g, old, og = both(cc, n, s, d, w)
+    try:
+        rp, col, ww = cc.cc_graph_copy_csr(g)
+        assert (rp == og.row_ptr).all() and (col == og.col).all()
+        assert (old == og.old_id).all()
+        if weighted:
+            assert (ww == og.w).all()
+    finally:
+        cc.cc_graph_free(g)
+    g, old = cc.cc_graph_from_edges(n, s, d, w, keep_component=False)
+    og = orc.csr_from_edges(n, s, d, w=w, keep_component=False)
+    try:
+        rp, col, ww = cc.cc_graph_copy_csr(g)
+        assert (rp == og.row_ptr).all() and (col == og.col).all()
+        assert (old == np.arange(n)).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
 def test_graph_build_weighted_directed(cc):
     n, s, d = synth.rmat_edges(9, 6, seed=8)
     w = synth.random_weights(s.size, 1, 30, seed=9)
