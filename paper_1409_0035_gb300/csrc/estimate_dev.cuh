@@ -1,0 +1,216 @@
+// Device functions of the estimator pipeline (estimate.cu): each takes an
+// explicit (start, stride) or source index so that the same code runs as a
+// stand-alone kernel or inside a team of the batched persistent launch.
+#pragma once
+#include <cstdint>
+
+#include "cc_internal.h"
+#include "estimate.h"
+
+namespace ccg {
+namespace {
+
+typedef unsigned __int128 u128;
+constexpr int kTailThreads = 256;
+
+// Round-to-nearest-even conversion of an unsigned 128-bit integer: the top
+// 64 significant bits with every lower bit folded into a sticky bit are
+// converted by the hardware (correctly rounded), then scaled by a power of
+// two (exact).
+__device__ __forceinline__ double u128_to_double(u128 x)
+{
+    const uint64_t hi = (uint64_t)(x >> 64);
+    if (hi == 0) return (double)(uint64_t)x;
+    const int lz = __clzll((long long)hi);
+    const u128 y = x << lz;
+    uint64_t top = (uint64_t)(y >> 64);
+    if ((uint64_t)y != 0) top |= 1ull;
+    return ldexp((double)top, 64 - lz);
+}
+
+__device__ __forceinline__ void d_fill_i32(int32_t *p, int64_t n, int32_t v, int64_t i0,
+                                int64_t stride)
+{
+    for (int64_t i = i0; i < n;
+         i += stride)
+        p[i] = v;
+}
+
+__device__ __forceinline__ void d_scatter_sidx(int32_t *sidx, const int32_t *src, int k,
+                                               int64_t i0, int64_t stride)
+{
+    for (int64_t i = i0; i < k; i += stride) sidx[src[i]] = (int32_t)i;
+}
+
+// S(c_i) = sum over levels l of l * |{v not in C at distance l}| plus the
+// distances to the sampled nodes (row i of delta_cc).
+__device__ __forceinline__ void d_S_sampled(const uint32_t *hist, int D, int k,
+                                            const uint32_t *dcc, uint64_t *S, int64_t i0,
+                                            int64_t stride)
+{
+    for (int64_t i = i0; i < k; i += stride) {
+        uint64_t s = 0;
+        for (int l = 1; l <= D; ++l) s += (uint64_t)l * hist[(int64_t)l * k + i];
+        for (int j = 0; j < k; ++j) s += dcc[i * k + j];
+        S[i] = s;
+    }
+}
+
+// Tail tables of the per-source distance histogram: TN[i][t] = number of
+// nodes of V \ C farther than t from c_i, TS[i][t] = the sum of their
+// distances, t = 0..D.  (Role of Algorithm 1's reverse scan of the
+// bin/count arrays.)  One CTA per source scans the histogram downwards in
+// tiles with a shared-memory suffix scan.
+__device__ __forceinline__ void d_tail_source(const uint32_t *hist, int64_t D, int k,
+                                              uint64_t *TN, uint64_t *TS, int i)
+{
+    __shared__ unsigned long long sN[kTailThreads], sS[kTailThreads];
+    const int tid = threadIdx.x;
+    unsigned long long cn = 0, cs = 0;
+    for (int64_t top = D; top >= 0; top -= kTailThreads) {
+        const int64_t t = top - tid;
+        const unsigned long long h = t >= 0 ? hist[t * k + i] : 0ull;
+        sN[tid] = h;
+        sS[tid] = t >= 0 ? (unsigned long long)t * h : 0ull;
+        __syncthreads();
+        for (int o = 1; o < kTailThreads; o <<= 1) {
+            unsigned long long a = 0, b = 0;
+            if (tid >= o) { a = sN[tid - o]; b = sS[tid - o]; }
+            __syncthreads();
+            sN[tid] += a;
+            sS[tid] += b;
+            __syncthreads();
+        }
+        if (t >= 0) {
+            TN[(int64_t)i * (D + 1) + t] = cn + sN[tid] - h;
+            TS[(int64_t)i * (D + 1) + t] = cs + sS[tid] - (unsigned long long)t * h;
+        }
+        cn += sN[kTailThreads - 1];
+        cs += sS[kTailThreads - 1];
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void d_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd,
+                                           int64_t i0, int64_t stride)
+{
+    for (int64_t p = i0; p < k; p += stride) {
+        uint32_t m = 0;
+        for (int i = 0; i < k; ++i) m = max(m, dcc[p * k + i]);
+        maxd[p] = m;
+    }
+}
+
+// Per unsampled node: threshold t = floor(Delta * den / num) (so that "d >
+// Delta/eps" is "d > t" for integer d), H statistics from the tail tables of
+// the pivot, |L cap C| and whether L(v) misses some sampled node (then the
+// hybrid needs the second pass).
+// mode & 1: thresholds and |L cap C| (needs delta_cc); mode & 2: H
+// statistics from the tail tables (needs the histogram of the pass that
+// produced it).
+__device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
+                           const int32_t *sidx, const int32_t *pivot,
+                           const uint32_t *delta, const uint32_t *dcc,
+                           const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
+                           HybPrep *hp, unsigned *npartial, int64_t i0,
+                                int64_t stride)
+{
+    for (int64_t v = i0; v < n;
+         v += stride) {
+        HybPrep h = (mode & 1) ? HybPrep{0, 0, 0, 0} : hp[v];
+        if (sidx[v] < 0) {
+            const int p = pivot[v];
+            const uint64_t t = (uint64_t)delta[v] * b / a;
+            if (mode & 2) {
+                const int64_t tt = t < (uint64_t)D ? (int64_t)t : D;
+                h.Hnum = TN[(int64_t)p * (D + 1) + tt];
+                h.Hsum = TS[(int64_t)p * (D + 1) + tt];
+            }
+            if (mode & 1) {
+                h.thr = t;
+                if (t >= maxd[p]) {
+                    h.LCnum = (uint64_t)k;
+                } else {
+                    uint64_t c = 0;
+                    for (int i = 0; i < k; ++i) c += dcc[(int64_t)p * k + i] <= t;
+                    h.LCnum = c | kPartialBit;
+                    atomicAdd(npartial, 1u);
+                }
+            }
+        }
+        hp[v] = h;
+    }
+}
+
+// L(v) cap C as a bit mask per (node, word): bit i set when the pivot's
+// distance to c_i is at most the threshold.  Zero for sampled nodes.
+__device__ __forceinline__ void d_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
+                        const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, int64_t i0,
+                                int64_t stride)
+{
+    for (int64_t i = i0; i < n * W;
+         i += stride) {
+        const int64_t v = i / W;
+        const int w = (int)(i % W);
+        uint64_t m = 0;
+        // Only nodes whose L(v) misses a sampled node accumulate in the
+        // second pass; the others take LCsum = sum.
+        if (sidx[v] < 0 && (hp[v].LCnum & kPartialBit)) {
+            const int p = pivot[v];
+            const uint64_t t = hp[v].thr;
+            const int lo = w * 64, hi = min(k, lo + 64);
+            for (int s = lo; s < hi; ++s)
+                if (dcc[(int64_t)p * k + s] <= t) m |= 1ull << (s - lo);
+        }
+        Lmask[i] = m;
+    }
+}
+
+__device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
+                                int64_t stride)
+{
+    for (int64_t v = i0; v < A.n;
+         v += stride) {
+        const uint64_t nm1 = (uint64_t)(A.n - 1);
+        const int j = A.sidx[v];
+        const uint64_t sum = A.sum2[2 * v];
+        double est[CC_NUM_EST];
+        uint64_t h6[6] = {0, 0, 0, 0, 0, 0};
+        if (j >= 0) {
+            const double ex = (double)A.S_samp[j];
+            est[0] = est[1] = est[2] = est[3] = ex;
+        } else {
+            const int p = A.pivot[v];
+            const uint64_t Sp = A.S_samp[p];
+            est[0] = u128_to_double((u128)nm1 * sum) / (double)A.k;
+            est[1] = (double)Sp;
+            est[2] = u128_to_double((u128)Sp + (u128)nm1 * A.delta[v]);
+            est[3] = 0.0;
+            if (A.hybrid) {
+                const HybPrep h = A.hp[v];
+                const uint64_t LCnum = h.LCnum & ~kPartialBit;
+                const bool partial = (h.LCnum & kPartialBit) != 0;
+                const uint64_t LCsum = partial ? A.lc2[2 * v] : sum;
+                const uint64_t LCsq = partial ? A.lc2[2 * v + 1] : A.sum2[2 * v + 1];
+                const uint64_t HCsum = sum - LCsum;
+                const uint64_t HCnum = (uint64_t)A.k - LCnum;
+                const uint64_t Lnum = nm1 - h.Hnum - HCnum;
+                const u128 N = (u128)(h.Hsum + HCsum) * LCnum + (u128)LCsum * Lnum;
+                est[3] = u128_to_double(N) / (double)LCnum;
+                h6[0] = h.Hsum; h6[1] = h.Hnum; h6[2] = HCsum;
+                h6[3] = LCsum; h6[4] = LCnum; h6[5] = LCsq;
+            }
+        }
+        for (int e = 0; e < CC_NUM_EST; ++e) {
+            if (e == CC_EST_HYBRID && !A.hybrid) continue;
+            if (A.s_hat[e]) A.s_hat[e][v] = est[e];
+            if (A.clo[e]) A.clo[e][v] = (double)nm1 / est[e];
+        }
+        if (A.hyb_int && A.hybrid)
+            for (int q = 0; q < 6; ++q) A.hyb_int[6 * v + q] = h6[q];
+        if (A.sample_sum) A.sample_sum[v] = sum;
+    }
+}
+
+}  // namespace
+}  // namespace ccg

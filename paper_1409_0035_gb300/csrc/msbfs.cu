@@ -26,663 +26,18 @@
 // CC_ERR_TIMEOUT and every CTA returns.
 #include <cstdint>
 
-#include "cc_internal.h"
+
+#include "msbfs_dev.cuh"
 
 namespace ccg {
 
 namespace {
 
-constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kUnroll = 4;  // independent gathers in flight per lane and step
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bits of word w that do not correspond to a source (index >= k): preset in
-// visited so that "all bits set" means "reached by every source".
-__device__ __forceinline__ uint64_t pad_mask(int k, int w)
-{
-    const int lo = w * 64;
-    if (k <= lo) return ~0ull;
-    if (k >= lo + 64) return 0ull;
-    return ~0ull << (k - lo);
-}
-
-// Grid-wide barrier over `nblocks` CTAs with a bounded wait.  Returns false
-// (in every thread of the CTA) when the wait ran out or another CTA reported
-// an error.  Same arrival/generation scheme as a cooperative-groups grid
-// sync, with a time limit.
-__device__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint64_t timeout_ns)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *vgen = &ctl->bar_gen;
-        volatile int *verr = &ctl->err;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const uint64_t t0 = gtimer();
-            unsigned ns = 8;
-            while (*vgen == g) {
-                if (*verr != 0) { ok = 0; break; }
-                if (gtimer() - t0 > timeout_ns) {
-                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
-            }
-        }
-        __threadfence();
-        if (*verr != 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// 32 x 32 bit-matrix transpose across a warp: on return lane c holds, in
-// bit r, bit c of the value lane r passed in.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
-{
-#pragma unroll
-    for (int j = 16; j >= 1; j >>= 1) {
-        const uint32_t m = j == 16 ? 0x0000FFFFu
-                         : j == 8  ? 0x00FF00FFu
-                         : j == 4  ? 0x0F0F0F0Fu
-                         : j == 2  ? 0x33333333u
-                                   : 0x55555555u;
-        const uint32_t y = __shfl_xor_sync(FULL, x, j);
-        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j))
-                       : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
-
-template <int W>
-struct LaneAcc {
-    // Per-lane histogram counts (W <= 8): hc[2s+h] counts source
-    // s*64 + h*32 + lane.
-    uint32_t hc[W <= 8 ? 2 * W : 1];
-    unsigned long long ef, eu_dec, words;
-    unsigned int ninc_dec, nfront;
-};
-
-// Update, reduce and enqueue one warp tile.  Lanes form groups of W; group
-// g = lane / W is one node (valid or not), lane % W its word.  Must be
-// called by all 32 lanes together.
-template <int W>
-__device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
-                                            int v, uint64_t vis, uint64_t nw,
-                                            int64_t deg, uint64_t *Fout,
-                                            LaneAcc<W> &A, unsigned *s_hist,
-                                            bool clear_tflag)
-{
-    const int lane = threadIdx.x & 31;
-    const int w = lane & (W - 1);
-    const int64_t vw = (int64_t)v * W + w;
-    // Frontier and visited words are written only when new bits arrive.  A
-    // frontier word left unwritten keeps bits of an older level of the same
-    // parity; each such source reached every neighbour one level after this
-    // node, so those bits are already in the neighbours' visited words and
-    // are masked off wherever the word is read.
-    if (valid && nw) {
-        Fout[vw] = nw;
-        J.vis[vw] = vis | nw;
-    }
-    int sx = -1;
-    if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC))) sx = J.sidx[v];
-    int c = __popcll(nw);
-    int cL = 0;
-    if ((J.red & RED_LC) && valid && sx < 0 && nw) cL = __popcll(nw & J.Lmask[vw]);
-    int had = (vis & ~pad_mask(J.k, w)) != 0;
-    int done_before = vis == ~0ull;
-    int done_after = (vis | nw) == ~0ull;
-    int pv = nw ? (w * 64 + __ffsll((long long)nw) - 1) : 0x7FFFFFFF;
-#pragma unroll
-    for (int o = 1; o < W; o <<= 1) {
-        c += __shfl_xor_sync(FULL, c, o);
-        cL += __shfl_xor_sync(FULL, cL, o);
-        had |= __shfl_xor_sync(FULL, had, o);
-        done_before &= __shfl_xor_sync(FULL, done_before, o);
-        done_after &= __shfl_xor_sync(FULL, done_after, o);
-        pv = min(pv, __shfl_xor_sync(FULL, pv, o));
-    }
-    const bool leader = valid && w == 0;
-    if (leader && c > 0) {
-        const uint64_t ul = (uint64_t)l;
-        if (J.red & RED_SUM) {
-            J.sum2[2 * (int64_t)v] += ul * (uint64_t)c;
-            J.sum2[2 * (int64_t)v + 1] += ul * ul * (uint64_t)c;
-        }
-        if (cL > 0) {
-            J.lc2[2 * (int64_t)v] += ul * (uint64_t)cL;
-            J.lc2[2 * (int64_t)v + 1] += ul * ul * (uint64_t)cL;
-        }
-        if ((J.red & RED_PIVOT) && !had) {
-            J.pivot[v] = pv;
-            J.delta[v] = (uint32_t)l;
-        }
-    }
-    if (leader && clear_tflag) J.tflag[v] = 0u;
-    if ((J.red & RED_DCC) && sx >= 0 && nw) {
-        uint64_t b = nw;
-        while (b) {
-            const int i = w * 64 + __ffsll((long long)b) - 1;
-            b &= b - 1;
-            J.dcc[(int64_t)i * J.dcc_k + sx] = (uint32_t)l;
-        }
-    }
-    if (J.red & RED_HIST) {
-        const uint64_t x = (valid && sx < 0) ? nw : 0ull;
-        if constexpr (W <= 8) {
-            if (__ballot_sync(FULL, x != 0ull)) {
-                const uint32_t lo = warp_transpose32((uint32_t)x, lane);
-                const uint32_t hi = warp_transpose32((uint32_t)(x >> 32), lane);
-                constexpr uint32_t M0 = W == 1 ? 0xFFFFFFFFu
-                                      : W == 2 ? 0x55555555u
-                                      : W == 4 ? 0x11111111u
-                                               : 0x01010101u;
-#pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    A.hc[2 * s] += __popc(lo & (M0 << s));
-                    A.hc[2 * s + 1] += __popc(hi & (M0 << s));
-                }
-            }
-        } else {
-            uint64_t b = x;
-            while (b) {
-                const int i = w * 64 + __ffsll((long long)b) - 1;
-                b &= b - 1;
-                atomicAdd(&s_hist[i], 1u);
-            }
-        }
-    }
-    // Stamp frontier nodes with the level (a later top-down level builds its
-    // queue from the stamps) and count level statistics.
-    const bool fr = leader && c > 0;
-    if (fr) {
-        J.fstamp[v] = (uint32_t)l;
-        A.ef += (unsigned long long)deg;
-        A.nfront += 1;
-    }
-    if (leader && done_after && !done_before) {
-        A.eu_dec += (unsigned long long)deg;
-        A.ninc_dec += 1;
-    }
-}
-
-__device__ __forceinline__ void trace_words(Ctl *ctl, int l, unsigned long long words)
-{
-    if (l >= kTraceLevels) return;
-    unsigned long long x = words;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&ctl->lvl_words[l], x);
-}
-
-// OR of `x` over the lanes holding the same word slot (lane % W).
-template <int W>
-__device__ __forceinline__ uint64_t or_same_word(uint64_t x)
-{
-#pragma unroll
-    for (int o = W; o < 32; o <<= 1) x |= __shfl_xor_sync(FULL, x, o);
-    return x;
-}
-
-// OR of the frontier words (slot w) of up to U CSR entries x, x+stride, ...
-// below e.  The U column loads and the U gathers are independent, so they
-// are all in flight together.
-template <int W, int U>
-__device__ __forceinline__ uint64_t gather_or(const int32_t *__restrict__ col,
-                                              const uint64_t *Fin, int64_t x, int64_t e,
-                                              int stride, int w, unsigned long long &words)
-{
-    int c[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int64_t ee = x + (int64_t)u * stride;
-        c[u] = ee < e ? __ldg(col + ee) : -1;
-    }
-    uint64_t f = 0;
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-        if (c[u] >= 0) {
-            f |= Fin[(int64_t)c[u] * W + w];
-            words += 1;
-        }
-    return f;
-}
-
-__device__ __forceinline__ unsigned long long block_sum64(unsigned long long x,
-                                                          unsigned long long *s)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) s[wid] = x;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
-    return t;  // valid in thread 0
-}
-
-// Flush per-lane counters of one level phase to the level control block and
-// (when asked) the CTA histogram to the global histogram of level l.
-template <int W>
-__device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
-                            unsigned *s_hist, bool flush_hist)
-{
-    __shared__ unsigned long long s_red[4][kBlock / 32];
-    unsigned long long x[4] = {A.ef, A.eu_dec, A.ninc_dec, A.nfront};
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) x[q] += __shfl_xor_sync(FULL, x[q], o);
-        if (lane == 0) s_red[q][wid] = x[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        unsigned long long t = 0;
-        for (int i = 0; i < kBlock / 32; ++i) t += s_red[threadIdx.x][i];
-        if (t) {
-            if (threadIdx.x == 0) atomicAdd(&C->ef, t);
-            if (threadIdx.x == 1) atomicAdd(&C->eu_dec, t);
-            if (threadIdx.x == 2) atomicAdd(&C->ninc_dec, (unsigned)t);
-            if (threadIdx.x == 3) atomicAdd(&C->qlen, (unsigned)t);
-        }
-    }
-    A.ef = A.eu_dec = 0;
-    A.ninc_dec = A.nfront = 0;
-    if (!flush_hist) return;
-    if constexpr (W <= 8) {
-#pragma unroll
-        for (int s = 0; s < W; ++s)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int i = s * 64 + h * 32 + lane;
-                if (A.hc[2 * s + h]) atomicAdd(&s_hist[i], A.hc[2 * s + h]);
-                A.hc[2 * s + h] = 0;
-            }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < J.k; i += blockDim.x) {
-        const unsigned c = s_hist[i];
-        if (c) {
-            atomicAdd(&J.hist[(int64_t)l * J.k + i], c);
-            s_hist[i] = 0;
-        }
-    }
-}
-
-// Order-preserving stream compaction over [0, N) by all CTAs: each CTA
-// takes a contiguous slice, counts its keepers, reserves their slots with
-// one atomicAdd on *counter, then writes them in slice order.
-template <class Keep, class Get>
-__device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsigned *counter)
-{
-    __shared__ unsigned s_w[kBlock / 32];
-    __shared__ unsigned s_base;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(N, lo + per);
-    unsigned c = 0;
-    for (int64_t i = lo + tid; i < hi; i += kBlock) c += keep(i) ? 1u : 0u;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-    if (lane == 0) s_w[wid] = c;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned t = 0;
-        for (int i = 0; i < kBlock / 32; ++i) t += s_w[i];
-        s_base = t ? atomicAdd(counter, t) : 0u;
-    }
-    __syncthreads();
-    unsigned base = s_base;
-    for (int64_t c0 = lo; c0 < hi; c0 += kBlock) {
-        const int64_t i = c0 + tid;
-        const bool k = i < hi && keep(i);
-        const unsigned bal = __ballot_sync(FULL, k);
-        if (lane == 0) s_w[wid] = __popc(bal);
-        __syncthreads();
-        unsigned off = 0, tot = 0;
-        for (int q = 0; q < kBlock / 32; ++q) {
-            if (q < wid) off += s_w[q];
-            tot += s_w[q];
-        }
-        if (k) out[base + off + __popc(bal & ((1u << lane) - 1u))] = get(i);
-        base += tot;
-        __syncthreads();
-    }
-}
-
-// Top-down push of one frontier node's words f (slot w per lane) to the
-// CSR entries [b, e): new bits are OR-ed into nxt and each node reached for
-// the first time this level is appended (once) to the touched list.  Called
-// by a whole warp; lane groups of W take NPW entries per step, kUnroll steps
-// at a time.
-template <int W>
-__device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restrict__ col,
-                                        uint64_t f, int64_t b, int64_t e, LevelCtl *C,
-                                        int32_t *Tout, LaneAcc<W> &A)
-{
-    constexpr int NPW = 32 / W;
-    const int lane = threadIdx.x & 31;
-    const int w = lane & (W - 1);
-    const int grp = lane / W;
-    if (f == 0ull) return;
-    for (int64_t base = b + grp; base < e; base += NPW * kUnroll) {
-        int vv[kUnroll];
-        uint64_t vs[kUnroll];
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q) {
-            const int64_t ee = base + (int64_t)q * NPW;
-            vv[q] = ee < e ? __ldg(col + ee) : -1;
-        }
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q)
-            vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + w] : ~0ull;
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q) {
-            if (vv[q] < 0) continue;
-            const int v = vv[q];
-            A.words += 1;
-            const uint64_t nbits = f & ~vs[q];
-            if (!nbits) continue;
-            const uint64_t old =
-                atomicOr((unsigned long long *)&J.nxt[(int64_t)v * W + w], nbits);
-            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u) {
-                const unsigned m = __activemask();
-                const int first = __ffs(m) - 1;
-                unsigned pos = 0;
-                if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
-                pos = __shfl_sync(m, pos, first);
-                Tout[pos + __popc(m & ((1u << lane) - 1u))] = v;
-            }
-        }
-    }
-}
-
 template <int W>
 __global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
 {
     extern __shared__ unsigned s_hist[];  // W * 64 counters
-    constexpr int NPW = 32 / W;           // nodes (or entries) per warp step
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t gthreads = (int64_t)gridDim.x * kBlock;
-    const int64_t gtid = (int64_t)blockIdx.x * kBlock + tid;
-    const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
-    const int w = lane & (W - 1);
-    const int grp = lane / W;
-    const int64_t n = J.n;
-    const int64_t *rp = J.rp;
-    const int32_t *col = J.col;
-    Ctl *ctl = J.ctl;
-    const unsigned nb = gridDim.x;
-    const bool doHist = (J.red & RED_HIST) != 0;
-
-    LaneAcc<W> A;
-#pragma unroll
-    for (int i = 0; i < (W <= 8 ? 2 * W : 1); ++i) A.hc[i] = 0;
-    A.ef = A.eu_dec = A.words = 0;
-    A.ninc_dec = A.nfront = 0;
-
-    // ---- level 0: clear the state, seed the sources -----------------------
-    for (int64_t i = gtid; i < n * W; i += gthreads) {
-        J.vis[i] = pad_mask(J.k, (int)(i & (W - 1)));
-        J.F0[i] = 0;
-        J.F1[i] = 0;
-        J.nxt[i] = 0;
-    }
-    for (int64_t v = gtid; v < n; v += gthreads) {
-        J.tflag[v] = 0;
-        J.fstamp[v] = kInf;
-    }
-    for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
-    if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-    for (int64_t i = gtid; i < J.k; i += gthreads) {
-        const int v = J.sources[i];
-        const uint64_t bit = 1ull << (i & 63);
-        const int64_t vw = (int64_t)v * W + (i >> 6);
-        atomicOr((unsigned long long *)&J.vis[vw], bit);
-        atomicOr((unsigned long long *)&J.F0[vw], bit);
-        J.fstamp[v] = 0u;
-        if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
-        if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
-        const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
-        atomicAdd(&ctl->lev[0].ef, d);
-        if (J.k == 1) {
-            atomicAdd(&ctl->lev[0].eu_dec, d);
-            atomicAdd(&ctl->lev[0].ninc_dec, 1u);
-        }
-    }
-    if (gtid == 0) {
-        ctl->lev[0].qlen = (unsigned)J.k;
-        ctl->lev[0].tlen = (unsigned)J.k;  // level 0 "touched" the sources
-    }
-    if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-
-    long long eu = J.arcs, ninc = n;
-    int last = 0;
-    // Active light-node list: Llist, later rebuilt (order-preserving) into
-    // AL0 / AL1 once the incomplete nodes fall below half of it.
-    const int32_t *ALcur = J.Llist;
-    int64_t al_len = J.nL;
-    int al_next = 0;
-    // Queue of a top-down level: the previous level's touched list when that
-    // level was top-down (level 0 "touched" the sources), else built from
-    // the frontier stamps.
-    bool prev_td = true;
-    const int32_t *prevT = J.sources;
-    int l = 1;
-    for (;; ++l) {
-        volatile LevelCtl *P = &ctl->lev[(l - 1) & 3];
-        const unsigned qprev = P->qlen;
-        const unsigned tprev = P->tlen;
-        const unsigned long long ef = P->ef;
-        eu -= (long long)P->eu_dec;
-        ninc -= (long long)P->ninc_dec;
-        if (qprev > 0) last = l - 1;
-        if (qprev == 0 || ninc == 0) break;
-        if (doHist && l >= J.hist_cap) {
-            if (gtid == 0) atomicCAS(&ctl->err, 0, 1);  // histogram too short
-            break;
-        }
-        const bool td = ef * (unsigned long long)J.alpha < (unsigned long long)eu;
-        if (gtid == 0 && l < kTraceLevels) {
-            ctl->lvl_ns[l] = gtimer();
-            ctl->lvl_td[l] = td;
-            ctl->lvl_front[l] = qprev;
-            ctl->lvl_ef[l] = ef;
-        }
-        const unsigned long long words_before = A.words;
-        if (gtid == 0) {
-            LevelCtl *Z = &ctl->lev[(l + 1) & 3];
-            Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
-            Z->alen = 0; Z->qcnt = 0;
-        }
-        uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
-        uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
-        LevelCtl *C = &ctl->lev[l & 3];
-
-        if (td) {
-            const int32_t *Qin = prevT;
-            int64_t qn = tprev;
-            if (!prev_td) {
-                const unsigned want = (unsigned)(l - 1);
-                block_compact(
-                    n, [&](int64_t i) { return J.fstamp[i] == want; },
-                    [&](int64_t i) { return (int32_t)i; }, J.Q0, &C->qcnt);
-                if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-                Qin = J.Q0;
-                qn = ((volatile LevelCtl *)C)->qcnt;
-            }
-            int32_t *Tout = (Qin == J.T) ? J.Q1 : J.T;
-            // P1: push the frontier words of the queued nodes; when the
-            // graph has chunk tasks, a heavy node's list is pushed by them.
-            for (int64_t t = gwarp; t < qn; t += nwarps) {
-                const int u = Qin[t];
-                const int64_t b = rp[u], e = rp[u + 1];
-                if (J.nHch > 0 && e - b > kMediumMaxDeg) continue;
-                const uint64_t f = Fin[(int64_t)u * W + w];
-                td_push<W>(J, col, f, b, e, C, Tout, A);
-            }
-            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
-                const int u = J.Hch_node[t];
-                if (J.fstamp[u] != (unsigned)(l - 1)) continue;
-                const uint64_t f = Fin[(int64_t)u * W + w];
-                if (__all_sync(FULL, f == 0ull)) continue;
-                const int64_t b = J.Hch_begin[t];
-                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A);
-            }
-            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-            // P2: finalise the touched nodes.
-            const int64_t tl = ((volatile LevelCtl *)C)->tlen;
-            for (int64_t t = gwarp; t * NPW < tl; t += nwarps) {
-                const int64_t li = t * NPW + grp;
-                const bool valid = li < tl;
-                const int v = valid ? Tout[li] : 0;
-                const int64_t vw = (int64_t)v * W + w;
-                uint64_t vis = ~0ull, acc = 0;
-                int64_t deg = 0;
-                if (valid) {
-                    vis = J.vis[vw];
-                    acc = J.nxt[vw];
-                    if (acc) J.nxt[vw] = 0;
-                    deg = rp[v + 1] - rp[v];
-                }
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, true);
-            }
-            trace_words(ctl, l, A.words - words_before);
-            flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-            if (gtid == 0) ctl->td_levels += 1;
-            prev_td = true;
-            prevT = Tout;
-        } else {
-            // Rebuild the light list when fewer than half of it can still be
-            // incomplete (ninc bounds the incomplete light nodes).
-            if (2 * ninc < al_len) {
-                int32_t *ALout = al_next ? J.AL1 : J.AL0;
-                const int32_t *ALin = ALcur;
-                block_compact(
-                    al_len,
-                    [&](int64_t i) {
-                        const int64_t v = ALin[i];
-                        bool inc = false;
-                        for (int q = 0; q < W; ++q) inc |= J.vis[v * W + q] != ~0ull;
-                        return inc;
-                    },
-                    [&](int64_t i) { return ALin[i]; }, ALout, &C->alen);
-                if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-                ALcur = ALout;
-                al_len = ((volatile LevelCtl *)C)->alen;
-                al_next ^= 1;
-            }
-            // A1: light nodes of the active list, one thread per (node, word).
-            for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
-                const int64_t li = t * NPW + grp;
-                const bool valid = li < al_len;
-                const int v = valid ? ALcur[li] : 0;
-                const int64_t vw = (int64_t)v * W + w;
-                uint64_t vis = valid ? J.vis[vw] : ~0ull;
-                int64_t b = 0, e = 0;
-                if (valid) { b = rp[v]; e = rp[v + 1]; }
-                uint64_t acc = 0;
-                if (vis != ~0ull) {
-                    for (int64_t x = b; x < e; x += kUnroll) {
-                        acc |= gather_or<W, kUnroll>(col, Fin, x, e, 1, w, A.words);
-                        if ((acc | vis) == ~0ull) break;
-                    }
-                }
-                __syncwarp();
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, A, s_hist,
-                               false);
-            }
-            // A2: medium nodes, one warp per node.
-            for (int64_t t = gwarp; t < J.nM; t += nwarps) {
-                const int v = J.Mlist[t];
-                const uint64_t visw = J.vis[(int64_t)v * W + w];
-                if (__all_sync(FULL, visw == ~0ull)) continue;
-                const int64_t b = rp[v], e = rp[v + 1];
-                uint64_t acc = 0;
-                for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
-                    const uint64_t r = or_same_word<W>(acc);
-                    if (__all_sync(FULL, (r | visw) == ~0ull)) break;
-                }
-                const uint64_t r = or_same_word<W>(acc);
-                tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, A, s_hist,
-                               false);
-            }
-            // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
-            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
-                const int v = J.Hch_node[t];
-                const int64_t vw = (int64_t)v * W + w;
-                const int64_t b = J.Hch_begin[t];
-                const int64_t e = min(b + (int64_t)kChunk, rp[v + 1]);
-                const uint64_t visw = J.vis[vw];
-                const uint64_t cur = J.nxt[vw];
-                if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
-                uint64_t acc = 0;
-                for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
-                    const uint64_t r = or_same_word<W>(acc);
-                    if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
-                }
-                const uint64_t r = or_same_word<W>(acc);
-                const uint64_t nbits = r & ~visw & ~cur;
-                if (lane < W && nbits)
-                    atomicOr((unsigned long long *)&J.nxt[vw], nbits);
-            }
-            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-            // B: finalise the heavy nodes.
-            for (int64_t t = gwarp; t * NPW < J.nH; t += nwarps) {
-                const int64_t li = t * NPW + grp;
-                const bool valid = li < J.nH;
-                const int v = valid ? J.Hlist[li] : 0;
-                const int64_t vw = (int64_t)v * W + w;
-                uint64_t vis = ~0ull, acc = 0;
-                int64_t deg = 0;
-                if (valid) {
-                    vis = J.vis[vw];
-                    acc = J.nxt[vw];
-                    if (acc) J.nxt[vw] = 0;
-                    deg = rp[v + 1] - rp[v];
-                }
-                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, false);
-            }
-            trace_words(ctl, l, A.words - words_before);
-            flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(ctl, nb, J.timeout_ns)) return;
-            if (gtid == 0) ctl->bu_levels += 1;
-            prev_td = false;
-        }
-    }
-    // Pass statistics.
-    __shared__ unsigned long long s_red[kBlock / 32];
-    const unsigned long long words = block_sum64(A.words, s_red);
-    if (tid == 0) atomicAdd(&ctl->words, words);
-    if (gtid == 0) {
-        ctl->levels = last;
-        ctl->ninc_final = ninc;
-        ctl->lvl_ns[l < kTraceLevels ? l : kTraceLevels] = gtimer();
-    }
+    bfs_pass<W>(J, blockIdx.x, gridDim.x, J.ctl, s_hist);
 }
 
 __global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t timeout_ns)
