@@ -224,6 +224,49 @@ int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
                                int32_t *d_pivot, uint32_t *d_delta,
                                uint64_t *d_S_sampled, void *stream);
 
+/* ---- batches: many graphs in one persistent launch ------------------------- */
+typedef struct cc_batch *cc_batch_t;
+
+/*
+ * cc_batch_create -- prepare all-nodes estimates (sections 2-3, every
+ * estimator) for ngraphs resident unweighted undirected graphs at once.
+ *   graphs[i]      handles (must outlive the batch)
+ *   samples[i]     host int32[ks[i]] distinct node ids of graph i
+ *   ks[i]          1 <= k <= 512
+ *   eps_num/den    per-graph hybrid eps (NULL: 1/round(sqrt(k)))
+ *   autotune       1: time every graph alone once, then choose the team
+ *                  count by a cost model and by timing the best plans;
+ *                  0: plan from CSR sizes only
+ * The run is one cooperative launch covering the GPU: its CTAs form equal
+ * teams, each team estimating its graphs one after another with team-wide
+ * bounded barriers.  The launch (and its memsets) is captured in a CUDA
+ * graph on the first run when the runtime allows it.  Device memory for
+ * every graph's state and results is owned by the batch.
+ * Errors: CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA.
+ */
+int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs,
+                    const int32_t *const *samples, const int32_t *ks,
+                    const uint32_t *eps_num, const uint32_t *eps_den,
+                    int32_t autotune, cc_batch_t *out);
+
+/* One batched run on `stream` (cudaStream_t or NULL); synchronous.  Returns
+ * the first per-graph error (CC_ERR_DISCONNECTED, CC_ERR_TOO_LARGE when a
+ * graph needs more than 8191 levels, CC_ERR_TIMEOUT) or CC_OK. */
+int cc_batch_run(cc_batch_t b, void *stream);
+
+/* Copy graph i's results of the last run into `out` (host pointers, or
+ * device pointers with device_outputs = 1); same fields as cc_estimate. */
+int cc_batch_result(cc_batch_t b, int32_t i, const cc_out *out,
+                    int32_t device_outputs);
+
+/* Plan and timing of the last run: team count, CTAs in the launch, device
+ * time of the last run in ms (CUDA events around the launch), whether the
+ * run replayed a captured CUDA graph.  Any pointer may be NULL. */
+int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
+                  int32_t *graph_captured);
+
+int cc_batch_free(cc_batch_t b);
+
 /* ---- tuning ---------------------------------------------------------------- */
 /* Direction switch of the breadth-first traversal of one graph (0 restores
  * the default 14): a level runs top-down while (CSR entries of the

@@ -34,7 +34,8 @@ EXPORTS = (
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
-    "cc_set_tuning",
+    "cc_set_tuning", "cc_batch_create", "cc_batch_run", "cc_batch_result",
+    "cc_batch_info", "cc_batch_free",
     "cc_selftest_barrier_timeout", "cc_strerror",
 )
 
@@ -87,6 +88,11 @@ def lib():
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
         L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
         L.cc_set_tuning.argtypes = [P, i32]
+        L.cc_batch_create.argtypes = [i32, P, P, P, P, P, i32, P]
+        L.cc_batch_run.argtypes = [P, P]
+        L.cc_batch_result.argtypes = [P, i32, P, i32]
+        L.cc_batch_info.argtypes = [P, P, P, P, P]
+        L.cc_batch_free.argtypes = [P]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
@@ -276,3 +282,56 @@ def cc_sampling_pivots_noalloc(n, d_row_ptr, d_col, sample, d_sample_sum, d_pivo
 
 def cc_selftest_barrier_timeout(timeout_ns):
     return lib().cc_selftest_barrier_timeout(ctypes.c_uint64(int(timeout_ns)))
+
+
+# ---------------------------------------------------------------- batches
+
+def cc_batch_create(graphs, samples, eps=None, autotune=True):
+    """graphs: list of handles; samples: list of int32 arrays; eps: list of
+    (num, den) or None."""
+    ng = len(graphs)
+    hs = (ctypes.c_void_p * ng)(*graphs)
+    arrs = [np.ascontiguousarray(s, dtype=np.int32) for s in samples]
+    ptrs = (ctypes.c_void_p * ng)(*[a.ctypes.data for a in arrs])
+    ks = np.array([a.size for a in arrs], dtype=np.int32)
+    num = den = None
+    if eps is not None:
+        num = np.array([e[0] for e in eps], dtype=np.uint32)
+        den = np.array([e[1] for e in eps], dtype=np.uint32)
+    b = ctypes.c_void_p()
+    _chk(lib().cc_batch_create(ng, hs, ptrs, _p(ks), _p(num), _p(den), int(autotune),
+                               ctypes.byref(b)), "cc_batch_create")
+    return b.value
+
+
+def cc_batch_run(b, stream=None):
+    _chk(lib().cc_batch_run(b, stream), "cc_batch_run")
+
+
+def cc_batch_result(b, i, n, k):
+    """Host copies of graph i's results (same dict as cc_estimate)."""
+    res = dict(s_hat=np.zeros((CC_NUM_EST, n)), closeness=np.zeros((CC_NUM_EST, n)),
+               pivot=np.empty(n, np.int32), delta=np.empty(n, np.uint32),
+               sum=np.empty(n, np.uint64), hyb=np.zeros((n, 6), np.uint64),
+               S_samp=np.empty(k, np.uint64), delta_cc=np.empty((k, k), np.uint32))
+    o = cc_out()
+    for e in range(CC_NUM_EST):
+        o.s_hat[e] = _p(res["s_hat"][e])
+        o.closeness[e] = _p(res["closeness"][e])
+    o.pivot, o.delta = _p(res["pivot"]), _p(res["delta"])
+    o.sample_sum, o.hyb_int = _p(res["sum"]), _p(res["hyb"])
+    o.S_sampled, o.delta_cc = _p(res["S_samp"]), _p(res["delta_cc"])
+    _chk(lib().cc_batch_result(b, int(i), ctypes.byref(o), 0), "cc_batch_result")
+    return res
+
+
+def cc_batch_info(b):
+    t, g, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_double()
+    _chk(lib().cc_batch_info(b, ctypes.byref(t), ctypes.byref(g), ctypes.byref(ms),
+                             ctypes.byref(c)), "cc_batch_info")
+    return dict(teams=t.value, grid=g.value, last_ms=ms.value, graph_captured=bool(c.value))
+
+
+def cc_batch_free(b):
+    _chk(lib().cc_batch_free(b), "cc_batch_free")

@@ -586,6 +586,32 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
     return CC_OK;
 }
 
+}  // namespace
+
+int ccg::graph_view(cc_graph_t g, GraphView *v)
+{
+    if (!g || !v) return CC_ERR_ARG;
+    v->n = g->n;
+    v->arcs = g->arcs;
+    v->directed = g->directed;
+    v->weighted = g->weighted;
+    v->rp = g->fw.rp.as<int64_t>();
+    v->col = g->fw.col.as<int32_t>();
+    v->L = g->fw.cls.L.as<int32_t>();
+    v->M = g->fw.cls.M.as<int32_t>();
+    v->H = g->fw.cls.H.as<int32_t>();
+    v->Hn = g->fw.cls.Hn.as<int32_t>();
+    v->Hb = g->fw.cls.Hb.as<int64_t>();
+    v->nL = g->fw.cls.nL;
+    v->nM = g->fw.cls.nM;
+    v->nH = g->fw.cls.nH;
+    v->nHch = g->fw.cls.nHch;
+    v->alpha = g->alpha;
+    return CC_OK;
+}
+
+namespace {
+
 int device_ok()
 {
     int n = 0;

@@ -97,6 +97,19 @@ int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used);
 
 int launch_barrier_selftest(uint64_t timeout_ns, int *err_out);
 
+// Device view of a resident graph (forward CSR and its degree classes).
+struct GraphView {
+    int64_t n, arcs;
+    bool directed, weighted;
+    const int64_t *rp;
+    const int32_t *col;
+    const int32_t *L, *M, *H, *Hn;
+    const int64_t *Hb;
+    int64_t nL, nM, nH, nHch;
+    int alpha;
+};
+int graph_view(cc_graph_t g, GraphView *v);
+
 // Host-built CSR (the "graph to CSR" step).
 struct HostCSR {
     int64_t n = 0;

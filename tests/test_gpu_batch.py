@@ -1,0 +1,69 @@
+"""Batched persistent launch: every graph's results equal the single-graph
+path's bit for bit (and the oracle's, on the smaller graphs), twice in a
+row, with and without autotuning."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cc():
+    from paper_1409_0035_gb300 import build
+    build.build()
+    import paper_1409_0035_gb300 as m
+    return m
+
+
+def mixed_batch():
+    gens = [synth.rmat_edges(9, 8, seed=1), synth.rmat_edges(11, 16, seed=2),
+            synth.grid_edges(40, 25), synth.grid_edges(9, 7),
+            synth.watts_strogatz_edges(1500, 10, 0.05, seed=3),
+            synth.rmat_edges(8, 12, seed=4), synth.path_edges(400),
+            synth.star_edges(600), synth.rmat_edges(12, 8, seed=5),
+            synth.watts_strogatz_edges(4096, 10, 0.05, seed=6)]
+    ks = [16, 64, 256, 20, 512, 3, 64, 100, 256, 64]
+    return gens, ks
+
+
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_matches_single(cc, autotune):
+    gens, ks = mixed_batch()
+    handles, samples, olds, ns = [], [], [], []
+    try:
+        for (n, s, d), k in zip(gens, ks):
+            g, old = cc.cc_graph_from_edges(n, s, d)
+            handles.append(g)
+            nn = cc.cc_graph_info(g)[0]
+            ns.append(nn)
+            samples.append(cc.cc_sample_choose(g, min(k, nn), 7 + k))
+        b = cc.cc_batch_create(handles, samples, autotune=autotune)
+        try:
+            info = cc.cc_batch_info(b)
+            assert 1 <= info["teams"] <= 64
+            for rep in range(2):
+                cc.cc_batch_run(b)
+                for i, g in enumerate(handles):
+                    got = cc.cc_batch_result(b, i, ns[i], len(samples[i]))
+                    want = cc.cc_estimate(g, samples[i])
+                    for key in want:
+                        assert (got[key] == want[key]).all(), (i, key)
+            info = cc.cc_batch_info(b)
+            assert info["last_ms"] > 0
+        finally:
+            cc.cc_batch_free(b)
+        # oracle on two of the graphs
+        for i in (0, 3):
+            n, s, d = gens[i]
+            og = orc.csr_from_edges(n, s, d)
+            k = len(samples[i])
+            want = orc.estimate(og, samples[i], eps=orc.default_eps(k))
+            got = cc.cc_estimate(handles[i], samples[i])
+            assert (got["hyb"] == want["hyb"]).all()
+            assert np.allclose(got["s_hat"], want["s_hat"], rtol=1e-12, atol=0)
+    finally:
+        for g in handles:
+            cc.cc_graph_free(g)
