@@ -271,12 +271,17 @@ __global__ void k_hook(const int64_t *rp, const int32_t *col, int64_t n, int32_t
     }
 }
 
-__global__ void k_flatten_count(int32_t *parent, int64_t n, uint32_t *size)
+// Component label = root, found with reads only (a concurrent path-halving
+// write could otherwise replace a freshly written root by a non-root
+// ancestor).
+__global__ void k_label_count(const int32_t *parent, int64_t n, int32_t *label,
+                              uint32_t *size)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r = find_root(parent, (int32_t)v);
-        parent[v] = r;
+        int32_t r = (int32_t)v;
+        while (parent[r] != r) r = parent[r];
+        label[v] = r;
         atomicAdd(&size[r], 1u);
     }
 }
@@ -314,16 +319,21 @@ __global__ void k_kept_deg(const int64_t *rp, const uint64_t *flags, const uint6
     }
 }
 
+// A neighbour outside the kept component cannot occur for a correct
+// labelling; it is reported rather than written.
 __global__ void k_rewrite_rows(const int64_t *rp, const int32_t *col, const uint32_t *w,
                                const int32_t *old_id, const int32_t *newid,
-                               const uint64_t *nrp, int64_t nk, int32_t *ncol, uint32_t *nw)
+                               const uint64_t *nrp, int64_t nk, int32_t *ncol, uint32_t *nw,
+                               int *err)
 {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nk;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = old_id[x];
         int64_t o = (int64_t)nrp[x];
         for (int64_t e = rp[v]; e < rp[v + 1]; ++e, ++o) {
-            ncol[o] = newid[col[e]];
+            const int32_t y = newid[col[e]];
+            if (y < 0) atomicExch(err, CC_ERR_GRAPH);
+            ncol[o] = y < 0 ? 0 : y;
             if (w) nw[o] = w[e];
         }
     }
@@ -449,8 +459,9 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
     G_RC(v0.alloc(A0 * 4));
     G_RC(k1.alloc(A0 * 8));
     G_RC(v1.alloc(A0 * 4));
-    G_RC(fl.alloc(A0 * 8));
-    G_RC(pos.alloc((A0 + 1) * 8));
+    const int64_t F = std::max<int64_t>(A0, n) + 1;  // flags over arcs or nodes
+    G_RC(fl.alloc(F * 8));
+    G_RC(pos.alloc(F * 8));
     G_RC(err.alloc(4));
     if (m > 0) {
         G_CK(cudaMemcpy(dsrc.p, h_src, m * 4, cudaMemcpyHostToDevice));
@@ -499,7 +510,7 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
     if (A2 > 0) k_heads<<<gsz(A2), 256, 0, st>>>(ko, (int64_t)A2, b, col.as<int32_t>());
     uint32_t *wv = vo;  // merged lengths, in arc order
     int64_t nk = n;
-    Buf nrp, ncol, nw, parent, size, newid, oldid, degs, best;
+    Buf nrp, ncol, nw, parent, label, size, newid, oldid, degs, best;
     int64_t *frp = rp.as<int64_t>();
     int32_t *fcol = col.as<int32_t>();
     uint32_t *fw = h_w ? wv : nullptr;
@@ -512,14 +523,16 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
         G_CK(cudaMemset(best.p, 0, 8));
         k_iota32<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n);
         k_hook<<<gsz(n), 256, 0, st>>>(frp, fcol, n, parent.as<int32_t>());
-        k_flatten_count<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, size.as<uint32_t>());
+        G_RC(label.alloc(n * 4));
+        k_label_count<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, label.as<int32_t>(),
+                                              size.as<uint32_t>());
         k_pick<<<gsz(n), 256, 0, st>>>(size.as<uint32_t>(), n,
                                        best.as<unsigned long long>());
         unsigned long long hb = 0;
         G_CK(cudaMemcpy(&hb, best.p, 8, cudaMemcpyDeviceToHost));
         const int32_t root = (int32_t)(0xFFFFFFFFull - (hb & 0xFFFFFFFFull));
         // 6. renumber the kept nodes and rewrite their rows
-        k_keep_flags<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, root, fl.as<uint64_t>());
+        k_keep_flags<<<gsz(n), 256, 0, st>>>(label.as<int32_t>(), n, root, fl.as<uint64_t>());
         uint64_t kept = 0;
         G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), n, &kept, st));
         nk = (int64_t)kept;
@@ -541,7 +554,9 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
         k_rewrite_rows<<<gsz(nk), 256, 0, st>>>(frp, fcol, fw, oldid.as<int32_t>(),
                                                 newid.as<int32_t>(), degs.as<uint64_t>(), nk,
                                                 ncol.as<int32_t>(),
-                                                h_w ? nw.as<uint32_t>() : nullptr);
+                                                h_w ? nw.as<uint32_t>() : nullptr, err.as<int>());
+        G_CK(cudaMemcpy(&herr, err.p, 4, cudaMemcpyDeviceToHost));
+        if (herr) return herr;
         out.arcs = (int64_t)arcs;
         out.old_id.resize(nk);
         G_CK(cudaMemcpy(out.old_id.data(), oldid.p, nk * 4, cudaMemcpyDeviceToHost));
