@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--cpu-sources", type=int, default=12,
                     help="sources in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat20",
+                    choices=["rmat20", "config1", "batch64", "road4m", "rt22"],
+                    help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
 
@@ -165,18 +168,31 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def kernel_traffic(path_json):
+def kernel_source_sha():
+    """sha256 over the traversal kernel's sources."""
+    h = hashlib.sha256()
+    for f in ("msbfs_dev.cuh", "msbfs.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1409_0035_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(path_md):
     """Per-launch DRAM bytes from the committed ncu summary, only while the
     kernel source is unchanged since the capture."""
+    meta = {}
     try:
-        meta = json.load(open(path_json))
-    except (OSError, ValueError):
+        for line in open(path_md):
+            if ":" in line and line.strip().startswith(("source_sha256", "dram_bytes_per_launch")):
+                k, v = line.split(":", 1)
+                meta[k.strip()] = v.strip().strip("`")
+    except OSError:
         return None
-    src = os.path.join(ROOT, "paper_1409_0035_gb300", "csrc", "msbfs.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if meta.get("source_sha256") != sha:
+    if meta.get("source_sha256") != kernel_source_sha():
         return None
-    return meta.get("dram_bytes_per_launch")
+    try:
+        return float(meta["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def run_ours(args):
@@ -305,8 +321,7 @@ def run_ours(args):
     per_launch_bytes = kbytes / max(1, klaunch)
     per_launch_ms = kms / max(1, klaunch)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = kernel_traffic(os.path.join(ROOT, "profiles",
-                                          "msbfs_rmat20_k256.json"))
+    traffic = kernel_traffic(os.path.join(ROOT, "profiles", "msbfs_rmat20_k256.md"))
     gpu_launches = kall
 
     line = {"metric": "source-edge traversals/s (GTEPS)", "value": value,
@@ -346,10 +361,138 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------- other configs
+
+def _time_steps(fn, steps, warmup, flush=None):
+    """Device time (ms) of `steps` calls of fn after `warmup` calls, CUDA
+    events on the current stream, L2 flushed before each timed call."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def batch64_graphs(master=7):
+    """32 R-MAT (scale 10..18, edge factor 8..16), 16 square grids (side
+    64..1024), 16 Watts-Strogatz (n = 2^12..2^16, degree 10, p = 0.05); per
+    graph k in {16, 64, 256, 512}; all draws from splitmix64(master, i)."""
+    import synth
+    u = lambda i: float(synth.uniform_at(master, [i])[0])
+    out = []
+    for g in range(64):
+        kind = "rmat" if g < 32 else ("grid" if g < 48 else "ws")
+        k = (16, 64, 256, 512)[min(3, int(u(4 * g) * 4))]
+        if kind == "rmat":
+            scale = 10 + min(8, int(u(4 * g + 1) * 9))
+            ef = 8 + min(8, int(u(4 * g + 2) * 9))
+            e = synth.rmat_edges(scale, ef, seed=1000 + g)
+            desc = f"rmat s{scale} ef{ef}"
+        elif kind == "grid":
+            side = 64 + int(u(4 * g + 1) * (1024 - 64 + 1))
+            e = synth.grid_edges(side, side)
+            desc = f"grid {side}"
+        else:
+            ln = 12 + min(4, int(u(4 * g + 1) * 5))
+            e = synth.watts_strogatz_edges(1 << ln, 10, 0.05, seed=2000 + g)
+            desc = f"ws 2^{ln}"
+        out.append((desc, e, k))
+    return out
+
+
+def run_extra(args):
+    import numpy as np
+    import torch
+    from paper_1409_0035_gb300 import build as ccbuild
+    ccbuild.build()
+    import paper_1409_0035_gb300 as cc
+    import synth
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    line = {"metric": "source-edge traversals/s (GTEPS)", "unit": "GTEPS",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "workload": args.workload}
+    if args.workload == "batch64":
+        specs = batch64_graphs()
+        handles, samples, work, kinds = [], [], 0, []
+        for i, (desc, (n, s, d), k) in enumerate(specs):
+            g, _ = cc.cc_graph_from_edges(n, s, d)
+            nn, arcs, _, _ = cc.cc_graph_info(g)
+            k = min(k, nn)
+            handles.append(g)
+            samples.append(cc.cc_sample_choose(g, k, 3000 + i))
+            work += k * (arcs // 2)
+            kinds.append(desc)
+        b = cc.cc_batch_create(handles, samples, autotune=True)
+        ms = _time_steps(lambda: cc.cc_batch_run(b), args.steps, args.warmup, flush)
+        info = cc.cc_batch_info(b)
+        seq = 0.0
+        for g, C in zip(handles, samples):
+            seq += _time_steps(lambda: cc.cc_estimate(g, C), 1, 1)
+        line.update(value=work / (ms / 1e3) / 1e9, ms_per_step=ms,
+                    sequential={"value": work / (seq / 1e3) / 1e9, "ms": seq},
+                    speedup_vs_sequential=seq / ms, plan=info,
+                    config={"workload": "batch64", "graphs": kinds,
+                            "source_edges": work})
+        cc.cc_batch_free(b)
+        for g in handles:
+            cc.cc_graph_free(g)
+    elif args.workload in ("road4m", "rt22", "config1"):
+        if args.workload == "road4m":
+            n, s, d, length = synth.road_like_edges(4 << 20, seed=1)
+            variants = [("round(1000 len)+1", synth.edge_lengths_to_weights(length, 1e3)),
+                        ("round(1e6 len)+1", synth.edge_lengths_to_weights(length, 1e6))]
+            k, directed = 64, False
+        elif args.workload == "rt22":
+            n, s, d = synth.rmat_edges(22, 16, seed=1)
+            variants = [("unit", None)]
+            k, directed = 128, True
+        else:
+            n, s, d = synth.rmat_edges(12, 8, seed=1)
+            variants = [("unit", None)]
+            k, directed = 64, False
+        results = []
+        for name, w in variants:
+            g, _ = cc.cc_graph_from_edges(n, s, d, w, directed=directed)
+            nn, arcs, _, _ = cc.cc_graph_info(g)
+            m = arcs if directed else arcs // 2
+            C = cc.cc_sample_choose(g, k, 2)
+            o = cc.cc_opts_default(k)
+            o.roundtrip = int(directed)
+            ms = _time_steps(lambda: cc.cc_estimate(g, C, o), args.steps, args.warmup, flush)
+            units = k * m * (2 if directed else 1)
+            r = {"weights": name, "n": nn, "m": m, "k": k, "ms_per_step": ms,
+                 "value": units / (ms / 1e3) / 1e9,
+                 "kernel_launches": cc.cc_last_call_timing(g)[0],
+                 "levels_or_rounds": cc.cc_last_pass_stats(g)["levels"]}
+            if args.workload == "config1":
+                t0 = time.perf_counter()
+                cc.cc_exact(g)
+                r["exact_all_pairs_s"] = time.perf_counter() - t0
+            results.append(r)
+            cc.cc_graph_free(g)
+        line.update(value=results[0]["value"], ms_per_step=results[0]["ms_per_step"],
+                    variants=results, config={"workload": args.workload})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "rmat20":
+        run_extra(args)
     else:
         run_ours(args)
 

@@ -13,6 +13,7 @@ from .graphs import (  # noqa: F401
     grid_edges,
     watts_strogatz_edges,
     rgg_edges,
+    road_like_edges,
     path_edges,
     star_edges,
     cycle_edges,

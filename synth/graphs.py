@@ -182,3 +182,30 @@ def complete_edges(n: int):
     """Complete graph K_n (each pair once)."""
     iu, ju = np.triu_indices(n, 1)
     return n, iu.astype(np.uint32), ju.astype(np.uint32)
+
+
+def road_like_edges(n: int, mean_degree: float = 2.6, gen_degree: float = 5.0, seed=1):
+    """Road-like graph: a random geometric graph on the unit square generated
+    at mean degree `gen_degree` (above the 2-D percolation threshold, so one
+    component spans the square), thinned to about `mean_degree`: a random
+    spanning forest (minimum spanning forest under the random keys
+    uniform_at(seed + 2, e)) is always kept and every other edge is kept with
+    the probability that brings the mean degree to `mean_degree` (draw
+    uniform_at(seed + 3, e)).  Returns (n, src, dst, length)."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import minimum_spanning_tree
+
+    radius = float(np.sqrt(gen_degree / (np.pi * n)))
+    n, src, dst, length = rgg_edges(n, radius, seed=seed)
+    m = src.size
+    key = uniform_at(seed + 2, np.arange(m, dtype=np.uint64)) + 1e-9
+    g = coo_matrix((key, (src.astype(np.int64), dst.astype(np.int64))), shape=(n, n))
+    forest = minimum_spanning_tree(g.tocsr()).tocoo()
+    fpair = np.minimum(forest.row, forest.col).astype(np.int64) * n + \
+        np.maximum(forest.row, forest.col).astype(np.int64)
+    upair = np.minimum(src, dst).astype(np.int64) * n + np.maximum(src, dst).astype(np.int64)
+    in_forest = np.isin(upair, fpair)
+    extra_needed = max(0.0, mean_degree * n / 2.0 - in_forest.sum())
+    q = min(1.0, extra_needed / max(1, (~in_forest).sum()))
+    keep = in_forest | (uniform_at(seed + 3, np.arange(m, dtype=np.uint64)) < q)
+    return n, src[keep], dst[keep], length[keep]
