@@ -1,0 +1,73 @@
+// Bounded two-level barrier over the CTAs of a team (all co-resident: the
+// kernels using it are cooperative launches).
+//
+// CTA r arrives on group counter r % G (G = min(32, team size)); the last
+// arrival of a group resets that counter and arrives on the top counter; the
+// last top arrival resets it and advances the generation that every CTA
+// waits on.  Spreading the arrivals over G counters avoids serialising
+// hundreds of atomics on one address.  A wait that runs past timeout_ns
+// records CC_ERR_TIMEOUT, and every CTA stops waiting as soon as the team
+// reports a negative error code.
+#pragma once
+#include <cstdint>
+
+#include "cc_internal.h"
+
+namespace ccg {
+namespace {
+
+__device__ __forceinline__ uint64_t bar_clock()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false (in every thread of the CTA) when the wait ran out or the
+// team reported an error.
+__device__ bool grid_sync(Ctl *ctl, unsigned rank, unsigned nblocks, uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = &ctl->bar_gen;
+        volatile int *verr = &ctl->err;
+        const unsigned g = *vgen;
+        const unsigned G = nblocks < (unsigned)kBarGroups ? nblocks : (unsigned)kBarGroups;
+        const unsigned grp = rank % G;
+        const unsigned gsize = nblocks / G + (grp < nblocks % G ? 1u : 0u);
+        __threadfence();
+        if (atomicAdd(&ctl->bar_sub[grp], 1u) == gsize - 1) {
+            atomicExch(&ctl->bar_sub[grp], 0u);
+            __threadfence();
+            if (atomicAdd(&ctl->bar_count, 1u) == G - 1) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                atomicAdd(&ctl->bar_gen, 1u);
+            }
+        }
+        if (*vgen == g) {
+            const uint64_t t0 = bar_clock();
+            unsigned ns = 8;
+            while (*vgen == g) {
+                if (*verr < 0) { ok = 0; break; }
+                if (bar_clock() - t0 > timeout_ns) {
+                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 128) ns <<= 1;
+            }
+        }
+        __threadfence();
+        if (*verr < 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace
+}  // namespace ccg

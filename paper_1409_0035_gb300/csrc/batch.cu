@@ -13,8 +13,8 @@
 // The team count and the graph-to-team assignment come from a planner:
 // with autotuning it times every graph once alone (whole GPU), models a
 // graph's time on a team of s CTAs as levels * c + work * G / s, assigns
-// graphs to P teams longest-first for P in {1, 2, ..., 64}, then times the
-// best few plans for real and keeps the fastest.  The launch and its
+// graphs to P teams longest-first for P in {1, 2, ..., 64}, then times every
+// plan for real and keeps the fastest.  The launch and its
 // memsets are captured once in a CUDA graph and replayed on every run.
 #include <algorithm>
 #include <cmath>
@@ -66,12 +66,12 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
     const uint64_t to = B.j.timeout_ns;
     int32_t *sidx = const_cast<int32_t *>(B.j.sidx);
     d_fill_i32(sidx, n, -1, gtid, gthreads);
-    if (!grid_sync(bar, size, to)) return;
+    if (!grid_sync(bar, rank, size, to)) return;
     d_scatter_sidx(sidx, B.j.sources, k, gtid, gthreads);
-    if (!grid_sync(bar, size, to)) return;
+    if (!grid_sync(bar, rank, size, to)) return;
 
     bfs_pass<W>(B.j, rank, size, bar, s_hist);
-    if (!grid_sync(bar, size, to)) return;
+    if (!grid_sync(bar, rank, size, to)) return;
     volatile Ctl *c1 = B.ctl1;
     if (c1->ninc_final != 0 || c1->err != 0) {
         if (gtid == 0) *B.status = c1->err == 1 ? CC_ERR_TOO_LARGE
@@ -85,20 +85,20 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
         for (int i = (int)rank; i < k; i += (int)size)
             d_tail_source(B.hist, D, k, B.TN, B.TS, i);
         d_maxdelta(B.j.dcc, k, B.maxd, gtid, gthreads);
-        if (!grid_sync(bar, size, to)) return;
+        if (!grid_sync(bar, rank, size, to)) return;
         d_hyb_prep(3, n, k, D, B.a, B.b, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.maxd,
                    B.TN, B.TS, B.hp, B.npartial, gtid, gthreads);
-        if (!grid_sync(bar, size, to)) return;
+        if (!grid_sync(bar, rank, size, to)) return;
         if (*(volatile unsigned *)B.npartial > 0) {
             d_lmask(n, W, k, B.j.sidx, B.j.pivot, B.j.dcc, B.hp, B.Lmask, gtid, gthreads);
-            if (!grid_sync(bar, size, to)) return;
+            if (!grid_sync(bar, rank, size, to)) return;
             BfsJob j2 = B.j;
             j2.red = RED_LC;
             j2.Lmask = B.Lmask;
             j2.lc2 = B.lc2;
             j2.ctl = B.ctl2;
             bfs_pass<W>(j2, rank, size, bar, s_hist);
-            if (!grid_sync(bar, size, to)) return;
+            if (!grid_sync(bar, rank, size, to)) return;
         }
     }
     FinalizeArgs fa;
@@ -119,7 +119,7 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
     fa.hyb_int = B.want_hybrid ? B.hyb : nullptr;
     fa.sample_sum = nullptr;
     d_finalize(fa, gtid, gthreads);
-    if (!grid_sync(bar, size, to)) return;
+    if (!grid_sync(bar, rank, size, to)) return;
     if (gtid == 0) *B.status = CC_OK;
 }
 
@@ -480,7 +480,9 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
             b->levels[i] = 8;
         }
     }
-    // Model every team count; with autotuning time the three best for real.
+    // Model every team count; with autotuning time every plan for real (the
+    // model cannot tell work-bound from latency-bound graphs, whose level
+    // time does not shrink with more CTAs).
     std::vector<std::pair<double, int>> cand;
     for (int P = 1; P <= P_max; P *= 2) {
         std::vector<int> t;
@@ -490,7 +492,7 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
     int bestP = cand[0].second;
     if (autotune) {
         double best = 1e300;
-        for (size_t c = 0; c < std::min<size_t>(3, cand.size()); ++c) {
+        for (size_t c = 0; c < cand.size(); ++c) {
             std::vector<int> t;
             plan(b, cand[c].second, t);
             B_RC(upload_plan(b, cand[c].second, t));

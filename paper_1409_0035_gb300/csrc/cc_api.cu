@@ -373,10 +373,24 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 }
 
 // One 32-source chunk of shortest paths (forward, and reversed for round
-// trips) into g->distF / g->distR.
+// trips) into g->distF / g->distR.  Unit lengths use the bit-packed
+// traversal writing levels; arc lengths the label-correcting kernel.
 int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, cudaStream_t st)
 {
     const int64_t n = g->n;
+    if (!g->weighted) {
+        RC(ensure_state(g, 1));
+        for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
+            BfsJob j = base_job(g, 1, dir ? g->rv : g->fw);
+            j.k = kc;
+            j.sources = d_sources;
+            j.red = RED_LEVELS;
+            j.dist_out = (dir ? g->distR : g->distF).as<uint32_t>();
+            RC(run_pass(g, 1, j, st));
+            if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
+        }
+        return CC_OK;
+    }
     for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
         const DevCSR &c = dir ? g->rv : g->fw;
         SsspJob j;

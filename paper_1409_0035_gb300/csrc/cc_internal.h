@@ -23,6 +23,7 @@ enum : uint32_t {
     RED_DCC = 4u,    // delta_cc[i][j] for sampled nodes
     RED_HIST = 8u,   // per-source level histogram over V \ C
     RED_LC = 16u,    // hybrid pass: lc[v] += d, d^2 over sources in Lmask(v)
+    RED_LEVELS = 32u, // k <= 32: dist_out[v * 32 + i] = level of v from source i
 };
 
 // Per-level statistics, indexed by level mod 4 (written during level l,
@@ -39,6 +40,7 @@ struct LevelCtl {
 };
 
 constexpr int kTraceLevels = 64;
+constexpr int kBarGroups = 32;  // arrival counters of the two-level barrier
 
 struct Ctl {
     unsigned int bar_count;
@@ -49,6 +51,7 @@ struct Ctl {
     unsigned long long td_levels, bu_levels;
     unsigned long long edges, words;  // CSR entries examined, words gathered
     LevelCtl lev[4];
+    unsigned int bar_sub[kBarGroups];
     // Trace of the first kTraceLevels levels: global timer at the start of
     // each level (and at the end of the pass), direction and frontier size.
     unsigned long long lvl_ns[kTraceLevels + 1];
@@ -86,6 +89,7 @@ struct BfsJob {
     int hist_cap;
     const uint64_t *Lmask;  // n*W
     uint64_t *lc2;          // n x 2: {LCsum, LCsumSq}
+    uint32_t *dist_out;     // RED_LEVELS: n x 32 chunk of levels
     Ctl *ctl;
     uint64_t timeout_ns;
     int alpha;              // top-down while ef * alpha < eu

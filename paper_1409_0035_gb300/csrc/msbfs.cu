@@ -44,7 +44,7 @@ __global__ void barrier_selftest_kernel(Ctl *ctl, uint64_t timeout_ns)
 {
     // A team of two CTAs of which only one is launched: the barrier cannot
     // complete and must give up after timeout_ns.
-    grid_sync(ctl, 2u, timeout_ns);
+    grid_sync(ctl, 0u, 2u, timeout_ns);
 }
 
 template <int W>

@@ -5,6 +5,7 @@
 #pragma once
 #include <cstdint>
 
+#include "barrier.cuh"
 #include "cc_internal.h"
 
 namespace ccg {
@@ -29,47 +30,6 @@ __device__ __forceinline__ uint64_t pad_mask(int k, int w)
     if (k <= lo) return ~0ull;
     if (k >= lo + 64) return 0ull;
     return ~0ull << (k - lo);
-}
-
-// Barrier over the `nblocks` CTAs of a team with a bounded wait.  Returns
-// false (in every thread of the CTA) when the wait ran out or another CTA of
-// the team reported an error (a negative code).  Same arrival/generation scheme as a cooperative-groups grid
-// sync, with a time limit.
-__device__ bool grid_sync(Ctl *ctl, unsigned nblocks, uint64_t timeout_ns)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *vgen = &ctl->bar_gen;
-        volatile int *verr = &ctl->err;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const uint64_t t0 = gtimer();
-            unsigned ns = 8;
-            while (*vgen == g) {
-                if (*verr < 0) { ok = 0; break; }
-                if (gtimer() - t0 > timeout_ns) {
-                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
-            }
-        }
-        __threadfence();
-        if (*verr < 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 // 32 x 32 bit-matrix transpose across a warp: on return lane c holds, in
@@ -156,6 +116,14 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         }
     }
     if (leader && clear_tflag) J.tflag[v] = 0u;
+    if ((J.red & RED_LEVELS) && valid && nw) {
+        uint64_t b = nw;
+        while (b) {
+            const int i = w * 64 + __ffsll((long long)b) - 1;
+            b &= b - 1;
+            J.dist_out[(int64_t)v * 32 + i] = (uint32_t)l;
+        }
+    }
     if ((J.red & RED_DCC) && sx >= 0 && nw) {
         uint64_t b = nw;
         while (b) {
@@ -437,7 +405,9 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         J.fstamp[v] = kInf;
     }
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
-    if (!grid_sync(bar, nb, J.timeout_ns)) return;
+    if (J.red & RED_LEVELS)
+        for (int64_t i = gtid; i < n * 32; i += gthreads) J.dist_out[i] = kInf;
+    if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
     for (int64_t i = gtid; i < J.k; i += gthreads) {
         const int v = J.sources[i];
         const uint64_t bit = 1ull << (i & 63);
@@ -445,6 +415,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         atomicOr((unsigned long long *)&J.vis[vw], bit);
         atomicOr((unsigned long long *)&J.F0[vw], bit);
         J.fstamp[v] = 0u;
+        if (J.red & RED_LEVELS) J.dist_out[(int64_t)v * 32 + i] = 0u;
         if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
         if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
         const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);
@@ -458,7 +429,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         ctl->lev[0].qlen = (unsigned)J.k;
         ctl->lev[0].tlen = (unsigned)J.k;  // level 0 "touched" the sources
     }
-    if (!grid_sync(bar, nb, J.timeout_ns)) return;
+    if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
 
     long long eu = J.arcs, ninc = n;
     int last = 0;
@@ -511,7 +482,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 block_compact(
                     n, [&](int64_t i) { return J.fstamp[i] == want; },
                     [&](int64_t i) { return (int32_t)i; }, J.Q0, &C->qcnt, team_rank, team_size);
-                if (!grid_sync(bar, nb, J.timeout_ns)) return;
+                if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
                 Qin = J.Q0;
                 qn = ((volatile LevelCtl *)C)->qcnt;
             }
@@ -533,7 +504,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const int64_t b = J.Hch_begin[t];
                 td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A);
             }
-            if (!grid_sync(bar, nb, J.timeout_ns)) return;
+            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
             // P2: finalise the touched nodes.
             const int64_t tl = ((volatile LevelCtl *)C)->tlen;
             for (int64_t t = gwarp; t * NPW < tl; t += nwarps) {
@@ -553,7 +524,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(bar, nb, J.timeout_ns)) return;
+            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->td_levels += 1;
             prev_td = true;
             prevT = Tout;
@@ -572,7 +543,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                         return inc;
                     },
                     [&](int64_t i) { return ALin[i]; }, ALout, &C->alen, team_rank, team_size);
-                if (!grid_sync(bar, nb, J.timeout_ns)) return;
+                if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
                 ALcur = ALout;
                 al_len = ((volatile LevelCtl *)C)->alen;
                 al_next ^= 1;
@@ -633,7 +604,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 if (lane < W && nbits)
                     atomicOr((unsigned long long *)&J.nxt[vw], nbits);
             }
-            if (!grid_sync(bar, nb, J.timeout_ns)) return;
+            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
             // B: finalise the heavy nodes.
             for (int64_t t = gwarp; t * NPW < J.nH; t += nwarps) {
                 const int64_t li = t * NPW + grp;
@@ -652,7 +623,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(bar, nb, J.timeout_ns)) return;
+            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
             if (gtid == 0) ctl->bu_levels += 1;
             prev_td = false;
         }

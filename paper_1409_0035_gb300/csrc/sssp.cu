@@ -18,6 +18,7 @@
 // either one distance matrix or the pair.
 #include <cstdint>
 
+#include "barrier.cuh"
 #include "cc_internal.h"
 #include "sssp.h"
 
@@ -34,44 +35,6 @@ __device__ __forceinline__ uint64_t gtimer()
     return t;
 }
 
-// Bounded grid barrier (same scheme as the traversal kernel's).
-__device__ bool grid_sync2(Ctl *ctl, unsigned nblocks, uint64_t timeout_ns)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *vgen = &ctl->bar_gen;
-        volatile int *verr = &ctl->err;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const uint64_t t0 = gtimer();
-            unsigned ns = 8;
-            while (*vgen == g) {
-                if (*verr < 0) { ok = 0; break; }
-                if (gtimer() - t0 > timeout_ns) {
-                    atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
-            }
-        }
-        __threadfence();
-        if (*verr < 0) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
 {
     const int lane = threadIdx.x & 31;
@@ -85,7 +48,7 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
 
     for (int64_t i = gtid; i < n * kChunkSrc; i += gthreads) J.dist[i] = kInf;
     for (int64_t v = gtid; v < n; v += gthreads) J.mask[v] = 0u;
-    if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+    if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     if (gtid < J.kc) {
         const int v = J.sources[gtid];
         J.dist[(int64_t)v * kChunkSrc + gtid] = 0u;
@@ -94,7 +57,7 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
             J.Q0[p] = v;
         }
     }
-    if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+    if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
 
     int r = 0;
     for (;; ++r) {
@@ -137,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                 }
             }
         }
-        if (!grid_sync2(ctl, nb, J.timeout_ns)) return;
+        if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     }
     __shared__ unsigned long long s_rel[kBlock / 32];
     for (int o = 16; o >= 1; o >>= 1) relax += __shfl_xor_sync(FULL, relax, o);
