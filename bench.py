@@ -438,11 +438,21 @@ def run_extra(args):
         ms = _time_steps(lambda: cc.cc_batch_run(b), args.steps, args.warmup, flush)
         info = cc.cc_batch_info(b)
         seq = 0.0
-        for g, C in zip(handles, samples):
-            seq += _time_steps(lambda: cc.cc_estimate(g, C), 1, 1)
+        per = []
+        for g, C, desc in zip(handles, samples, kinds):
+            t = _time_steps(lambda: cc.cc_estimate(g, C), 1, 1)
+            seq += t
+            per.append((t, desc, len(C), cc.cc_last_pass_stats(g)["levels"]))
+        per.sort(reverse=True)
+        by_kind = {}
+        for t, desc, k, lv in per:
+            by_kind[desc.split()[0]] = by_kind.get(desc.split()[0], 0.0) + t
         line.update(value=work / (ms / 1e3) / 1e9, ms_per_step=ms,
                     sequential={"value": work / (seq / 1e3) / 1e9, "ms": seq},
                     speedup_vs_sequential=seq / ms, plan=info,
+                    sequential_ms_by_kind=by_kind,
+                    slowest=[{"graph": d, "k": k, "levels": lv, "ms": t}
+                             for t, d, k, lv in per[:6]],
                     config={"workload": "batch64", "graphs": kinds,
                             "source_edges": work})
         cc.cc_batch_free(b)

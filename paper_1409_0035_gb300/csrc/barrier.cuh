@@ -69,5 +69,37 @@ __device__ bool grid_sync(Ctl *ctl, unsigned rank, unsigned nblocks, uint64_t ti
     return s_ok != 0;
 }
 
+// Per-CTA staging of queue appends: appends go to shared memory and the
+// CTA reserves its slots in the global queue with one atomicAdd when it
+// flushes, instead of one global atomic per appended node.
+constexpr int kStage = 1024;
+
+struct Stage {
+    int32_t *buf;      // shared, kStage entries
+    unsigned *count;   // shared
+    unsigned *base;    // shared
+};
+
+__device__ __forceinline__ void stage_push(const Stage &s, int32_t v, int32_t *gq,
+                                           unsigned *glen)
+{
+    const unsigned p = atomicAdd(s.count, 1u);
+    if (p < (unsigned)kStage) s.buf[p] = v;
+    else gq[atomicAdd(glen, 1u)] = v;  // stage full: append directly
+}
+
+// Called by every thread of the CTA; leaves the stage empty.
+__device__ __forceinline__ void stage_flush(const Stage &s, int32_t *gq, unsigned *glen)
+{
+    __syncthreads();
+    const unsigned m = min(*s.count, (unsigned)kStage);
+    if (threadIdx.x == 0) *s.base = m ? atomicAdd(glen, m) : 0u;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < m; i += blockDim.x) gq[*s.base + i] = s.buf[i];
+    __syncthreads();
+    if (threadIdx.x == 0) *s.count = 0;
+    __syncthreads();
+}
+
 }  // namespace
 }  // namespace ccg

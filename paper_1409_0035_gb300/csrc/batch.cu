@@ -397,6 +397,8 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         j.Llist = v.L; j.Mlist = v.M; j.Hlist = v.H;
         j.nL = v.nL; j.nM = v.nM; j.nH = v.nH;
         j.Hch_node = v.Hn; j.Hch_begin = v.Hb; j.nHch = v.nHch;
+        j.tHn = v.Hn; j.tHb = v.Hb; j.ntH = v.nHch;
+        j.prp = v.rp; j.pcol = v.col;
         void *p[20];
         p[0] = take(n * W * 8); p[1] = take(n * W * 8); p[2] = take(n * W * 8);
         p[3] = take(n * W * 8); p[4] = take(n * 4); p[5] = take(n * 4); p[6] = take(n * 4);

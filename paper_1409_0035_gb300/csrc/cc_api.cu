@@ -161,14 +161,23 @@ int ensure_state(cc_graph *g, int W)
     return CC_OK;
 }
 
-BfsJob base_job(cc_graph *g, int W, const DevCSR &csr)
+// Pass over `push` (top-down, arcs leaving a node) and `pull` (bottom-up,
+// arcs entering a node): the same CSR for undirected graphs; G and G^T for
+// a forward pass on a directed graph, G^T and G for a reverse pass.
+BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
 {
+    const DevCSR &csr = pull;
     BfsJob j;
     std::memset(&j, 0, sizeof(j));
     j.n = g->n;
     j.arcs = g->arcs;
-    j.rp = csr.rp.as<int64_t>();
-    j.col = csr.col.as<int32_t>();
+    j.rp = push.rp.as<int64_t>();
+    j.col = push.col.as<int32_t>();
+    j.tHn = push.cls.Hn.as<int32_t>();
+    j.tHb = push.cls.Hb.as<int64_t>();
+    j.ntH = push.cls.nHch;
+    j.prp = pull.rp.as<int64_t>();
+    j.pcol = pull.col.as<int32_t>();
     j.Llist = csr.cls.L.as<int32_t>();
     j.Mlist = csr.cls.M.as<int32_t>();
     j.Hlist = csr.cls.H.as<int32_t>();
@@ -310,7 +319,7 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     const int W = pow2_words(k);
     RC(ensure_state(g, W));
     if (g->hist_cap == 0) g->hist_cap = (int)std::min<int64_t>(n + 1, 4096);
-    BfsJob j = base_job(g, W, g->fw);
+    BfsJob j = base_job(g, W, g->fw, g->fw);
     j.k = k;
     j.sources = g->sources.as<int32_t>();
     j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
@@ -363,7 +372,7 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
               g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
     g->call_kernels += 1;
     CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
-    BfsJob j2 = base_job(g, W, g->fw);
+    BfsJob j2 = base_job(g, W, g->fw, g->fw);
     j2.k = k;
     j2.sources = g->sources.as<int32_t>();
     j2.red = RED_LC;
@@ -381,7 +390,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, cudaStream_t st)
     if (!g->weighted) {
         RC(ensure_state(g, 1));
         for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
-            BfsJob j = base_job(g, 1, dir ? g->rv : g->fw);
+            BfsJob j = base_job(g, 1, dir ? g->rv : g->fw, dir ? g->fw : g->rv);
             j.k = kc;
             j.sources = d_sources;
             j.red = RED_LEVELS;
@@ -900,7 +909,7 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
             for (int i = 0; i < kk; ++i) src[i] = (int32_t)(base + i);
             CK(cudaMemcpyAsync(g->sources.p, src.data(), (size_t)kk * 4,
                                cudaMemcpyHostToDevice, st));
-            BfsJob j = base_job(g, W, g->fw);
+            BfsJob j = base_job(g, W, g->fw, g->fw);
             j.k = kk;
             j.sources = g->sources.as<int32_t>();
             j.red = RED_SUM;
@@ -936,7 +945,7 @@ int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k, uint
     std::vector<uint64_t> Sh(k, 0);
     std::vector<uint32_t> hist;
     for (int i = 0; i < k; ++i) {
-        BfsJob j = base_job(g, 1, g->fw);
+        BfsJob j = base_job(g, 1, g->fw, g->fw);
         j.k = 1;
         j.sources = g->sources.as<int32_t>() + i;
         j.red = RED_SUM | (S_sampled ? RED_HIST : 0u);

@@ -64,8 +64,17 @@ struct Ctl {
 // One traversal pass over one graph.
 struct BfsJob {
     int64_t n, arcs;
+    // Top-down pushes along (rp, col) -- the arcs leaving a node -- with
+    // 256-arc tasks (tHn, tHb) for its heavy nodes; bottom-up pulls along
+    // (prp, pcol) -- the arcs entering a node -- whose degree classes are
+    // Llist/Mlist/Hlist/Hch.  Both are the same CSR for undirected graphs.
     const int64_t *rp;
     const int32_t *col;
+    const int32_t *tHn;
+    const int64_t *tHb;
+    int64_t ntH;
+    const int64_t *prp;
+    const int32_t *pcol;
     int k;                  // sources in this pass
     const int32_t *sources; // k node ids
     const int32_t *sidx;    // n: sample index or -1 (pass-level sample)

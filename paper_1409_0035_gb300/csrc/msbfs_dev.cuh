@@ -327,7 +327,7 @@ __device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsig
 template <int W>
 __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restrict__ col,
                                         uint64_t f, int64_t b, int64_t e, LevelCtl *C,
-                                        int32_t *Tout, LaneAcc<W> &A)
+                                        int32_t *Tout, LaneAcc<W> &A, const Stage &stage)
 {
     constexpr int NPW = 32 / W;
     const int lane = threadIdx.x & 31;
@@ -354,14 +354,8 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
             if (!nbits) continue;
             const uint64_t old =
                 atomicOr((unsigned long long *)&J.nxt[(int64_t)v * W + w], nbits);
-            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u) {
-                const unsigned m = __activemask();
-                const int first = __ffs(m) - 1;
-                unsigned pos = 0;
-                if (lane == first) pos = atomicAdd(&C->tlen, (unsigned)__popc(m));
-                pos = __shfl_sync(m, pos, first);
-                Tout[pos + __popc(m & ((1u << lane) - 1u))] = v;
-            }
+            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u)
+                stage_push(stage, v, Tout, &C->tlen);
         }
     }
 }
@@ -383,9 +377,16 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     const int64_t n = J.n;
     const int64_t *rp = J.rp;
     const int32_t *col = J.col;
+    const int64_t *prp = J.prp;
+    const int32_t *pcol = J.pcol;
     Ctl *ctl = J.ctl;
     const unsigned nb = team_size;
     const bool doHist = (J.red & RED_HIST) != 0;
+
+    __shared__ int32_t s_buf[kStage];
+    __shared__ unsigned s_cnt, s_base;
+    const Stage stage{s_buf, &s_cnt, &s_base};
+    if (threadIdx.x == 0) s_cnt = 0;
 
     LaneAcc<W> A;
 #pragma unroll
@@ -492,18 +493,20 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             for (int64_t t = gwarp; t < qn; t += nwarps) {
                 const int u = Qin[t];
                 const int64_t b = rp[u], e = rp[u + 1];
-                if (J.nHch > 0 && e - b > kMediumMaxDeg) continue;
+                if (J.ntH > 0 && e - b > kMediumMaxDeg) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
-                td_push<W>(J, col, f, b, e, C, Tout, A);
+                td_push<W>(J, col, f, b, e, C, Tout, A, stage);
             }
-            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
-                const int u = J.Hch_node[t];
+            for (int64_t t = gwarp; t < J.ntH; t += nwarps) {
+                const int u = J.tHn[t];
                 if (J.fstamp[u] != (unsigned)(l - 1)) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
                 if (__all_sync(FULL, f == 0ull)) continue;
-                const int64_t b = J.Hch_begin[t];
-                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A);
+                const int64_t b = J.tHb[t];
+                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A,
+                           stage);
             }
+            stage_flush(stage, Tout, &C->tlen);
             if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
             // P2: finalise the touched nodes.
             const int64_t tl = ((volatile LevelCtl *)C)->tlen;
@@ -518,7 +521,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                     vis = J.vis[vw];
                     acc = J.nxt[vw];
                     if (acc) J.nxt[vw] = 0;
-                    deg = rp[v + 1] - rp[v];
+                    deg = prp[v + 1] - prp[v];
                 }
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, true);
             }
@@ -556,11 +559,11 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = valid ? J.vis[vw] : ~0ull;
                 int64_t b = 0, e = 0;
-                if (valid) { b = rp[v]; e = rp[v + 1]; }
+                if (valid) { b = prp[v]; e = prp[v + 1]; }
                 uint64_t acc = 0;
                 if (vis != ~0ull) {
                     for (int64_t x = b; x < e; x += kUnroll) {
-                        acc |= gather_or<W, kUnroll>(col, Fin, x, e, 1, w, A.words);
+                        acc |= gather_or<W, kUnroll>(pcol, Fin, x, e, 1, w, A.words);
                         if ((acc | vis) == ~0ull) break;
                     }
                 }
@@ -573,10 +576,10 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const int v = J.Mlist[t];
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
                 if (__all_sync(FULL, visw == ~0ull)) continue;
-                const int64_t b = rp[v], e = rp[v + 1];
+                const int64_t b = prp[v], e = prp[v + 1];
                 uint64_t acc = 0;
                 for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
+                    acc |= gather_or<W, kUnroll>(pcol, Fin, base + grp, e, NPW, w, A.words);
                     const uint64_t r = or_same_word<W>(acc);
                     if (__all_sync(FULL, (r | visw) == ~0ull)) break;
                 }
@@ -589,13 +592,13 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const int v = J.Hch_node[t];
                 const int64_t vw = (int64_t)v * W + w;
                 const int64_t b = J.Hch_begin[t];
-                const int64_t e = min(b + (int64_t)kChunk, rp[v + 1]);
+                const int64_t e = min(b + (int64_t)kChunk, prp[v + 1]);
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
                 uint64_t acc = 0;
                 for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(col, Fin, base + grp, e, NPW, w, A.words);
+                    acc |= gather_or<W, kUnroll>(pcol, Fin, base + grp, e, NPW, w, A.words);
                     const uint64_t r = or_same_word<W>(acc);
                     if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
                 }
@@ -617,7 +620,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                     vis = J.vis[vw];
                     acc = J.nxt[vw];
                     if (acc) J.nxt[vw] = 0;
-                    deg = rp[v + 1] - rp[v];
+                    deg = prp[v + 1] - prp[v];
                 }
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, false);
             }

@@ -206,6 +206,8 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     j.arcs = arcs;
     j.rp = d_row_ptr;
     j.col = d_col;
+    j.prp = d_row_ptr;
+    j.pcol = d_col;
     j.k = k;
     j.sources = src;
     j.sidx = sidx;

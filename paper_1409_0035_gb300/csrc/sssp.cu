@@ -28,13 +28,6 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
 {
     const int lane = threadIdx.x & 31;
@@ -45,6 +38,10 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
     Ctl *ctl = J.ctl;
     const unsigned nb = gridDim.x;
     unsigned long long relax = 0;
+    __shared__ int32_t s_buf[kStage];
+    __shared__ unsigned s_cnt, s_base;
+    const Stage stage{s_buf, &s_cnt, &s_base};
+    if (threadIdx.x == 0) s_cnt = 0;
 
     for (int64_t i = gtid; i < n * kChunkSrc; i += gthreads) J.dist[i] = kInf;
     for (int64_t v = gtid; v < n; v += gthreads) J.mask[v] = 0u;
@@ -94,12 +91,11 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                     }
                 }
                 const unsigned bits = __ballot_sync(FULL, imp);
-                if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u) {
-                    const unsigned p = atomicAdd(qout_len, 1u);
-                    Qout[p] = v;
-                }
+                if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u)
+                    stage_push(stage, v, Qout, qout_len);
             }
         }
+        stage_flush(stage, Qout, qout_len);
         if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     }
     __shared__ unsigned long long s_rel[kBlock / 32];
