@@ -47,8 +47,11 @@ def parse():
     ap.add_argument("--cpu-sources", type=int, default=12,
                     help="sources in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=300,
+                    help="serve workload: requests in the Poisson stream")
+    ap.add_argument("--slots", type=int, default=8, help="serve workload: slots")
     ap.add_argument("--workload", default="rmat20",
-                    choices=["rmat20", "config1", "batch64", "road4m", "rt22"],
+                    choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve"],
                     help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
@@ -411,6 +414,76 @@ def batch64_graphs(master=7):
     return out
 
 
+def serve_pool():
+    """40 resident graphs: R-MAT scale 12 + (i mod 11), edge factor 16, for
+    i < 20; square grids with side 256 * 2^(i mod 5) for the other 20."""
+    import synth
+    pool = []
+    for i in range(40):
+        if i < 20:
+            scale = 12 + (i % 11)
+            pool.append((f"rmat s{scale}", synth.rmat_edges(scale, 16, seed=500 + i)))
+        else:
+            side = 256 << (i % 5)
+            pool.append((f"grid {side}", synth.grid_edges(side, side)))
+    return pool
+
+
+def run_serve(args, cc):
+    """Poisson arrivals (200 requests/s, seed 3) of (graph, estimator, k)
+    requests over the resident pool; continuous batching in the server."""
+    import numpy as np
+    import synth
+    pool = serve_pool()
+    handles, ns, ms_ = [], [], []
+    for desc, (n, s, d) in pool:
+        g, _ = cc.cc_graph_from_edges(n, s, d)
+        nn, arcs, _, _ = cc.cc_graph_info(g)
+        handles.append(g)
+        ns.append(nn)
+        ms_.append(arcs // 2)
+    R = args.requests
+    c = np.arange(4 * R, dtype=np.uint64)
+    u = synth.uniform_at(3, c)
+    gaps = -np.log1p(-u[0::4]) / 200.0
+    gsel = np.minimum((u[1::4] * 40).astype(int), 39)
+    est = (0, 1, 3)  # sampling, pivoting, hybrid
+    esel = [est[min(2, int(x * 3))] for x in u[2::4]]
+    ksel = [(64, 128, 256, 512, 1024)[min(4, int(x * 5))] for x in u[3::4]]
+    srv = cc.cc_server_create(handles, slots=args.slots)
+    t0 = time.perf_counter()
+    ids, t_next = [], t0
+    for i in range(R):
+        t_next += gaps[i]
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        k = min(ksel[i], ns[gsel[i]])
+        ids.append((cc.cc_server_submit(srv, int(gsel[i]), esel[i], k, 7000 + i), i, k))
+    work, est_nodes, lat = 0, 0, []
+    for rid, i, k in ids:
+        st = cc.cc_server_wait(srv, rid, 600000)
+        if st != cc.CC_OK:
+            raise RuntimeError(f"request {i} failed: {cc.cc_strerror(st)}")
+        r = cc.cc_server_result(srv, rid, ns[gsel[i]])
+        lat.append(r["latency_ms"])
+        work += k * ms_[gsel[i]]
+        est_nodes += ns[gsel[i]]
+    wall = time.perf_counter() - t0
+    stats = cc.cc_server_stats(srv)
+    cc.cc_server_free(srv)
+    for g in handles:
+        cc.cc_graph_free(g)
+    return {"value": work / wall / 1e9, "ms_per_step": wall * 1e3 / R,
+            "requests": R, "wall_s": wall, "requests_per_s": R / wall,
+            "offered_requests_per_s": 200.0, "estimates_per_s": est_nodes / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "server_stats": stats, "slots": args.slots,
+            "config": {"workload": "serve", "pool": [d for d, _ in pool],
+                       "arrivals": "Poisson 200/s, seed 3", "k": [64, 128, 256, 512, 1024],
+                       "estimators": ["sampling", "pivoting", "hybrid"]}}
+
+
 def run_extra(args):
     import numpy as np
     import torch
@@ -423,7 +496,9 @@ def run_extra(args):
     line = {"metric": "source-edge traversals/s (GTEPS)", "unit": "GTEPS",
             "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "data": "synthetic", "workload": args.workload}
-    if args.workload == "batch64":
+    if args.workload == "serve":
+        line.update(run_serve(args, cc))
+    elif args.workload == "batch64":
         specs = batch64_graphs()
         handles, samples, work, kinds = [], [], 0, []
         for i, (desc, (n, s, d), k) in enumerate(specs):

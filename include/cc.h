@@ -267,6 +267,51 @@ int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
 
 int cc_batch_free(cc_batch_t b);
 
+/* ---- serving ------------------------------------------------------------------ */
+typedef struct cc_server *cc_server_t;
+
+/*
+ * cc_server_create -- serve all-nodes estimates (section 2 estimators) over a
+ * pool of resident graphs with continuous batching.
+ *   graphs        handles kept resident (must outlive the server)
+ *   slots         1..64 concurrent requests; each slot has a worker thread,
+ *                 a CUDA stream and its own workspace, and its launches use
+ *                 at most 1/slots of the GPU's CTAs so that slots overlap
+ *   hbm_budget    bytes of device memory the running requests may use
+ *                 (0: half of the free memory at creation)
+ * A submitted request waits, first come first served, until a slot is free
+ * and its footprint fits in the budget left by the running ones.
+ */
+int cc_server_create(int32_t ngraphs, const cc_graph_t *graphs, int32_t slots,
+                     uint64_t hbm_budget, cc_server_t *out);
+
+/* Queue a request: graph index, estimator (CC_EST_*), k, sample seed (the
+ * sample is cc_sample_choose's), eps = eps_num/eps_den.  Non-blocking;
+ * returns its id.  CC_ERR_TOO_LARGE when it could never fit the budget. */
+int cc_server_submit(cc_server_t s, int32_t graph, int32_t estimator, int32_t k,
+                     uint64_t seed, uint32_t eps_num, uint32_t eps_den,
+                     int64_t *request_id);
+
+/* Wait up to timeout_ms for a request: CC_OK when done, its error code when
+ * it failed, CC_ERR_TIMEOUT when still waiting or running. */
+int cc_server_wait(cc_server_t s, int64_t request_id, int32_t timeout_ms);
+
+/* Copy a finished request's results (host arrays of the graph's n nodes,
+ * each may be NULL: the requested estimator's S estimate and closeness,
+ * pivot, Delta, sum of distances to the sample) and its latency from
+ * submission to completion in ms; releases the request. */
+int cc_server_result(cc_server_t s, int64_t request_id, double *s_hat,
+                     double *closeness, int32_t *pivot, uint32_t *delta,
+                     uint64_t *sample_sum, double *latency_ms);
+
+/* Latency statistics over the completed requests (ms, submission to
+ * completion) and the largest number of requests that ran at once. */
+int cc_server_stats(cc_server_t s, int64_t *completed, double *p50_ms,
+                    double *p99_ms, double *mean_ms, int32_t *peak_running);
+
+/* Drain the queue, stop the workers and release the server. */
+int cc_server_free(cc_server_t s);
+
 /* ---- tuning ---------------------------------------------------------------- */
 /* Direction switch of the breadth-first traversal of one graph (0 restores
  * the default 14): a level runs top-down while (CSR entries of the

@@ -35,7 +35,8 @@ EXPORTS = (
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
     "cc_set_tuning", "cc_batch_create", "cc_batch_run", "cc_batch_result",
-    "cc_batch_info", "cc_batch_free",
+    "cc_batch_info", "cc_batch_free", "cc_server_create", "cc_server_submit",
+    "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror",
 )
 
@@ -93,6 +94,12 @@ def lib():
         L.cc_batch_result.argtypes = [P, i32, P, i32]
         L.cc_batch_info.argtypes = [P, P, P, P, P]
         L.cc_batch_free.argtypes = [P]
+        L.cc_server_create.argtypes = [i32, P, i32, u64, P]
+        L.cc_server_submit.argtypes = [P, i32, i32, i32, u64, ctypes.c_uint32, ctypes.c_uint32, P]
+        L.cc_server_wait.argtypes = [P, i64, i32]
+        L.cc_server_result.argtypes = [P, i64, P, P, P, P, P, P]
+        L.cc_server_stats.argtypes = [P, P, P, P, P, P]
+        L.cc_server_free.argtypes = [P]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
         L.cc_strerror.argtypes = [c_int]
@@ -335,3 +342,51 @@ def cc_batch_info(b):
 
 def cc_batch_free(b):
     _chk(lib().cc_batch_free(b), "cc_batch_free")
+
+
+# ---------------------------------------------------------------- serving
+
+def cc_server_create(graphs, slots=4, hbm_budget=0):
+    hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    h = ctypes.c_void_p()
+    _chk(lib().cc_server_create(len(graphs), hs, int(slots), ctypes.c_uint64(hbm_budget),
+                                ctypes.byref(h)), "cc_server_create")
+    return h.value
+
+
+def cc_server_submit(s, graph, estimator, k, seed, eps=None):
+    a, b = eps if eps is not None else (1, max(1, int(round(k ** 0.5))))
+    rid = ctypes.c_int64()
+    _chk(lib().cc_server_submit(s, int(graph), int(estimator), int(k),
+                                ctypes.c_uint64(seed & (2**64 - 1)), a, b, ctypes.byref(rid)),
+         "cc_server_submit")
+    return rid.value
+
+
+def cc_server_wait(s, rid, timeout_ms=60000):
+    """Returns the status code (CC_OK, an error, or CC_ERR_TIMEOUT)."""
+    return lib().cc_server_wait(s, int(rid), int(timeout_ms))
+
+
+def cc_server_result(s, rid, n):
+    out = dict(s_hat=np.empty(n), closeness=np.empty(n), pivot=np.empty(n, np.int32),
+               delta=np.empty(n, np.uint32), sum=np.empty(n, np.uint64))
+    lat = ctypes.c_double()
+    _chk(lib().cc_server_result(s, int(rid), _p(out["s_hat"]), _p(out["closeness"]),
+                                _p(out["pivot"]), _p(out["delta"]), _p(out["sum"]),
+                                ctypes.byref(lat)), "cc_server_result")
+    out["latency_ms"] = lat.value
+    return out
+
+
+def cc_server_stats(s):
+    c, pk = ctypes.c_int64(), ctypes.c_int32()
+    p50, p99, mean = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _chk(lib().cc_server_stats(s, ctypes.byref(c), ctypes.byref(p50), ctypes.byref(p99),
+                               ctypes.byref(mean), ctypes.byref(pk)), "cc_server_stats")
+    return dict(completed=c.value, p50_ms=p50.value, p99_ms=p99.value, mean_ms=mean.value,
+                peak_running=pk.value)
+
+
+def cc_server_free(s):
+    _chk(lib().cc_server_free(s), "cc_server_free")

@@ -68,6 +68,8 @@ struct cc_graph {
         distF, distR, mask, best, dmax, errflag, AL0, AL1, fstamp;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = kAlpha;  // traversal tuning
+    int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
+    bool borrowed = false;  // CSR buffers belong to another handle
     int hist_cap = 0;
     Ctl last{};
     // Traversal launches of the last API call: count, device time (CUDA
@@ -203,6 +205,7 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
     j.ctl = g->ctl.as<Ctl>();
     j.timeout_ns = kTimeoutNs;
     j.alpha = g->alpha;
+    j.max_ctas = g->max_ctas;
     (void)W;
     return j;
 }
@@ -294,6 +297,13 @@ int adopt_device_csr(cc_graph *g, DeviceCSR &d)
 
 void free_graph(cc_graph *g)
 {
+    if (g->borrowed) {  // drop the borrowed CSR pointers unfreed
+        DevBuf *csr[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
+                         &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->rv.rp, &g->rv.col,
+                         &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
+                         &g->rv.cls.Hb};
+        for (DevBuf *b : csr) { b->p = nullptr; b->cap = 0; }
+    }
     DevBuf *all[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
                      &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->rv.rp, &g->rv.col,
                      &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
@@ -416,6 +426,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, cudaStream_t st)
         j.Q1 = g->Q1.as<int32_t>();
         j.ctl = g->ctl.as<Ctl>();
         j.timeout_ns = kTimeoutNs;
+        j.max_ctas = g->max_ctas;
         if (!g->ev0) {
             CK(cudaEventCreate(&g->ev0));
             CK(cudaEventCreate(&g->ev1));
@@ -610,6 +621,46 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
 }
 
 }  // namespace
+
+// Point `dst` (a handle with its own workspace) at the resident CSR of
+// `src`, borrowing it: used by the server's slots.
+int ccg::graph_borrow(cc_graph_t dst, cc_graph_t src)
+{
+    if (!dst || !src) return CC_ERR_ARG;
+    dst->n = src->n;
+    dst->arcs = src->arcs;
+    dst->directed = src->directed;
+    dst->weighted = src->weighted;
+    auto cp = [](DevBuf &d, const DevBuf &s) { d.p = s.p; d.cap = s.cap; };
+    cp(dst->fw.rp, src->fw.rp); cp(dst->fw.col, src->fw.col); cp(dst->fw.w, src->fw.w);
+    cp(dst->rv.rp, src->rv.rp); cp(dst->rv.col, src->rv.col); cp(dst->rv.w, src->rv.w);
+    for (int d = 0; d < 2; ++d) {
+        Classes &c = d ? dst->rv.cls : dst->fw.cls;
+        const Classes &s = d ? src->rv.cls : src->fw.cls;
+        cp(c.L, s.L); cp(c.M, s.M); cp(c.H, s.H); cp(c.Hn, s.Hn); cp(c.Hb, s.Hb);
+        c.nL = s.nL; c.nM = s.nM; c.nH = s.nH; c.nHch = s.nHch;
+    }
+    dst->alpha = src->alpha;
+    dst->borrowed = true;
+    return CC_OK;
+}
+
+cc_graph_t ccg::graph_new_empty() { return new (std::nothrow) cc_graph(); }
+
+size_t ccg::graph_workspace_bytes(cc_graph_t g)
+{
+    const DevBuf *ws[] = {&g->vis, &g->F0, &g->F1, &g->nxt, &g->Q0, &g->Q1, &g->T, &g->tflag,
+                          &g->sidx, &g->sum2, &g->pivot, &g->delta, &g->lc2, &g->Lmask, &g->hp,
+                          &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp, &g->maxd, &g->sources,
+                          &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
+                          &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
+                          &g->AL0, &g->AL1, &g->fstamp};
+    size_t t = 0;
+    for (const DevBuf *b : ws) t += b->cap;
+    return t;
+}
+
+void ccg::graph_set_max_ctas(cc_graph_t g, int c) { g->max_ctas = c; }
 
 int ccg::graph_view(cc_graph_t g, GraphView *v)
 {

@@ -102,6 +102,7 @@ struct BfsJob {
     Ctl *ctl;
     uint64_t timeout_ns;
     int alpha;              // top-down while ef * alpha < eu
+    int max_ctas;           // 0: a whole-GPU launch; else at most this many CTAs
 };
 
 // Launch one cooperative traversal pass (W = words per node, power of two
@@ -122,6 +123,16 @@ struct GraphView {
     int alpha;
 };
 int graph_view(cc_graph_t g, GraphView *v);
+// Server slots: an empty handle whose workspace persists, pointed at the
+// resident CSR of another handle per request.
+cc_graph_t graph_new_empty();
+int graph_borrow(cc_graph_t dst, cc_graph_t src);
+size_t graph_workspace_bytes(cc_graph_t g);
+void graph_set_max_ctas(cc_graph_t g, int ctas);
+// Sample choice with caller-provided device buffers (no allocation).
+int choose_sample_ws(int64_t n, int k, uint64_t seed, int32_t *host_out, void *cand,
+                     unsigned *count, int32_t *dout, cudaStream_t st);
+size_t sample_candidate_bytes();
 
 // Host-built CSR (the "graph to CSR" step).
 struct HostCSR {

@@ -63,7 +63,8 @@ int launch_w(const BfsJob &job, cudaStream_t st, int *grid_used)
             return CC_ERR_CUDA;
         if (blocks_per_sm < 1) return CC_ERR_CUDA;
     }
-    const int grid = blocks_per_sm * sms;
+    int grid = blocks_per_sm * sms;
+    if (job.max_ctas > 0 && job.max_ctas < grid) grid = job.max_ctas;
     if (grid_used) *grid_used = grid;
     BfsJob j = job;
     void *args[] = {&j};

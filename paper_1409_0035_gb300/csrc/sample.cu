@@ -81,29 +81,24 @@ k_sort_take(const Cand *buf, const unsigned *count, int k, int32_t *out)
 
 }  // namespace
 
-int choose_sample_device(int64_t n, int k, uint64_t seed, int32_t *host_out)
+size_t sample_candidate_bytes() { return sizeof(Cand) * kCap; }
+
+int choose_sample_ws(int64_t n, int k, uint64_t seed, int32_t *host_out, void *cand_buf,
+                     unsigned *cnt, int32_t *dout, cudaStream_t st)
 {
-    Cand *buf = nullptr;
-    unsigned *cnt = nullptr;
-    int32_t *dout = nullptr;
+    Cand *buf = static_cast<Cand *>(cand_buf);
     int rc = CC_ERR_TOO_LARGE;  // until a selection succeeds
-    if (cudaMalloc(&buf, sizeof(Cand) * kCap) != cudaSuccess ||
-        cudaMalloc(&cnt, 4) != cudaSuccess || cudaMalloc(&dout, (size_t)k * 4) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(buf); cudaFree(cnt); cudaFree(dout);
-        return CC_ERR_OOM;
-    }
     // Expected candidates: n * thr / 2^64.
     double frac = (2.0 * k + 64.0) / (double)n;
     for (int attempt = 0; attempt < 64; ++attempt) {
-        const uint64_t thr = frac >= 1.0 ? ~0ull
-                                         : (uint64_t)std::ldexp(frac, 64);
-        cudaMemset(cnt, 0, 4);
+        const uint64_t thr = frac >= 1.0 ? ~0ull : (uint64_t)std::ldexp(frac, 64);
+        if (cudaMemsetAsync(cnt, 0, 4, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
         int64_t grid = (n + 255) / 256;
         if (grid > 152 * 16) grid = 152 * 16;
-        k_candidates<<<(int)grid, 256>>>(n, seed, thr, buf, cnt);
+        k_candidates<<<(int)grid, 256, 0, st>>>(n, seed, thr, buf, cnt);
         unsigned c = 0;
-        if (cudaMemcpy(&c, cnt, 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
             rc = CC_ERR_CUDA;
             break;
         }
@@ -124,13 +119,30 @@ int choose_sample_device(int64_t n, int k, uint64_t seed, int32_t *host_out)
             rc = CC_ERR_CUDA;
             break;
         }
-        k_sort_take<<<1, kSortThreads, smem>>>(buf, cnt, k, dout);
-        rc = cudaMemcpy(host_out, dout, (size_t)k * 4, cudaMemcpyDeviceToHost) == cudaSuccess
+        k_sort_take<<<1, kSortThreads, smem, st>>>(buf, cnt, k, dout);
+        rc = cudaMemcpyAsync(host_out, dout, (size_t)k * 4, cudaMemcpyDeviceToHost, st) ==
+                             cudaSuccess &&
+                     cudaStreamSynchronize(st) == cudaSuccess
                  ? CC_OK
                  : CC_ERR_CUDA;
         break;
     }
     cudaGetLastError();
+    return rc;
+}
+
+int choose_sample_device(int64_t n, int k, uint64_t seed, int32_t *host_out)
+{
+    Cand *buf = nullptr;
+    unsigned *cnt = nullptr;
+    int32_t *dout = nullptr;
+    if (cudaMalloc(&buf, sizeof(Cand) * kCap) != cudaSuccess ||
+        cudaMalloc(&cnt, 4) != cudaSuccess || cudaMalloc(&dout, (size_t)k * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(buf); cudaFree(cnt); cudaFree(dout);
+        return CC_ERR_OOM;
+    }
+    const int rc = choose_sample_ws(n, k, seed, host_out, buf, cnt, dout, 0);
     cudaFree(buf);
     cudaFree(cnt);
     cudaFree(dout);

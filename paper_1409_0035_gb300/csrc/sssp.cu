@@ -231,7 +231,9 @@ int launch_mssp(const SsspJob &job, cudaStream_t st)
     }
     SsspJob j = job;
     void *args[] = {&j};
-    return cudaLaunchCooperativeKernel((const void *)mssp_kernel, dim3(blocks_per_sm * sms),
+    int grid = blocks_per_sm * sms;
+    if (job.max_ctas > 0 && job.max_ctas < grid) grid = job.max_ctas;
+    return cudaLaunchCooperativeKernel((const void *)mssp_kernel, dim3(grid),
                                        dim3(kBlock), args, 0, st) == cudaSuccess
                ? CC_OK
                : CC_ERR_CUDA;

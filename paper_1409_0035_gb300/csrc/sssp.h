@@ -22,6 +22,7 @@ struct SsspJob {
     int32_t *Q0, *Q1;       // n each
     Ctl *ctl;
     uint64_t timeout_ns;
+    int max_ctas;           // 0: a whole-GPU launch
 };
 
 struct ReduceJob {
