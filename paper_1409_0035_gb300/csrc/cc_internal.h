@@ -110,6 +110,10 @@ struct BfsJob {
 int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used);
 
 int launch_barrier_selftest(uint64_t timeout_ns, int *err_out);
+int msbfs_min_blocks_per_sm();
+int mssp_blocks_per_sm();
+void msbfs_set_carveout(int percent);
+void mssp_set_carveout(int percent);
 
 // Device view of a resident graph (forward CSR and its degree classes).
 struct GraphView {

@@ -89,6 +89,39 @@ int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used)
     }
 }
 
+// One shared-memory carveout for every traversal variant: an SM runs CTAs of
+// different kernels side by side only when they agree on the L1/shared split,
+// so persistent grids that share the GPU must not ask for different splits.
+void msbfs_set_carveout(int percent)
+{
+    const void *fns[] = {(const void *)msbfs_kernel<1>, (const void *)msbfs_kernel<2>,
+                         (const void *)msbfs_kernel<4>, (const void *)msbfs_kernel<8>,
+                         (const void *)msbfs_kernel<16>, (const void *)msbfs_kernel<32>};
+    for (const void *f : fns)
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, percent);
+    cudaGetLastError();
+}
+
+// Smallest number of co-resident CTAs per SM over every traversal variant.
+int msbfs_min_blocks_per_sm()
+{
+    int m = 1 << 30, b = 0;
+    const size_t kSmem[] = {64, 128, 256, 512, 1024, 2048};
+    const void *fns[] = {(const void *)msbfs_kernel<1>, (const void *)msbfs_kernel<2>,
+                         (const void *)msbfs_kernel<4>, (const void *)msbfs_kernel<8>,
+                         (const void *)msbfs_kernel<16>, (const void *)msbfs_kernel<32>};
+    for (int i = 0; i < 6; ++i) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fns[i], kBlock,
+                                                          kSmem[i] * sizeof(unsigned)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        m = b < m ? b : m;
+    }
+    return m < 1 ? 1 : m;
+}
+
 int launch_barrier_selftest(uint64_t timeout_ns, int *err_out)
 {
     Ctl *d = nullptr;

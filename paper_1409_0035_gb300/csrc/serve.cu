@@ -6,8 +6,8 @@
 // and runs requests with continuous batching: S slots, each a worker thread
 // with its own CUDA stream and its own workspace (a handle that borrows the
 // requested graph's CSR), whose cooperative launches are capped at 1/S of
-// the GPU's CTAs so that the requests of different slots run on the device
-// at the same time.  A waiting request is admitted, first come first served,
+// the CTAs the GPU can hold of its least-resident kernel variant, so that
+// the grids of all slots fit on the device together and run concurrently.  A waiting request is admitted, first come first served,
 // as soon as a slot is free and its HBM footprint fits in what the running
 // requests leave of the budget.  Arrival, start and finish times give each
 // request's latency.
@@ -169,10 +169,19 @@ int cc_server_create(int32_t ngraphs, const cc_graph_t *graphs, int32_t slots,
         return CC_ERR_CUDA;
     }
     srv->budget = hbm_budget_bytes ? (size_t)hbm_budget_bytes : free_b / 2;
+    // Every slot's cooperative grid must fit on the GPU together with all
+    // the others: cap each at (SMs x the smallest residency of any variant)
+    // divided among the slots.
+    // The persistent kernels also get one common L1/shared split (a quarter
+    // of the unified memory is more than four CTAs of any of them use), so
+    // that CTAs of different slots' kernels can share an SM.
+    msbfs_set_carveout(25);
+    mssp_set_carveout(25);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ctas = std::max(1, sms * 4 / slots);
+    const int per_sm = std::min(msbfs_min_blocks_per_sm(), mssp_blocks_per_sm());
+    const int ctas = std::max(1, sms * per_sm / slots);
     srv->slots.resize(slots);
     for (auto &S : srv->slots) {
         S.ws = graph_new_empty();

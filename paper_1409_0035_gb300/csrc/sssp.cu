@@ -239,6 +239,24 @@ int launch_mssp(const SsspJob &job, cudaStream_t st)
                : CC_ERR_CUDA;
 }
 
+void mssp_set_carveout(int percent)
+{
+    cudaFuncSetAttribute((const void *)mssp_kernel,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, percent);
+    cudaGetLastError();
+}
+
+int mssp_blocks_per_sm()
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mssp_kernel, kBlock, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b < 1 ? 1 : b;
+}
+
 void run_reduce1(const ReduceJob &r, cudaStream_t st)
 {
     k_reduce1<<<grid_of(r.n * 32), 256, 0, st>>>(r);
