@@ -314,9 +314,10 @@ int cc_server_free(cc_server_t s);
 
 /* ---- tuning ---------------------------------------------------------------- */
 /* Direction switch of the breadth-first traversal of one graph (0 restores
- * the default 14): a level runs top-down while (CSR entries of the
- * frontier) * alpha < (CSR entries of the nodes some source has not reached
- * yet), bottom-up otherwise.  Results do not depend on it, only the time. */
+ * the default: 6 when the sample fits one 64-bit word, else 14): a level
+ * runs top-down while (CSR entries of the frontier) * alpha < (CSR entries
+ * of the nodes some source has not reached yet), bottom-up otherwise.
+ * Results do not depend on it, only the time. */
 int cc_set_tuning(cc_graph_t g, int32_t alpha);
 
 /* ---- diagnostics --------------------------------------------------------- */
@@ -326,6 +327,31 @@ int cc_set_tuning(cc_graph_t g, int32_t alpha);
 int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td_levels,
                        int64_t *bu_levels, int64_t *edges_examined,
                        int64_t *words_gathered);
+
+/* Phases of a bit-packed traversal pass, for cc_last_pass_phases:
+ * state clearing and seeding (level 0); top-down queue building, pushes and
+ * finalisation of the touched nodes; bottom-up rebuild of the active light
+ * list, light, medium and heavy nodes, finalisation of the heavy nodes; and
+ * waiting in the grid barrier between them. */
+enum {
+    CC_PH_INIT = 0,
+    CC_PH_TD_QUEUE = 1,
+    CC_PH_TD_PUSH = 2,
+    CC_PH_TD_FINAL = 3,
+    CC_PH_BU_REBUILD = 4,
+    CC_PH_BU_LIGHT = 5,
+    CC_PH_BU_MEDIUM = 6,
+    CC_PH_BU_HEAVY = 7,
+    CC_PH_BU_FINAL = 8,
+    CC_PH_BARRIER = 9,
+    CC_NUM_PHASES = 10
+};
+
+/* Warp time by phase of the last bit-packed traversal pass on g (tracing;
+ * the paper has no counterpart): warp_cycles[p] (caller-owned, CC_NUM_PHASES
+ * entries) receives the SM clock cycles summed over all warps spent in phase
+ * p.  Only the shares are meaningful.  Zero after a weighted pass. */
+int cc_last_pass_phases(cc_graph_t g, int64_t *warp_cycles);
 
 /* Per-level trace of the last traversal pass on g (levels 1 .. D, at most
  * max_levels and at most 64): device time of each level in ns (global timer

@@ -37,8 +37,11 @@ EXPORTS = (
     "cc_set_tuning", "cc_batch_create", "cc_batch_run", "cc_batch_result",
     "cc_batch_info", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
-    "cc_selftest_barrier_timeout", "cc_strerror",
+    "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
 )
+
+PHASES = ("init", "td_queue", "td_push", "td_final", "bu_rebuild", "bu_light",
+          "bu_medium", "bu_heavy", "bu_final", "barrier")
 
 
 class CCError(RuntimeError):
@@ -86,6 +89,7 @@ def lib():
         L.cc_exact.argtypes = [P, P, P]
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
+        L.cc_last_pass_phases.argtypes = [P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
         L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
         L.cc_set_tuning.argtypes = [P, i32]
@@ -246,6 +250,13 @@ def cc_last_pass_stats(g):
          "cc_last_pass_stats")
     return dict(zip(("levels", "td_levels", "bu_levels", "edges", "words"),
                     [v.value for v in vals]))
+
+
+def cc_last_pass_phases(g):
+    """{phase: warp clock cycles} of the last bit-packed traversal pass."""
+    v = np.zeros(len(PHASES), np.int64)
+    _chk(lib().cc_last_pass_phases(g, _p(v)), "cc_last_pass_phases")
+    return dict(zip(PHASES, (int(x) for x in v)))
 
 
 def cc_set_tuning(g, alpha=0):

@@ -17,7 +17,6 @@ using namespace ccg;
 namespace {
 
 constexpr uint64_t kTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
-constexpr int kAlpha = 14;
 constexpr double kMaxHistBytes = 4.0 * (1ull << 30);  // distance histogram cap
 
 struct DevBuf {
@@ -67,7 +66,7 @@ struct cc_graph {
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
         distF, distR, mask, best, dmax, errflag, AL0, AL1, fstamp;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
-    int alpha = kAlpha;  // traversal tuning
+    int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
     bool borrowed = false;  // CSR buffers belong to another handle
     int hist_cap = 0;
@@ -101,12 +100,25 @@ int upload(DevBuf &b, const void *src, size_t bytes)
 
 int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c)
 {
-    std::vector<int32_t> L, M, H, Hn;
+    // Light and medium nodes are ordered by degree (stable counting sort,
+    // ties by id).  A warp scans W-lane groups of light nodes in lock step,
+    // so equal degrees keep its lanes busy for the same number of steps; and
+    // warps take every nwarps-th entry of a list, so a sorted list hands
+    // every warp about the same number of CSR entries.
+    std::vector<int64_t> start(kMediumMaxDeg + 2, 0);
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = rp[v + 1] - rp[v];
+        if (d <= kMediumMaxDeg) start[d + 1] += 1;
+    }
+    for (int d = 0; d <= kMediumMaxDeg; ++d) start[d + 1] += start[d];
+    const int64_t nlight = start[kLightMaxDeg + 1];
+    std::vector<int32_t> L((size_t)nlight), M((size_t)(start[kMediumMaxDeg + 1] - nlight)), H,
+        Hn;
     std::vector<int64_t> Hb;
     for (int64_t v = 0; v < n; ++v) {
         const int64_t d = rp[v + 1] - rp[v];
-        if (d <= kLightMaxDeg) L.push_back((int32_t)v);
-        else if (d <= kMediumMaxDeg) M.push_back((int32_t)v);
+        if (d <= kLightMaxDeg) L[(size_t)start[d]++] = (int32_t)v;
+        else if (d <= kMediumMaxDeg) M[(size_t)(start[d]++ - nlight)] = (int32_t)v;
         else {
             H.push_back((int32_t)v);
             for (int64_t b = rp[v]; b < rp[v + 1]; b += kChunk) {
@@ -204,9 +216,8 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
     j.sum2 = g->sum2.as<uint64_t>();
     j.ctl = g->ctl.as<Ctl>();
     j.timeout_ns = kTimeoutNs;
-    j.alpha = g->alpha;
+    j.alpha = g->alpha ? g->alpha : default_alpha(W);
     j.max_ctas = g->max_ctas;
-    (void)W;
     return j;
 }
 
@@ -824,10 +835,17 @@ int cc_last_pass_stats(cc_graph_t g, int64_t *levels, int64_t *td, int64_t *bu,
     return CC_OK;
 }
 
+int cc_last_pass_phases(cc_graph_t g, int64_t *warp_cycles)
+{
+    if (!g || !warp_cycles) return CC_ERR_ARG;
+    for (int p = 0; p < CC_NUM_PHASES; ++p) warp_cycles[p] = (int64_t)g->last.ph_cycles[p];
+    return CC_OK;
+}
+
 int cc_set_tuning(cc_graph_t g, int32_t alpha)
 {
     if (!g || alpha < 0) return CC_ERR_ARG;
-    g->alpha = alpha ? alpha : kAlpha;
+    g->alpha = alpha;
     return CC_OK;
 }
 

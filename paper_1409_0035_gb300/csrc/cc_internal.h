@@ -40,18 +40,15 @@ struct LevelCtl {
 };
 
 constexpr int kTraceLevels = 64;
-constexpr int kBarGroups = 32;  // arrival counters of the two-level barrier
 
 struct Ctl {
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned long long bar_arrive;  // grid barrier arrivals (see barrier.cuh)
     int err;                // 0 or a CC_ERR_* code
     int levels;             // last level that produced new bits
     long long ninc_final;   // nodes never completed (non-zero: disconnected)
     unsigned long long td_levels, bu_levels;
     unsigned long long edges, words;  // CSR entries examined, words gathered
     LevelCtl lev[4];
-    unsigned int bar_sub[kBarGroups];
     // Trace of the first kTraceLevels levels: global timer at the start of
     // each level (and at the end of the pass), direction and frontier size.
     unsigned long long lvl_ns[kTraceLevels + 1];
@@ -59,6 +56,8 @@ struct Ctl {
     unsigned int lvl_front[kTraceLevels];
     unsigned long long lvl_ef[kTraceLevels];
     unsigned long long lvl_words[kTraceLevels];
+    // Warp clock cycles spent in each CC_PH_* phase over the pass.
+    unsigned long long ph_cycles[CC_NUM_PHASES];
 };
 
 // One traversal pass over one graph.
@@ -127,6 +126,10 @@ struct GraphView {
     int alpha;
 };
 int graph_view(cc_graph_t g, GraphView *v);
+// Default direction switch of the bit-packed traversal (alpha of
+// cc_set_tuning) for W words per node: with one word a top-down push costs
+// about as much as a gathered word, with more the atomic pushes cost more.
+inline int default_alpha(int W) { return W == 1 ? 6 : 14; }
 // Server slots: an empty handle whose workspace persists, pointed at the
 // resident CSR of another handle per request.
 cc_graph_t graph_new_empty();

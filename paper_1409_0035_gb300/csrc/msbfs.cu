@@ -33,8 +33,19 @@ namespace ccg {
 
 namespace {
 
+// Resident CTAs per SM the register allocation must allow, for W <= 4 and
+// for W >= 8 words per node (build-time tunables).
+#ifndef CC_MSBFS_MIN_CTAS_NARROW
+#define CC_MSBFS_MIN_CTAS_NARROW 4
+#endif
+#ifndef CC_MSBFS_MIN_CTAS_WIDE
+#define CC_MSBFS_MIN_CTAS_WIDE 4
+#endif
+
 template <int W>
-__global__ void __launch_bounds__(kBlock, W >= 8 ? 3 : 4) msbfs_kernel(BfsJob J)
+__global__ void __launch_bounds__(kBlock, W >= 8 ? CC_MSBFS_MIN_CTAS_WIDE
+                                                 : CC_MSBFS_MIN_CTAS_NARROW)
+    msbfs_kernel(BfsJob J)
 {
     extern __shared__ unsigned s_hist[];  // W * 64 counters
     bfs_pass<W>(J, blockIdx.x, gridDim.x, J.ctl, s_hist);

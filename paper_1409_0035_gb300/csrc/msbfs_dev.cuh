@@ -13,7 +13,10 @@ namespace {
 
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kUnroll = 4;  // independent gathers in flight per lane and step
+#ifndef CC_MSBFS_UNROLL
+#define CC_MSBFS_UNROLL 4
+#endif
+constexpr int kUnroll = CC_MSBFS_UNROLL;  // independent gathers in flight per lane and step
 
 __device__ __forceinline__ uint64_t gtimer()
 {
@@ -189,20 +192,24 @@ __device__ __forceinline__ uint64_t or_same_word(uint64_t x)
     return x;
 }
 
-// OR of the frontier words (slot w) of up to U CSR entries x, x+stride, ...
-// below e.  The U column loads and the U gathers are independent, so they
-// are all in flight together.
-template <int W, int U>
-__device__ __forceinline__ uint64_t gather_or(const int32_t *__restrict__ col,
-                                              const uint64_t *Fin, int64_t x, int64_t e,
-                                              int stride, int w, unsigned long long &words)
+// Column indices of the U CSR entries x, x+stride, ... (-1 from e on).
+template <int U>
+__device__ __forceinline__ void load_cols(const int32_t *__restrict__ col, int64_t x, int64_t e,
+                                          int stride, int (&c)[U])
 {
-    int c[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t ee = x + (int64_t)u * stride;
         c[u] = ee < e ? __ldg(col + ee) : -1;
     }
+}
+
+// OR of the frontier words (slot w) of the columns in c; the U gathers are
+// independent, so they are all in flight together.
+template <int W, int U>
+__device__ __forceinline__ uint64_t gather_cols(const uint64_t *Fin, const int (&c)[U], int w,
+                                                unsigned long long &words)
+{
     uint64_t f = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -211,6 +218,32 @@ __device__ __forceinline__ uint64_t gather_or(const int32_t *__restrict__ col,
             words += 1;
         }
     return f;
+}
+
+// OR of the frontier words (word w) of the neighbours col[base + off],
+// col[base + off + stride], ... below e, U per step, until `done(acc)`
+// holds.  The step count depends on base, e, stride and `done` only, so it
+// is uniform over lanes that share them (`done` may be warp-collective).
+// The column indices of the next step are loaded while the current frontier
+// words are in flight: a step costs one dependent round trip, not two.
+template <int W, int U, class Done>
+__device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
+                                                const uint64_t *Fin, int64_t base, int off,
+                                                int64_t e, int stride, int w,
+                                                unsigned long long &words, Done done)
+{
+    uint64_t acc = 0;
+    int c[U];
+    load_cols<U>(col, base + off, e, stride, c);
+    for (; base < e; base += (int64_t)U * stride) {
+        int cn[U];
+        load_cols<U>(col, base + off + (int64_t)U * stride, e, stride, cn);
+        acc |= gather_cols<W, U>(Fin, c, w, words);
+        if (done(acc)) break;
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = cn[u];
+    }
+    return acc;
 }
 
 __device__ __forceinline__ unsigned long long block_sum64(unsigned long long x,
@@ -334,14 +367,16 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
     const int w = lane & (W - 1);
     const int grp = lane / W;
     if (f == 0ull) return;
+    // The next step's column indices load while this step's visited words
+    // are in flight.
+    int vn[kUnroll];
+    load_cols<kUnroll>(col, b + grp, e, NPW, vn);
     for (int64_t base = b + grp; base < e; base += NPW * kUnroll) {
         int vv[kUnroll];
         uint64_t vs[kUnroll];
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) {
-            const int64_t ee = base + (int64_t)q * NPW;
-            vv[q] = ee < e ? __ldg(col + ee) : -1;
-        }
+        for (int q = 0; q < kUnroll; ++q) vv[q] = vn[q];
+        load_cols<kUnroll>(col, base + (int64_t)NPW * kUnroll, e, NPW, vn);
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q)
             vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + w] : ~0ull;
@@ -388,6 +423,25 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     const Stage stage{s_buf, &s_cnt, &s_base};
     if (threadIdx.x == 0) s_cnt = 0;
 
+    // Warp time per phase (tracing): lane 0 of each warp adds the clock
+    // cycles since its previous lap to the CTA's counter of the phase that
+    // just ended; waits in the grid barrier count as CC_PH_BARRIER.
+    __shared__ unsigned long long s_ph[CC_NUM_PHASES];
+    if (threadIdx.x < CC_NUM_PHASES) s_ph[threadIdx.x] = 0;
+    __syncthreads();
+    long long ph_t = clock64();
+    auto lap = [&](int p) {
+        const long long t = clock64();
+        if (lane == 0) atomicAdd(&s_ph[p], (unsigned long long)(t - ph_t));
+        ph_t = t;
+    };
+    auto sync_after = [&](int p) {
+        lap(p);
+        const bool ok = grid_sync(bar, team_rank, nb, J.timeout_ns);
+        lap(CC_PH_BARRIER);
+        return ok;
+    };
+
     LaneAcc<W> A;
 #pragma unroll
     for (int i = 0; i < (W <= 8 ? 2 * W : 1); ++i) A.hc[i] = 0;
@@ -408,7 +462,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
     if (J.red & RED_LEVELS)
         for (int64_t i = gtid; i < n * 32; i += gthreads) J.dist_out[i] = kInf;
-    if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+    if (!sync_after(CC_PH_INIT)) return;
     for (int64_t i = gtid; i < J.k; i += gthreads) {
         const int v = J.sources[i];
         const uint64_t bit = 1ull << (i & 63);
@@ -430,7 +484,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         ctl->lev[0].qlen = (unsigned)J.k;
         ctl->lev[0].tlen = (unsigned)J.k;  // level 0 "touched" the sources
     }
-    if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+    if (!sync_after(CC_PH_INIT)) return;
 
     long long eu = J.arcs, ninc = n;
     int last = 0;
@@ -483,7 +537,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 block_compact(
                     n, [&](int64_t i) { return J.fstamp[i] == want; },
                     [&](int64_t i) { return (int32_t)i; }, J.Q0, &C->qcnt, team_rank, team_size);
-                if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+                if (!sync_after(CC_PH_TD_QUEUE)) return;
                 Qin = J.Q0;
                 qn = ((volatile LevelCtl *)C)->qcnt;
             }
@@ -507,7 +561,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                            stage);
             }
             stage_flush(stage, Tout, &C->tlen);
-            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+            if (!sync_after(CC_PH_TD_PUSH)) return;
             // P2: finalise the touched nodes.
             const int64_t tl = ((volatile LevelCtl *)C)->tlen;
             for (int64_t t = gwarp; t * NPW < tl; t += nwarps) {
@@ -527,7 +581,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+            if (!sync_after(CC_PH_TD_FINAL)) return;
             if (gtid == 0) ctl->td_levels += 1;
             prev_td = true;
             prevT = Tout;
@@ -546,7 +600,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                         return inc;
                     },
                     [&](int64_t i) { return ALin[i]; }, ALout, &C->alen, team_rank, team_size);
-                if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+                if (!sync_after(CC_PH_BU_REBUILD)) return;
                 ALcur = ALout;
                 al_len = ((volatile LevelCtl *)C)->alen;
                 al_next ^= 1;
@@ -561,32 +615,29 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 int64_t b = 0, e = 0;
                 if (valid) { b = prp[v]; e = prp[v + 1]; }
                 uint64_t acc = 0;
-                if (vis != ~0ull) {
-                    for (int64_t x = b; x < e; x += kUnroll) {
-                        acc |= gather_or<W, kUnroll>(pcol, Fin, x, e, 1, w, A.words);
-                        if ((acc | vis) == ~0ull) break;
-                    }
-                }
+                if (vis != ~0ull)
+                    acc = gather_scan<W, kUnroll>(pcol, Fin, b, 0, e, 1, w, A.words,
+                                                  [&](uint64_t a) { return (a | vis) == ~0ull; });
                 __syncwarp();
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, A, s_hist,
                                false);
             }
+            lap(CC_PH_BU_LIGHT);
             // A2: medium nodes, one warp per node.
             for (int64_t t = gwarp; t < J.nM; t += nwarps) {
                 const int v = J.Mlist[t];
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
                 if (__all_sync(FULL, visw == ~0ull)) continue;
                 const int64_t b = prp[v], e = prp[v + 1];
-                uint64_t acc = 0;
-                for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(pcol, Fin, base + grp, e, NPW, w, A.words);
-                    const uint64_t r = or_same_word<W>(acc);
-                    if (__all_sync(FULL, (r | visw) == ~0ull)) break;
-                }
+                const uint64_t acc = gather_scan<W, kUnroll>(
+                    pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
+                        return __all_sync(FULL, (or_same_word<W>(a) | visw) == ~0ull);
+                    });
                 const uint64_t r = or_same_word<W>(acc);
                 tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, A, s_hist,
                                false);
             }
+            lap(CC_PH_BU_MEDIUM);
             // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
             for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
                 const int v = J.Hch_node[t];
@@ -596,18 +647,15 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
-                uint64_t acc = 0;
-                for (int64_t base = b; base < e; base += NPW * kUnroll) {
-                    acc |= gather_or<W, kUnroll>(pcol, Fin, base + grp, e, NPW, w, A.words);
-                    const uint64_t r = or_same_word<W>(acc);
-                    if (__all_sync(FULL, (r | visw | cur) == ~0ull)) break;
-                }
-                const uint64_t r = or_same_word<W>(acc);
-                const uint64_t nbits = r & ~visw & ~cur;
+                const uint64_t acc = gather_scan<W, kUnroll>(
+                    pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
+                        return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);
+                    });
+                const uint64_t nbits = or_same_word<W>(acc) & ~visw & ~cur;
                 if (lane < W && nbits)
                     atomicOr((unsigned long long *)&J.nxt[vw], nbits);
             }
-            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+            if (!sync_after(CC_PH_BU_HEAVY)) return;
             // B: finalise the heavy nodes.
             for (int64_t t = gwarp; t * NPW < J.nH; t += nwarps) {
                 const int64_t li = t * NPW + grp;
@@ -626,7 +674,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             trace_words(ctl, l, A.words - words_before);
             flush_level<W>(J, l, C, A, s_hist, doHist);
-            if (!grid_sync(bar, team_rank, nb, J.timeout_ns)) return;
+            if (!sync_after(CC_PH_BU_FINAL)) return;
             if (gtid == 0) ctl->bu_levels += 1;
             prev_td = false;
         }
@@ -635,6 +683,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     __shared__ unsigned long long s_red[kBlock / 32];
     const unsigned long long words = block_sum64(A.words, s_red);
     if (tid == 0) atomicAdd(&ctl->words, words);
+    if (tid < CC_NUM_PHASES) atomicAdd(&ctl->ph_cycles[tid], s_ph[tid]);
     if (gtid == 0) {
         ctl->levels = last;
         ctl->ninc_final = ninc;
