@@ -415,6 +415,9 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         j.pivot = (int32_t *)p[13]; j.delta = (uint32_t *)p[14]; j.dcc = (uint32_t *)p[15];
         j.dcc_k = k;
         j.sources = (int32_t *)p[16];
+        j.ACH0 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nHch) * 4);
+        j.ACH1 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nHch) * 4);
+        if (!j.ACH0 || !j.ACH1) return CC_ERR_OOM;
         B_CK(cudaMemcpy(p[16], samples[i], (size_t)k * 4, cudaMemcpyHostToDevice));
         j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
         j.timeout_ns = 10ull * 1000 * 1000 * 1000;

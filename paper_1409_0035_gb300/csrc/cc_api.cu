@@ -64,7 +64,7 @@ struct cc_graph {
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
-        distF, distR, mask, best, dmax, errflag, AL0, AL1, fstamp;
+        distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp;
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
@@ -167,6 +167,9 @@ int ensure_state(cc_graph *g, int W)
     RC(g->T.ensure(n * 4));
     RC(g->AL0.ensure(n * 4));
     RC(g->AL1.ensure(n * 4));
+    const int64_t nch = std::max(g->fw.cls.nHch, g->rv.cls.nHch);
+    RC(g->ACH0.ensure((size_t)nch * 4));
+    RC(g->ACH1.ensure((size_t)nch * 4));
     RC(g->fstamp.ensure(n * 4));
     RC(g->tflag.ensure(n * 4));
     RC(g->sidx.ensure(n * 4));
@@ -210,6 +213,8 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
     j.T = g->T.as<int32_t>();
     j.AL0 = g->AL0.as<int32_t>();
     j.AL1 = g->AL1.as<int32_t>();
+    j.ACH0 = g->ACH0.as<int32_t>();
+    j.ACH1 = g->ACH1.as<int32_t>();
     j.fstamp = g->fstamp.as<uint32_t>();
     j.tflag = g->tflag.as<unsigned>();
     j.sidx = g->sidx.as<int32_t>();
@@ -323,7 +328,7 @@ void free_graph(cc_graph *g)
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->fstamp};
+                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -665,7 +670,7 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp, &g->maxd, &g->sources,
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
-                          &g->AL0, &g->AL1, &g->fstamp};
+                          &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;

@@ -34,7 +34,9 @@ struct LevelCtl {
     unsigned int ninc_dec;      // nodes that became complete this level
     unsigned int alen;          // rebuilt light list length (bottom-up)
     unsigned int qcnt;          // frontier queue built from the stamps (top-down)
-    unsigned int pad_[3];
+    unsigned int mlen;          // rebuilt medium list length (bottom-up)
+    unsigned int hlen;          // rebuilt heavy list length (bottom-up)
+    unsigned int hclen;         // rebuilt heavy chunk list length (bottom-up)
     unsigned long long ef;      // sum of degrees of the frontier nodes
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
@@ -84,7 +86,10 @@ struct BfsJob {
     int64_t nHch;
     uint64_t *vis, *F0, *F1, *nxt;  // n*W words each
     int32_t *Q0, *Q1, *T;           // n each
-    int32_t *AL0, *AL1;             // n each: active light-node lists
+    // n each: active node lists of the bottom-up levels, light nodes from
+    // entry 0, medium from nL, heavy from nL + nM.
+    int32_t *AL0, *AL1;
+    int32_t *ACH0, *ACH1;           // nHch each: active heavy chunk tasks
     uint32_t *fstamp;               // n: last level a node got new bits
     unsigned int *tflag;            // n
     uint32_t red;

@@ -488,11 +488,14 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
 
     long long eu = J.arcs, ninc = n;
     int last = 0;
-    // Active light-node list: Llist, later rebuilt (order-preserving) into
-    // AL0 / AL1 once the incomplete nodes fall below half of it.
-    const int32_t *ALcur = J.Llist;
-    int64_t al_len = J.nL;
-    int al_next = 0;
+    // Active lists of the bottom-up levels: the light, medium and heavy
+    // node lists and the heavy chunk tasks (null: all), later rebuilt
+    // (order-preserving) into AL0 / AL1 and ACH0 / ACH1 once the incomplete
+    // nodes fall below half of them.
+    const int32_t *ALcur = J.Llist, *MLcur = J.Mlist, *HLcur = J.Hlist;
+    const int32_t *HCcur = nullptr;
+    int64_t al_len = J.nL, ml_len = J.nM, hl_len = J.nH, hc_len = J.nHch;
+    int al_next = 0, ml_next = 0, hl_next = 0;
     // Queue of a top-down level: the previous level's touched list when that
     // level was top-down (level 0 "touched" the sources), else built from
     // the frontier stamps.
@@ -523,7 +526,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
             Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
-            Z->alen = 0; Z->qcnt = 0;
+            Z->alen = 0; Z->qcnt = 0; Z->mlen = 0; Z->hlen = 0; Z->hclen = 0;
         }
         uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
         uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
@@ -588,22 +591,57 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         } else {
             // Rebuild the light list when fewer than half of it can still be
             // incomplete (ninc bounds the incomplete light nodes).
-            if (2 * ninc < al_len) {
-                int32_t *ALout = al_next ? J.AL1 : J.AL0;
-                const int32_t *ALin = ALcur;
-                block_compact(
-                    al_len,
-                    [&](int64_t i) {
-                        const int64_t v = ALin[i];
-                        bool inc = false;
-                        for (int q = 0; q < W; ++q) inc |= J.vis[v * W + q] != ~0ull;
-                        return inc;
-                    },
-                    [&](int64_t i) { return ALin[i]; }, ALout, &C->alen, team_rank, team_size);
+            // ninc bounds the incomplete nodes of every class; the medium and
+            // heavy lists are rebuilt with the light list (heavy nodes complete
+            // early) or on their own bound.
+            const bool rb_l = 2 * ninc < al_len;
+            const bool rb_m = ml_len > 0 && (rb_l || 2 * ninc < ml_len);
+            const bool rb_h = hl_len > 0 && (rb_l || 2 * ninc < hl_len);
+            if (rb_l || rb_m || rb_h) {
+                auto incomplete = [&](int64_t v) {
+                    bool inc = false;
+                    for (int q = 0; q < W; ++q) inc |= J.vis[v * W + q] != ~0ull;
+                    return inc;
+                };
+                if (rb_l) {
+                    int32_t *out = al_next ? J.AL1 : J.AL0;
+                    const int32_t *in = ALcur;
+                    block_compact(
+                        al_len, [&](int64_t i) { return incomplete(in[i]); },
+                        [&](int64_t i) { return in[i]; }, out, &C->alen, team_rank, team_size);
+                    ALcur = out;
+                }
+                if (rb_m) {
+                    int32_t *out = (ml_next ? J.AL1 : J.AL0) + J.nL;
+                    const int32_t *in = MLcur;
+                    block_compact(
+                        ml_len, [&](int64_t i) { return incomplete(in[i]); },
+                        [&](int64_t i) { return in[i]; }, out, &C->mlen, team_rank, team_size);
+                    MLcur = out;
+                }
+                if (rb_h) {
+                    int32_t *out = (hl_next ? J.AL1 : J.AL0) + J.nL + J.nM;
+                    const int32_t *in = HLcur;
+                    block_compact(
+                        hl_len, [&](int64_t i) { return incomplete(in[i]); },
+                        [&](int64_t i) { return in[i]; }, out, &C->hlen, team_rank, team_size);
+                    HLcur = out;
+                    int32_t *cout = hl_next ? J.ACH1 : J.ACH0;
+                    const int32_t *cin = HCcur;
+                    block_compact(
+                        hc_len,
+                        [&](int64_t i) {
+                            return incomplete(J.Hch_node[cin ? cin[i] : (int32_t)i]);
+                        },
+                        [&](int64_t i) { return cin ? cin[i] : (int32_t)i; }, cout, &C->hclen,
+                        team_rank, team_size);
+                    HCcur = cout;
+                }
                 if (!sync_after(CC_PH_BU_REBUILD)) return;
-                ALcur = ALout;
-                al_len = ((volatile LevelCtl *)C)->alen;
-                al_next ^= 1;
+                const volatile LevelCtl *VC = C;
+                if (rb_l) { al_len = VC->alen; al_next ^= 1; }
+                if (rb_m) { ml_len = VC->mlen; ml_next ^= 1; }
+                if (rb_h) { hl_len = VC->hlen; hc_len = VC->hclen; hl_next ^= 1; }
             }
             // A1: light nodes of the active list, one thread per (node, word).
             for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
@@ -624,8 +662,8 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             lap(CC_PH_BU_LIGHT);
             // A2: medium nodes, one warp per node.
-            for (int64_t t = gwarp; t < J.nM; t += nwarps) {
-                const int v = J.Mlist[t];
+            for (int64_t t = gwarp; t < ml_len; t += nwarps) {
+                const int v = MLcur[t];
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
                 if (__all_sync(FULL, visw == ~0ull)) continue;
                 const int64_t b = prp[v], e = prp[v + 1];
@@ -639,10 +677,11 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             lap(CC_PH_BU_MEDIUM);
             // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
-            for (int64_t t = gwarp; t < J.nHch; t += nwarps) {
-                const int v = J.Hch_node[t];
+            for (int64_t t = gwarp; t < hc_len; t += nwarps) {
+                const int32_t ti = HCcur ? HCcur[t] : (int32_t)t;
+                const int v = J.Hch_node[ti];
                 const int64_t vw = (int64_t)v * W + w;
-                const int64_t b = J.Hch_begin[t];
+                const int64_t b = J.Hch_begin[ti];
                 const int64_t e = min(b + (int64_t)kChunk, prp[v + 1]);
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
@@ -657,10 +696,10 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             if (!sync_after(CC_PH_BU_HEAVY)) return;
             // B: finalise the heavy nodes.
-            for (int64_t t = gwarp; t * NPW < J.nH; t += nwarps) {
+            for (int64_t t = gwarp; t * NPW < hl_len; t += nwarps) {
                 const int64_t li = t * NPW + grp;
-                const bool valid = li < J.nH;
-                const int v = valid ? J.Hlist[li] : 0;
+                const bool valid = li < hl_len;
+                const int v = valid ? HLcur[li] : 0;
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = ~0ull, acc = 0;
                 int64_t deg = 0;
