@@ -56,6 +56,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over the ranks of the default process group (x
+    itself when there is none): the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size, units_per_rank, seconds):
+    """Units all ranks processed per second of the slowest rank: every rank
+    runs its own replica of the workload (weak scaling)."""
+    return world_size * units_per_rank / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,13 +285,12 @@ def run_ours(args):
         kms += ms
         kbytes += b
     torch.cuda.synchronize()
-    clk = clocks.stop()
     if ws > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_total = max_over_ranks(t_total, dev)
     ms_step = t_total / args.steps
-    value = ws * k * m * args.steps / (t_total / 1e3) / 1e9
+    value = whole_job_rate(ws, k * m * args.steps, t_total / 1e3) / 1e9
 
     # End to end: pinned host outputs, result download inside the region.
     host = {"s_hat": torch.empty((4, n), dtype=torch.float64, pin_memory=True),
@@ -304,10 +321,9 @@ def run_ours(args):
         cc.cc_estimate(g, C, opts_h, oh)
         e2e_t += time.perf_counter() - t0
     if ws > 1:
-        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = ws * k * m * args.steps / e2e_t / 1e9
+        torch.distributed.barrier()
+    e2e_t = max_over_ranks(e2e_t, dev)
+    e2e = whole_job_rate(ws, k * m * args.steps, e2e_t) / 1e9
 
     # One source per launch: the same traversal with one bit, k launches.
     nsingle = 16
