@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=120,
                     help="serve workload: requests in the Poisson stream")
     ap.add_argument("--slots", type=int, default=4, help="serve workload: slots")
+    ap.add_argument("--pool", default="default", choices=["default", "paper"],
+                    help="serve workload: graph pool (paper: R-MAT to scale 22, grids to 4096^2)")
     ap.add_argument("--workload", default="rmat20",
                     choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve"],
                     help="rmat20 is the headline; the others print their own line")
@@ -430,17 +432,19 @@ def batch64_graphs(master=7):
     return out
 
 
-def serve_pool():
+def serve_pool(paper=False):
     """40 resident graphs: R-MAT scale 12 + (i mod 9), edge factor 16, for
-    i < 20; square grids with side 256 * 2^(i mod 4) for the other 20."""
+    i < 20; square grids with side 256 * 2^(i mod 4) for the other 20.  With
+    `paper`, R-MAT scales 12 + (i mod 11) (up to 22) and grid sides
+    256 * 2^(i mod 5) (up to 4096)."""
     import synth
     pool = []
     for i in range(40):
         if i < 20:
-            scale = 12 + (i % 9)
+            scale = 12 + (i % (11 if paper else 9))
             pool.append((f"rmat s{scale}", synth.rmat_edges(scale, 16, seed=500 + i)))
         else:
-            side = 256 << (i % 4)
+            side = 256 << (i % (5 if paper else 4))
             pool.append((f"grid {side}", synth.grid_edges(side, side)))
     return pool
 
@@ -450,7 +454,7 @@ def run_serve(args, cc):
     requests over the resident pool; continuous batching in the server."""
     import numpy as np
     import synth
-    pool = serve_pool()
+    pool = serve_pool(paper=args.pool == "paper")
     handles, ns, ms_ = [], [], []
     for desc, (n, s, d) in pool:
         g, _ = cc.cc_graph_from_edges(n, s, d)
