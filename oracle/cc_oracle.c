@@ -368,6 +368,140 @@ int orc_closeness_from_S(int64_t n, const uint64_t *S, double *closeness)
 }
 
 /*
+ * Error estimate of the hybrid estimate of one node j not in C, for
+ * eps = a/b (Algorithm 1's last loop; section 4, eqs. (5) and (6)):
+ *
+ *   SqErrEst(j) = |L(j)| / |L(j) n C| * var(L(j) n C)
+ *               + |H(j)| * SQ(H(j)),
+ *
+ * var = sample variance of the distances d(c_i, j), c_i in L(j) n C
+ * (mean of squares minus square of mean), and SQ(H(j)) = the mean over
+ * c_i in HC(j) of (d(c_i, j) - d(c(j), c_i))^2.  When HC(j) is empty the
+ * paper falls back to a "suffix" of the sampled nodes farthest from c(j)
+ * without giving its size; here it is the single sampled node farthest
+ * from c(j) other than c(j) (ties to the smallest index; c(j) itself when
+ * k = 1).  Partition as in orc_estimate: x is beyond the threshold iff
+ * x*a > Delta(j)*b.  Numerators are exact integers (128-bit), converted
+ * once and divided once per term.  Writes the hybrid estimate to *est.
+ */
+#define D(i, v) ((uint64_t)table[(size_t)(i) * (size_t)n + (size_t)(v)])
+static double sqerr_node(int64_t n, int32_t k, const int32_t *sources,
+                         const int32_t *sidx, const uint32_t *table, int64_t j, int32_t p,
+                         uint64_t Dj, uint32_t a, uint32_t b, double *est)
+{
+    const uint64_t nm1 = (uint64_t)(n - 1);
+    const u128 thr = (u128)Dj * b;
+    uint64_t Hsum = 0, Hnum = 0;
+    for (int64_t w = 0; w < n; ++w) {
+        if (sidx[w] >= 0) continue;
+        uint64_t x = D(p, w);
+        if ((u128)x * a > thr) { Hsum += x; Hnum += 1; }
+    }
+    uint64_t HCsum = 0, HCnum = 0, LCsum = 0, LCnum = 0;
+    u128 LCsq = 0, HCsqerr = 0;
+    int32_t far = p;
+    for (int32_t i = 0; i < k; ++i) {
+        uint64_t x = D(p, sources[i]);      /* d(c(j), c_i) */
+        uint64_t dji = D(i, j);             /* d(c_i, j) */
+        if ((u128)x * a > thr) {
+            HCsum += dji; HCnum += 1;
+            int64_t e = (int64_t)dji - (int64_t)x;
+            HCsqerr += (u128)((uint64_t)(e < 0 ? -e : e)) * (uint64_t)(e < 0 ? -e : e);
+        } else {
+            LCsum += dji; LCnum += 1; LCsq += (u128)dji * dji;
+        }
+        if (i != p && (far == p || x > D(p, sources[far]))) far = i;
+    }
+    const uint64_t Lnum = nm1 - Hnum - HCnum;
+    u128 N = (u128)(Hsum + HCsum) * LCnum + (u128)LCsum * Lnum;
+    *est = (double)N / (double)LCnum;
+    /* sampling term: (LCsq*LCnum - LCsum^2) * Lnum / LCnum^3 */
+    const u128 var_num = LCsq * LCnum - (u128)LCsum * LCsum;
+    const double t1 = (double)(var_num * Lnum) /
+                      ((double)LCnum * (double)LCnum * (double)LCnum);
+    double t2;
+    if (HCnum > 0) {
+        t2 = (double)(HCsqerr * Hnum) / (double)HCnum;
+    } else {
+        int64_t e = (int64_t)D(far, j) - (int64_t)D(p, sources[far]);
+        uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+        t2 = (double)((u128)ae * ae * Hnum);
+    }
+    return t1 + t2;
+}
+
+/*
+ * orc_sqerr -- hybrid estimate and its error estimate SqErrEst for every
+ * node (0 for sampled nodes, whose S is exact).  Inputs as orc_estimate.
+ */
+int orc_sqerr(int64_t n, int32_t k, const int32_t *sources, const uint32_t *table,
+              uint32_t eps_a, uint32_t eps_b, double *s_hat, double *sqerr)
+{
+    if (n < 2 || k <= 0 || k > n || eps_a == 0 || eps_a > eps_b) return -1;
+    int32_t *sidx = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!sidx) return -4;
+    if (sample_index(n, k, sources, sidx)) { free(sidx); return -1; }
+    for (int64_t j = 0; j < n; ++j) {
+        if (sidx[j] >= 0) {
+            uint64_t s = 0;
+            for (int64_t v = 0; v < n; ++v) s += D(sidx[j], v);
+            s_hat[j] = (double)s;
+            sqerr[j] = 0.0;
+            continue;
+        }
+        int32_t p = 0;
+        for (int32_t i = 1; i < k; ++i)
+            if (D(i, j) < D(p, j)) p = i;
+        sqerr[j] = sqerr_node(n, k, sources, sidx, table, j, p, D(p, j), eps_a, eps_b,
+                              &s_hat[j]);
+    }
+    free(sidx);
+    return 0;
+}
+
+/*
+ * orc_adaptive -- the adaptive hybrid ("Hyb.-ad", section 6): for every
+ * node not in C, the hybrid estimate under each eps = as[e]/bs[e] of the
+ * list, keeping the one with the smallest SqErrEst (ties to the earlier
+ * entry).  choice[j] is that entry's position; -1 for sampled nodes, which
+ * get their exact S and error 0.
+ */
+int orc_adaptive(int64_t n, int32_t k, const int32_t *sources, const uint32_t *table,
+                 int32_t ne, const uint32_t *as, const uint32_t *bs, double *s_hat,
+                 double *sqerr, int32_t *choice)
+{
+    if (n < 2 || k <= 0 || k > n || ne <= 0) return -1;
+    for (int32_t e = 0; e < ne; ++e)
+        if (as[e] == 0 || as[e] > bs[e]) return -1;
+    int32_t *sidx = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!sidx) return -4;
+    if (sample_index(n, k, sources, sidx)) { free(sidx); return -1; }
+    for (int64_t j = 0; j < n; ++j) {
+        if (sidx[j] >= 0) {
+            uint64_t s = 0;
+            for (int64_t v = 0; v < n; ++v) s += D(sidx[j], v);
+            s_hat[j] = (double)s;
+            sqerr[j] = 0.0;
+            choice[j] = -1;
+            continue;
+        }
+        int32_t p = 0;
+        for (int32_t i = 1; i < k; ++i)
+            if (D(i, j) < D(p, j)) p = i;
+        for (int32_t e = 0; e < ne; ++e) {
+            double est;
+            double se = sqerr_node(n, k, sources, sidx, table, j, p, D(p, j), as[e], bs[e],
+                                   &est);
+            if (e == 0 || se < sqerr[j]) { sqerr[j] = se; s_hat[j] = est; choice[j] = e; }
+        }
+    }
+    free(sidx);
+    return 0;
+}
+
+#undef D
+
+/*
  * Streaming form of the sampling and pivoting statistics (section 3, second
  * paragraph): one SSSP per sampled node, each scanned node v adds d to
  * sum[v] and updates the running minimum Delta(v) / pivot c(v) (strict "<",

@@ -57,6 +57,8 @@ def _L():
                                      P, P, P]
         lib.orc_closeness_from_S.argtypes = [i64, P, P]
         lib.orc_streaming_pass.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
+        lib.orc_sqerr.argtypes = [i64, i32, P, P, u32, u32, P, P]
+        lib.orc_adaptive.argtypes = [i64, i32, P, P, i32, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -317,6 +319,44 @@ def estimate_from_table(table: np.ndarray, sources, eps=(1, 8)):
 def estimate(g: Graph, sources, eps=(1, 8), roundtrip=False):
     """dist_table + estimate_from_table."""
     return estimate_from_table(dist_table(g, sources, roundtrip), sources, eps)
+
+
+# The eps values of the adaptive hybrid (section 6): 0.001, 0.025, 0.05,
+# 0.1, 0.2, 0.5 and 0.99, as fractions a/b.
+ADAPTIVE_EPS = ((1, 1000), (1, 40), (1, 20), (1, 10), (1, 5), (1, 2), (99, 100))
+
+
+def sqerr_from_table(table: np.ndarray, sources, eps=(1, 8)):
+    """Hybrid estimate of S and its error estimate SqErrEst (Algorithm 1's
+    last loop; section 4) for every node, from a k x n metric table.
+    Returns (s_hat, sqerr); sampled nodes get their exact S and error 0."""
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    k, n = table.shape
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    s_hat = np.empty(n, np.float64)
+    sqerr = np.empty(n, np.float64)
+    rc = _L().orc_sqerr(n, k, _p(src), _p(table), int(eps[0]), int(eps[1]), _p(s_hat),
+                        _p(sqerr))
+    _check(rc, "sqerr")
+    return s_hat, sqerr
+
+
+def adaptive_from_table(table: np.ndarray, sources, eps_list=ADAPTIVE_EPS):
+    """The adaptive hybrid (section 6): per node the hybrid estimate under
+    the eps of eps_list with the smallest SqErrEst.  Returns (s_hat, sqerr,
+    choice) with choice = position in eps_list (-1 for sampled nodes)."""
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    k, n = table.shape
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    a = np.ascontiguousarray([e[0] for e in eps_list], dtype=np.uint32)
+    b = np.ascontiguousarray([e[1] for e in eps_list], dtype=np.uint32)
+    s_hat = np.empty(n, np.float64)
+    sqerr = np.empty(n, np.float64)
+    choice = np.empty(n, np.int32)
+    rc = _L().orc_adaptive(n, k, _p(src), _p(table), len(eps_list), _p(a), _p(b), _p(s_hat),
+                           _p(sqerr), _p(choice))
+    _check(rc, "adaptive")
+    return s_hat, sqerr, choice
 
 
 def streaming_pass(g: Graph, sources):
