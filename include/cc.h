@@ -142,6 +142,14 @@ typedef struct {
                                       LCsumSq of eq. (4); zeros for v in C */
     uint64_t *S_sampled;           /* k: exact S(c_i)                     */
     uint32_t *delta_cc;            /* k x k: d(c_i, c_j), row i           */
+    double *sq_err;                /* n: SqErrEst of the hybrid estimate
+                                      (Algorithm 1's last loop, section 4):
+                                      |L| var(L n C)/|L n C| + |H| * mean
+                                      over HC of (d(c_i,v) - d(c(v),c_i))^2;
+                                      when HC(v) is empty the sampled node
+                                      farthest from c(v) stands in for it;
+                                      0 for v in C.  Needs want_hybrid; asking
+                                      for it may add the second pass.      */
 } cc_out;
 
 typedef struct {

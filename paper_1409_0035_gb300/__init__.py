@@ -61,7 +61,8 @@ class cc_out(ctypes.Structure):
                 ("closeness", ctypes.c_void_p * CC_NUM_EST),
                 ("pivot", ctypes.c_void_p), ("delta", ctypes.c_void_p),
                 ("sample_sum", ctypes.c_void_p), ("hyb_int", ctypes.c_void_p),
-                ("S_sampled", ctypes.c_void_p), ("delta_cc", ctypes.c_void_p)]
+                ("S_sampled", ctypes.c_void_p), ("delta_cc", ctypes.c_void_p),
+                ("sq_err", ctypes.c_void_p)]
 
 
 _lib = None
@@ -196,10 +197,11 @@ def cc_opts_default(k):
     return o
 
 
-def cc_estimate(g, sample, opts=None, out=None):
+def cc_estimate(g, sample, opts=None, out=None, want_sqerr=False):
     """Low-level call: `out` is a filled cc_out (host or device pointers per
     opts.device_outputs).  Without `out`, allocates host numpy outputs and
-    returns them as a dict."""
+    returns them as a dict (with "sq_err", the hybrid's error estimate, when
+    want_sqerr)."""
     sample = np.ascontiguousarray(sample, dtype=np.int32)
     k = sample.size
     if opts is None:
@@ -220,6 +222,9 @@ def cc_estimate(g, sample, opts=None, out=None):
     o.pivot, o.delta = _p(res["pivot"]), _p(res["delta"])
     o.sample_sum, o.hyb_int = _p(res["sum"]), _p(res["hyb"])
     o.S_sampled, o.delta_cc = _p(res["S_samp"]), _p(res["delta_cc"])
+    if want_sqerr:
+        res["sq_err"] = np.empty(n, np.float64)
+        o.sq_err = _p(res["sq_err"])
     _chk(lib().cc_estimate(g, _p(sample), k, ctypes.byref(opts), ctypes.byref(o)),
          "cc_estimate")
     return res

@@ -87,7 +87,7 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
         d_maxdelta(B.j.dcc, k, B.maxd, gtid, gthreads);
         if (!grid_sync(bar, rank, size, to)) return;
         d_hyb_prep(3, n, k, D, B.a, B.b, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.maxd,
-                   B.TN, B.TS, B.hp, B.npartial, gtid, gthreads);
+                   B.TN, B.TS, B.hp, B.npartial, SqPrep{nullptr}, gtid, gthreads);
         if (!grid_sync(bar, rank, size, to)) return;
         if (*(volatile unsigned *)B.npartial > 0) {
             d_lmask(n, W, k, B.j.sidx, B.j.pivot, B.j.dcc, B.hp, B.Lmask, gtid, gthreads);
@@ -101,7 +101,7 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
             if (!grid_sync(bar, rank, size, to)) return;
         }
     }
-    FinalizeArgs fa;
+    FinalizeArgs fa{};
     fa.n = n;
     fa.k = k;
     fa.hybrid = B.want_hybrid;

@@ -65,6 +65,10 @@ struct cc_graph {
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
         distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp;
+    // error estimate of the hybrid (SqErrEst): squared errors, fallback
+    // distances, per-node flags, farthest-sample table, staged output
+    DevBuf hcse, fdist, sqflag, istar, sqe;
+    bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
@@ -328,7 +332,8 @@ void free_graph(cc_graph *g)
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp};
+                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
+                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -339,6 +344,20 @@ void free_graph(cc_graph *g)
 // Unweighted undirected graphs: one bit-packed multi-source pass for sums,
 // pivots, Delta, delta_cc and the per-level histogram, and a second pass
 // with the L(v) masks only when some node's L(v) misses a sampled node.
+// Buffers and the farthest-sample table of the error estimate.
+int prepare_sq(cc_graph *g, int k, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    RC(g->hcse.ensure((size_t)n * 16));
+    RC(g->fdist.ensure((size_t)n * 4));
+    RC(g->sqflag.ensure((size_t)n));
+    RC(g->istar.ensure((size_t)k * 4));
+    CK(cudaMemsetAsync(g->hcse.p, 0, (size_t)n * 16, st));
+    run_istar(g->dcc.as<uint32_t>(), k, g->istar.as<int32_t>(), st);
+    g->call_kernels += 1;
+    return CC_OK;
+}
+
 int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 {
     const int64_t n = g->n;
@@ -379,20 +398,30 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     RC(g->TS.ensure((size_t)k * (D + 1) * 8));
     RC(g->maxd.ensure((size_t)k * 4));
     RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
-    RC(g->npartial.ensure(4));
-    CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
+    RC(g->npartial.ensure(8));
+    CK(cudaMemsetAsync(g->npartial.p, 0, 8, st));
+    // Sums of squared levels (LCsumSq, the squared errors) stay in 64 bits.
+    if ((double)D * (double)D * (double)k >= 1.8e19) return CC_ERR_TOO_LARGE;
     run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
     run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
+    SqPrep sq{nullptr};
+    if (g->sq) {
+        RC(prepare_sq(g, k, st));
+        sq.flag = g->sqflag.as<uint8_t>();
+    }
     run_hyb_prep(3, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
-                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), st);
+                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), sq, st);
     g->call_kernels += 3;
-    unsigned npart = 0;
-    CK(cudaMemcpyAsync(&npart, g->npartial.p, 4, cudaMemcpyDeviceToHost, st));
+    unsigned npart[2] = {0, 0};
+    CK(cudaMemcpyAsync(npart, g->npartial.p, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     RC(g->lc2.ensure(n * 16));
-    if (npart == 0) return CC_OK;
+    // The second pass gathers LCsum for nodes whose L(v) misses a sampled
+    // node and, for the error estimate, the squared errors over HC(v) or
+    // the distance to the farthest sample where HC(v) is empty.
+    if (npart[0] == 0 && npart[1] == 0) return CC_OK;
     RC(g->Lmask.ensure((size_t)n * W * 8));
     run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
               g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
@@ -404,6 +433,16 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     j2.red = RED_LC;
     j2.Lmask = g->Lmask.as<uint64_t>();
     j2.lc2 = g->lc2.as<uint64_t>();
+    if (g->sq) {
+        j2.red |= RED_SQ;
+        j2.pivot = g->pivot.as<int32_t>();
+        j2.dcc = g->dcc.as<uint32_t>();
+        j2.dcc_k = k;
+        j2.sqflag = g->sqflag.as<uint8_t>();
+        j2.istar = g->istar.as<int32_t>();
+        j2.hcse = g->hcse.as<uint64_t>();
+        j2.fdist = g->fdist.as<uint32_t>();
+    }
     return run_pass(g, W, j2, st);
 }
 
@@ -529,28 +568,42 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 
     const int64_t D = (int64_t)dmax;
     if ((double)(D + 1) * k * 4.0 > (double)kMaxHistBytes) return CC_ERR_TOO_LARGE;
+    // Sums of squared distances (LCsumSq) stay in 64 bits.
+    if ((double)D * (double)D * (double)k >= 1.8e19) return CC_ERR_TOO_LARGE;
     RC(g->hist.ensure((size_t)(D + 1) * k * 4));
     RC(g->TN.ensure((size_t)k * (D + 1) * 8));
     RC(g->TS.ensure((size_t)k * (D + 1) * 8));
     RC(g->maxd.ensure((size_t)k * 4));
     RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
-    RC(g->npartial.ensure(4));
+    RC(g->npartial.ensure(8));
     RC(g->Lmask.ensure((size_t)n * W * 8));
     RC(g->lc2.ensure(n * 16));
-    CK(cudaMemsetAsync(g->npartial.p, 0, 4, st));
+    CK(cudaMemsetAsync(g->npartial.p, 0, 8, st));
     CK(cudaMemsetAsync(g->hist.p, 0, (size_t)(D + 1) * k * 4, st));
     CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
     run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
+    SqPrep sq{nullptr};
+    if (g->sq) {
+        RC(prepare_sq(g, k, st));
+        sq.flag = g->sqflag.as<uint8_t>();
+    }
     run_hyb_prep(1, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), nullptr, nullptr, g->hp.as<HybPrep>(),
-                 g->npartial.as<unsigned>(), st);
+                 g->npartial.as<unsigned>(), sq, st);
     run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
               g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
     g->call_kernels += 3;
     r.hist = g->hist.as<uint32_t>();
     r.Lmask = g->Lmask.as<uint64_t>();
     r.lc2 = g->lc2.as<uint64_t>();
+    if (g->sq) {
+        r.sqflag = g->sqflag.as<uint8_t>();
+        r.istar = g->istar.as<int32_t>();
+        r.pivot = g->pivot.as<int32_t>();
+        r.hcse = g->hcse.as<uint64_t>();
+        r.fdist = g->fdist.as<uint32_t>();
+    }
     for (int base = 0; base < k; base += kChunkSrc) {
         const int kc = std::min(kChunkSrc, k - base);
         RC(run_chunk(g, src + base, kc, st));
@@ -563,7 +616,7 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     run_hyb_prep(2, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
-                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), st);
+                 g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), SqPrep{nullptr}, st);
     g->call_kernels += 2;
     return CC_OK;
 }
@@ -574,7 +627,7 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
 {
     const int64_t n = g->n;
     const bool dev_out = opts->device_outputs != 0;
-    FinalizeArgs fa;
+    FinalizeArgs fa{};
     std::memset(&fa, 0, sizeof(fa));
     fa.n = n;
     fa.k = k;
@@ -609,6 +662,18 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
             fa.sample_sum = g->ssum.as<uint64_t>();
         }
     }
+    if (g->sq && hyb) {
+        if (dev_out) {
+            fa.sq_err = out->sq_err;
+        } else {
+            RC(g->sqe.ensure((size_t)n * 8));
+            fa.sq_err = g->sqe.as<double>();
+        }
+        fa.hcse = g->hcse.as<uint64_t>();
+        fa.fdist = g->fdist.as<uint32_t>();
+        fa.dcc = g->dcc.as<uint32_t>();
+        fa.istar = g->istar.as<int32_t>();
+    }
     run_finalize(fa, st);
     g->call_kernels += 1;
     const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -624,6 +689,7 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
             CK(cudaMemcpyAsync(out->hyb_int, fa.hyb_int, n * 48, kind, st));
         if (out->sample_sum)
             CK(cudaMemcpyAsync(out->sample_sum, fa.sample_sum, n * 8, kind, st));
+        if (fa.sq_err) CK(cudaMemcpyAsync(out->sq_err, fa.sq_err, n * 8, kind, st));
     }
     if (out->pivot) CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
     if (out->delta) CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
@@ -670,7 +736,8 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp, &g->maxd, &g->sources,
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
-                          &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp};
+                          &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
+                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;
@@ -920,6 +987,7 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *o
     run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
     g->call_kernels += 2;
     const bool hyb = opts->want_hybrid != 0;
+    g->sq = hyb && out->sq_err != nullptr;
     const int rc = (g->weighted || g->directed) ? estimate_chunked(g, k, opts, st)
                                                 : estimate_bfs(g, k, opts, st);
     if (rc != CC_OK) return rc;

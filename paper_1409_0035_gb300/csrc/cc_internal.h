@@ -24,6 +24,11 @@ enum : uint32_t {
     RED_HIST = 8u,   // per-source level histogram over V \ C
     RED_LC = 16u,    // hybrid pass: lc[v] += d, d^2 over sources in Lmask(v)
     RED_LEVELS = 32u, // k <= 32: dist_out[v * 32 + i] = level of v from source i
+    // hybrid pass with the error estimate: for nodes flagged in sqflag,
+    // hcse[v] += (d(c_i, v) - d(c(v), c_i))^2 over c_i beyond the threshold
+    // (flag 1: not in Lmask; 128-bit {lo, hi}), and fdist[v] = d(c_i, v) for
+    // c_i = istar[c(v)] (flag 2: no sampled node beyond the threshold)
+    RED_SQ = 64u,
 };
 
 // Per-level statistics, indexed by level mod 4 (written during level l,
@@ -103,6 +108,10 @@ struct BfsJob {
     const uint64_t *Lmask;  // n*W
     uint64_t *lc2;          // n x 2: {LCsum, LCsumSq}
     uint32_t *dist_out;     // RED_LEVELS: n x 32 chunk of levels
+    const uint8_t *sqflag;  // RED_SQ: per node, 1 = accumulate hcse, 2 = record fdist
+    const int32_t *istar;   // RED_SQ: per sample index, the farthest other sample
+    uint64_t *hcse;         // RED_SQ: n x 2
+    uint32_t *fdist;        // RED_SQ: n
     Ctl *ctl;
     uint64_t timeout_ns;
     int alpha;              // top-down while ef * alpha < eu

@@ -43,9 +43,15 @@ __global__ void k_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, ui
                            const int32_t *sidx, const int32_t *pivot,
                            const uint32_t *delta, const uint32_t *dcc,
                            const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
-                           HybPrep *hp, unsigned *npartial)
+                           HybPrep *hp, unsigned *npartial, SqPrep sq)
 {
-    d_hyb_prep(mode, n, k, D, a, b, sidx, pivot, delta, dcc, maxd, TN, TS, hp, npartial, GSTART, GSTRIDE);
+    d_hyb_prep(mode, n, k, D, a, b, sidx, pivot, delta, dcc, maxd, TN, TS, hp, npartial, sq,
+               GSTART, GSTRIDE);
+}
+
+__global__ void k_istar(const uint32_t *dcc, int k, int32_t *istar)
+{
+    d_istar(dcc, k, istar, GSTART, GSTRIDE);
 }
 
 __global__ void k_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
@@ -98,10 +104,16 @@ void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
 void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                   const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
                   const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
-                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, cudaStream_t st)
+                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, const SqPrep &sq,
+                  cudaStream_t st)
 {
     k_hyb_prep<<<grid_for(n, 256), 256, 0, st>>>(mode, n, k, D, a, b, sidx, pivot, delta,
-                                                 dcc, maxd, TN, TS, hp, npartial);
+                                                 dcc, maxd, TN, TS, hp, npartial, sq);
+}
+
+void run_istar(const uint32_t *dcc, int k, int32_t *istar, cudaStream_t st)
+{
+    k_istar<<<(k + 127) / 128, 128, 0, st>>>(dcc, k, istar);
 }
 
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,

@@ -16,6 +16,12 @@ struct HybPrep {
     uint64_t Hsum, Hnum, thr, LCnum;
 };
 
+// Error-estimate input flags written by the hybrid preparation (null: the
+// error estimate is not wanted).
+struct SqPrep {
+    uint8_t *flag;
+};
+
 struct FinalizeArgs {
     int64_t n;
     int k;
@@ -28,6 +34,11 @@ struct FinalizeArgs {
     double *clo[CC_NUM_EST];
     uint64_t *hyb_int;
     uint64_t *sample_sum;
+    // error estimate (null sq_err: not wanted)
+    double *sq_err;
+    const uint64_t *hcse;  // n x 2: 128-bit sum of squared errors over HC(v)
+    const uint32_t *fdist, *dcc;
+    const int32_t *istar;
 };
 
 void run_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
@@ -40,7 +51,9 @@ void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st);
 void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                   const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
                   const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
-                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, cudaStream_t st);
+                  const uint64_t *TS, HybPrep *hp, unsigned *npartial, const SqPrep &sq,
+                  cudaStream_t st);
+void run_istar(const uint32_t *dcc, int k, int32_t *istar, cudaStream_t st);
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
                const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st);
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);

@@ -101,18 +101,36 @@ __device__ __forceinline__ void d_maxdelta(const uint32_t *dcc, int k, uint32_t 
     }
 }
 
+// Per sampled node p: the sampled node farthest from it other than itself
+// (ties to the smallest index; p itself when k = 1) -- the stand-in for
+// HC(v) in the error estimate of nodes whose HC(v) is empty (section 4).
+__device__ __forceinline__ void d_istar(const uint32_t *dcc, int k, int32_t *istar,
+                                        int64_t i0, int64_t stride)
+{
+    for (int64_t p = i0; p < k; p += stride) {
+        int best = (int)p;
+        for (int i = 0; i < k; ++i)
+            if (i != (int)p && (best == (int)p || dcc[p * k + i] > dcc[p * k + best])) best = i;
+        istar[p] = best;
+    }
+}
+
 // Per unsampled node: threshold t = floor(Delta * den / num) (so that "d >
 // Delta/eps" is "d > t" for integer d), H statistics from the tail tables of
 // the pivot, |L cap C| and whether L(v) misses some sampled node (then the
 // hybrid needs the second pass).
 // mode & 1: thresholds and |L cap C| (needs delta_cc); mode & 2: H
 // statistics from the tail tables (needs the histogram of the pass that
-// produced it).
+// produced it).  With sq.flag, also which error-estimate input the second
+// pass must gather per node: 1 when some c_i is beyond the threshold (the
+// squared errors over them), 2 when none is (the distance to the farthest
+// sampled node from the pivot) -- with mode 3 only where H(v) is not empty;
+// npartial[1] counts the 2s.
 __device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                            const int32_t *sidx, const int32_t *pivot,
                            const uint32_t *delta, const uint32_t *dcc,
                            const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
-                           HybPrep *hp, unsigned *npartial, int64_t i0,
+                           HybPrep *hp, unsigned *npartial, const SqPrep &sq, int64_t i0,
                                 int64_t stride)
 {
     for (int64_t v = i0; v < n;
@@ -130,13 +148,21 @@ __device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D
                 h.thr = t;
                 if (t >= maxd[p]) {
                     h.LCnum = (uint64_t)k;
+                    if (sq.flag) {
+                        const uint8_t f = (!(mode & 2) || h.Hnum > 0) ? 2 : 0;
+                        sq.flag[v] = f;
+                        if (f) atomicAdd(&npartial[1], 1u);
+                    }
                 } else {
                     uint64_t c = 0;
                     for (int i = 0; i < k; ++i) c += dcc[(int64_t)p * k + i] <= t;
                     h.LCnum = c | kPartialBit;
                     atomicAdd(npartial, 1u);
+                    if (sq.flag) sq.flag[v] = 1;
                 }
             }
+        } else if (sq.flag && (mode & 1)) {
+            sq.flag[v] = 0;
         }
         hp[v] = h;
     }
@@ -199,8 +225,29 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
                 est[3] = u128_to_double(N) / (double)LCnum;
                 h6[0] = h.Hsum; h6[1] = h.Hnum; h6[2] = HCsum;
                 h6[3] = LCsum; h6[4] = LCnum; h6[5] = LCsq;
+                if (A.sq_err) {
+                    // SqErrEst (Algorithm 1's last loop; section 4): the
+                    // sampling term |L| var(L n C) / |L n C| and the pivoting
+                    // term |H| * mean over HC of (d(c_i, v) - d(c(v), c_i))^2.
+                    const u128 var_num = (u128)LCsq * LCnum - (u128)LCsum * LCsum;
+                    const double t1 = u128_to_double(var_num * Lnum) /
+                                      ((double)LCnum * (double)LCnum * (double)LCnum);
+                    double t2 = 0.0;
+                    if (HCnum > 0) {
+                        const u128 e2 = ((u128)A.hcse[2 * v + 1] << 64) | A.hcse[2 * v];
+                        t2 = u128_to_double(e2 * h.Hnum) / (double)HCnum;
+                    } else if (h.Hnum > 0) {
+                        const int is = A.istar[p];
+                        const int64_t e = (int64_t)A.fdist[v] -
+                                          (int64_t)A.dcc[(int64_t)p * A.k + is];
+                        const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+                        t2 = u128_to_double((u128)ae * ae * h.Hnum);
+                    }
+                    A.sq_err[v] = t1 + t2;
+                }
             }
         }
+        if (j >= 0 && A.sq_err) A.sq_err[v] = 0.0;
         for (int e = 0; e < CC_NUM_EST; ++e) {
             if (e == CC_EST_HYBRID && !A.hybrid) continue;
             if (A.s_hat[e]) A.s_hat[e][v] = est[e];

@@ -88,7 +88,31 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
     if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC))) sx = J.sidx[v];
     int c = __popcll(nw);
     int cL = 0;
-    if ((J.red & RED_LC) && valid && sx < 0 && nw) cL = __popcll(nw & J.Lmask[vw]);
+    unsigned long long xs = 0;
+    if ((J.red & RED_LC) && valid && sx < 0 && nw) {
+        const uint64_t lm = J.Lmask[vw];
+        cL = __popcll(nw & lm);
+        if (J.red & RED_SQ) {
+            const uint8_t f = J.sqflag[v];
+            if (f) {
+                const int p = J.pivot[v];
+                if (f & 1) {
+                    // Sources beyond the threshold reaching v now, at level l.
+                    uint64_t bh = nw & ~lm;
+                    while (bh) {
+                        const int i = w * 64 + __ffsll((long long)bh) - 1;
+                        bh &= bh - 1;
+                        const long long e = (long long)l - J.dcc[(int64_t)p * J.dcc_k + i];
+                        xs += (unsigned long long)(e * e);
+                    }
+                }
+                if (f & 2) {
+                    const int is = J.istar[p];
+                    if ((is >> 6) == w && ((nw >> (is & 63)) & 1ull)) J.fdist[v] = (uint32_t)l;
+                }
+            }
+        }
+    }
     int had = (vis & ~pad_mask(J.k, w)) != 0;
     int done_before = vis == ~0ull;
     int done_after = (vis | nw) == ~0ull;
@@ -97,6 +121,7 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
     for (int o = 1; o < W; o <<= 1) {
         c += __shfl_xor_sync(FULL, c, o);
         cL += __shfl_xor_sync(FULL, cL, o);
+        xs += __shfl_xor_sync(FULL, xs, o);
         had |= __shfl_xor_sync(FULL, had, o);
         done_before &= __shfl_xor_sync(FULL, done_before, o);
         done_after &= __shfl_xor_sync(FULL, done_after, o);
@@ -112,6 +137,11 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         if (cL > 0) {
             J.lc2[2 * (int64_t)v] += ul * (uint64_t)cL;
             J.lc2[2 * (int64_t)v + 1] += ul * ul * (uint64_t)cL;
+        }
+        if (xs) {
+            const uint64_t lo = J.hcse[2 * (int64_t)v] + xs;
+            J.hcse[2 * (int64_t)v + 1] += lo < xs ? 1u : 0u;
+            J.hcse[2 * (int64_t)v] = lo;
         }
         if ((J.red & RED_PIVOT) && !had) {
             J.pivot[v] = pv;

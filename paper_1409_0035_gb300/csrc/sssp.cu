@@ -193,6 +193,34 @@ __global__ void k_reduce2(ReduceJob R)
             R.lc2[2 * v] += s;
             R.lc2[2 * v + 1] += s2;
         }
+        const uint8_t f = R.sqflag ? R.sqflag[v] : 0;
+        if (f) {
+            const int p = R.pivot[v];
+            if (f & 1) {
+                // 128-bit warp sum of the squared errors of this chunk's
+                // sources beyond the threshold.
+                uint64_t lo = 0, hi = 0;
+                if (valid && !inL) {
+                    const int64_t e = (int64_t)d - (int64_t)R.dcc[(int64_t)p * R.k + gi];
+                    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+                    lo = ae * ae;
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const uint64_t olo = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+                    const uint64_t ohi = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+                    const uint64_t nlo = lo + olo;
+                    hi += ohi + (nlo < lo ? 1u : 0u);
+                    lo = nlo;
+                }
+                if (lane == 0 && (lo | hi)) {
+                    const uint64_t nlo = R.hcse[2 * v] + lo;
+                    R.hcse[2 * v + 1] += hi + (nlo < lo ? 1u : 0u);
+                    R.hcse[2 * v] = nlo;
+                }
+            }
+            if ((f & 2) && valid && gi == R.istar[p]) R.fdist[v] = (uint32_t)d;
+        }
     }
 }
 

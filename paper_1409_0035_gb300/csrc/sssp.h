@@ -40,6 +40,14 @@ struct ReduceJob {
     uint32_t *hist;                 // (D+1) x k
     const uint64_t *Lmask;          // n x W
     uint64_t *lc2;                  // n x 2
+    // error estimate (null sqflag: not wanted): per node flag 1 adds
+    // (d(c_i, v) - d(c(v), c_i))^2 over c_i outside Lmask into the 128-bit
+    // hcse[v] = {lo, hi}; flag 2 records fdist[v] = d(c_i, v) for
+    // c_i = istar[c(v)]
+    const uint8_t *sqflag;
+    const int32_t *istar, *pivot;
+    uint64_t *hcse;                 // n x 2
+    uint32_t *fdist;                // n
 };
 
 int launch_mssp(const SsspJob &job, cudaStream_t st);
