@@ -181,6 +181,27 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k,
                 const cc_opts *opts, cc_out *out);
 
 /*
+ * cc_estimate_adaptive -- the adaptive hybrid ("Hyb.-ad", section 6; the
+ * error estimate of section 4): one first traversal pass, then for each
+ * eps = eps_num[e]/eps_den[e] of the list the hybrid estimate of eq. (4)
+ * and its SqErrEst (see cc_out.sq_err); every node keeps the estimate with
+ * the smallest SqErrEst (ties to the earlier entry).  eps_num = eps_den =
+ * NULL selects the paper's list 0.001, 0.025, 0.05, 0.1, 0.2, 0.5, 0.99
+ * (n_eps ignored).  Outputs, n each, host or device per
+ * opts->device_outputs, any may be NULL: s_hat (sampled nodes: exact S),
+ * closeness (n-1)/s_hat, sq_err (0 for sampled nodes), choice (the entry
+ * used; -1 for sampled nodes).  opts->eps_* and want_hybrid are ignored;
+ * roundtrip must match the graph.  Each entry costs the ε-dependent part of
+ * cc_estimate again: thresholds and, where some node needs it, the second
+ * traversal pass.  Errors: as cc_estimate; CC_ERR_ARG for n_eps outside
+ * 1..64 or an entry with eps_num = 0 or eps_num > eps_den.
+ */
+int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k,
+                         const cc_opts *opts, int32_t n_eps, const uint32_t *eps_num,
+                         const uint32_t *eps_den, double *s_hat, double *closeness,
+                         double *sq_err, int32_t *choice);
+
+/*
  * cc_exact -- exact S(v) and B^-1(v) = (n-1)/S(v) for every node (eq. (1))
  * by traversals from every node, packed 64 per word.  Meant for small
  * graphs (the cost is n traversals).  closeness double[n], S uint64[n] (host,

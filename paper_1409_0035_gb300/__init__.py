@@ -38,6 +38,7 @@ EXPORTS = (
     "cc_batch_info", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
+    "cc_estimate_adaptive",
 )
 
 PHASES = ("init", "td_queue", "td_push", "td_final", "bu_rebuild", "bu_light",
@@ -87,6 +88,7 @@ def lib():
         L.cc_opts_default.argtypes = [P, i32]
         L.cc_opts_default.restype = None
         L.cc_estimate.argtypes = [P, P, i32, P, P]
+        L.cc_estimate_adaptive.argtypes = [P, P, i32, P, i32, P, P, P, P, P, P]
         L.cc_exact.argtypes = [P, P, P]
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
@@ -227,6 +229,33 @@ def cc_estimate(g, sample, opts=None, out=None, want_sqerr=False):
         o.sq_err = _p(res["sq_err"])
     _chk(lib().cc_estimate(g, _p(sample), k, ctypes.byref(opts), ctypes.byref(o)),
          "cc_estimate")
+    return res
+
+
+ADAPTIVE_EPS = ((1, 1000), (1, 40), (1, 20), (1, 10), (1, 5), (1, 2), (99, 100))
+
+
+def cc_estimate_adaptive(g, sample, opts=None, eps_list=None):
+    """Adaptive hybrid: per node the eq. (4) estimate of the eps (from
+    eps_list, default the paper's seven values) with the smallest SqErrEst.
+    Returns a dict of host arrays s_hat, closeness, sq_err, choice."""
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    k = sample.size
+    if opts is None:
+        opts = cc_opts_default(k)
+    n = cc_graph_info(g)[0]
+    res = dict(s_hat=np.empty(n), closeness=np.empty(n), sq_err=np.empty(n),
+               choice=np.empty(n, np.int32))
+    if eps_list is None:
+        ne, a, b = 0, None, None
+    else:
+        ne = len(eps_list)
+        a = np.ascontiguousarray([e[0] for e in eps_list], np.uint32)
+        b = np.ascontiguousarray([e[1] for e in eps_list], np.uint32)
+    _chk(lib().cc_estimate_adaptive(g, _p(sample), k, ctypes.byref(opts), ne, _p(a), _p(b),
+                                    _p(res["s_hat"]), _p(res["closeness"]),
+                                    _p(res["sq_err"]), _p(res["choice"])),
+         "cc_estimate_adaptive")
     return res
 
 

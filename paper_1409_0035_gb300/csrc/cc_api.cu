@@ -68,7 +68,10 @@ struct cc_graph {
     // error estimate of the hybrid (SqErrEst): squared errors, fallback
     // distances, per-node flags, farthest-sample table, staged output
     DevBuf hcse, fdist, sqflag, istar, sqe;
+    // adaptive hybrid: one eps's estimate and error, the best so far, choice
+    DevBuf ad_est, ad_sq, ad_best, ad_bsq, ad_clo, ad_choice;
     bool sq = false;       // the current cc_estimate call wants SqErrEst
+    int64_t D1 = 0;        // levels (largest distance) of the last first pass
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
@@ -333,7 +336,8 @@ void free_graph(cc_graph *g)
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
                      &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
-                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe};
+                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
+                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -358,7 +362,9 @@ int prepare_sq(cc_graph *g, int k, cudaStream_t st)
     return CC_OK;
 }
 
-int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+// First pass of the bit-packed path: sums, pivots, Delta, delta_cc, the
+// per-source level histogram and the exact S of the sampled nodes.
+int bfs_pass1(cc_graph *g, int k, cudaStream_t st)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
@@ -390,10 +396,21 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
     const int D = g->last.levels;
     g->dist_max = D;
+    g->D1 = D;
     run_S_sampled(g->hist.as<uint32_t>(), D, k, g->dcc.as<uint32_t>(),
                   g->Ssamp.as<uint64_t>(), st);
     g->call_kernels += 1;
-    if (!opts->want_hybrid) return CC_OK;
+    return CC_OK;
+}
+
+// The hybrid part of the bit-packed path for eps = a/b, after bfs_pass1:
+// H statistics from the histogram tails, thresholds, L-masks and, where
+// needed, the second pass.
+int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const int W = pow2_words(k);
+    const int64_t D = g->D1;
     RC(g->TN.ensure((size_t)k * (D + 1) * 8));
     RC(g->TS.ensure((size_t)k * (D + 1) * 8));
     RC(g->maxd.ensure((size_t)k * 4));
@@ -409,7 +426,7 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
         RC(prepare_sq(g, k, st));
         sq.flag = g->sqflag.as<uint8_t>();
     }
-    run_hyb_prep(3, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+    run_hyb_prep(3, n, k, D, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
                  g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), sq, st);
@@ -444,6 +461,13 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
         j2.fdist = g->fdist.as<uint32_t>();
     }
     return run_pass(g, W, j2, st);
+}
+
+int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+{
+    RC(bfs_pass1(g, k, st));
+    if (!opts->want_hybrid) return CC_OK;
+    return bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st);
 }
 
 // One 32-source chunk of shortest paths (forward, and reversed for round
@@ -526,7 +550,10 @@ ReduceJob base_reduce(cc_graph *g, int k, int W)
 // Weighted or directed (round-trip) graphs: the k sources in 32-source
 // chunks of shortest paths, each reduced into the same per-node statistics;
 // the hybrid needs a second sweep (histogram of distances and L(v) sums).
-int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+// First pass of the chunked path (weighted graphs, round trips): 32-source
+// chunks of shortest paths reduced into sums, pivots, Delta, delta_cc and
+// the exact S of the sampled nodes.
+int chunked_pass1(cc_graph *g, int k, cudaStream_t st)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
@@ -564,9 +591,20 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
                      g->delta.as<uint32_t>(), st);
     g->call_kernels += 1;
     g->dist_max = (int64_t)dmax;
-    if (!opts->want_hybrid) return CC_OK;
+    g->D1 = (int64_t)dmax;
+    return CC_OK;
+}
 
-    const int64_t D = (int64_t)dmax;
+// The hybrid part of the chunked path for eps = a/b, after chunked_pass1:
+// thresholds and L-masks, the chunks again for the distance histogram and
+// the L(v) n C sums, then the H statistics from the histogram tails.
+int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const int W = pow2_words(k);
+    const int32_t *src = g->sources.as<int32_t>();
+    ReduceJob r = base_reduce(g, k, W);
+    const int64_t D = g->D1;
     if ((double)(D + 1) * k * 4.0 > (double)kMaxHistBytes) return CC_ERR_TOO_LARGE;
     // Sums of squared distances (LCsumSq) stay in 64 bits.
     if ((double)D * (double)D * (double)k >= 1.8e19) return CC_ERR_TOO_LARGE;
@@ -587,7 +625,7 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
         RC(prepare_sq(g, k, st));
         sq.flag = g->sqflag.as<uint8_t>();
     }
-    run_hyb_prep(1, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+    run_hyb_prep(1, n, k, D, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), nullptr, nullptr, g->hp.as<HybPrep>(),
                  g->npartial.as<unsigned>(), sq, st);
@@ -613,12 +651,19 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
         g->call_kernels += 1;
     }
     run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
-    run_hyb_prep(2, n, k, D, opts->eps_num, opts->eps_den, g->sidx.as<int32_t>(),
+    run_hyb_prep(2, n, k, D, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
                  g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), SqPrep{nullptr}, st);
     g->call_kernels += 2;
     return CC_OK;
+}
+
+int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+{
+    RC(chunked_pass1(g, k, st));
+    if (!opts->want_hybrid) return CC_OK;
+    return chunked_hybrid(g, k, opts->eps_num, opts->eps_den, st);
 }
 
 // Finalise into device buffers (or straight into device outputs) and copy.
@@ -737,7 +782,8 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
                           &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
-                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe};
+                     &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
+                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;
@@ -992,6 +1038,87 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *o
                                                 : estimate_bfs(g, k, opts, st);
     if (rc != CC_OK) return rc;
     return finish_outputs(g, k, hyb, opts, out, st);
+}
+
+int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *opts,
+                         int32_t n_eps, const uint32_t *eps_num, const uint32_t *eps_den,
+                         double *s_hat, double *closeness, double *sq_err, int32_t *choice)
+{
+    static const uint32_t kNum[] = {1, 1, 1, 1, 1, 1, 99};
+    static const uint32_t kDen[] = {1000, 40, 20, 10, 5, 2, 100};
+    if (!g || !opts) return CC_ERR_ARG;
+    if (!eps_num || !eps_den) {
+        if (eps_num || eps_den) return CC_ERR_ARG;
+        n_eps = 7;
+        eps_num = kNum;
+        eps_den = kDen;
+    }
+    if (n_eps < 1 || n_eps > 64) return CC_ERR_ARG;
+    for (int e = 0; e < n_eps; ++e)
+        if (eps_num[e] == 0 || eps_num[e] > eps_den[e]) return CC_ERR_ARG;
+    if ((opts->roundtrip != 0) != g->directed) return CC_ERR_ARG;
+    RC(validate_sample(g, sample, k));
+    reset_timing(g);
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const int64_t n = g->n;
+    RC(g->sidx.ensure(n * 4));
+    RC(g->sum2.ensure(n * 16));
+    RC(g->pivot.ensure(n * 4));
+    RC(g->delta.ensure(n * 4));
+    RC(g->dcc.ensure((size_t)k * k * 4));
+    RC(g->Ssamp.ensure((size_t)k * 8));
+    RC(g->sources.ensure((size_t)k * 4));
+    RC(g->ctl.ensure(sizeof(Ctl)));
+    RC(g->ad_est.ensure((size_t)n * 8));
+    RC(g->ad_sq.ensure((size_t)n * 8));
+    RC(g->ad_best.ensure((size_t)n * 8));
+    RC(g->ad_bsq.ensure((size_t)n * 8));
+    RC(g->ad_clo.ensure((size_t)n * 8));
+    RC(g->ad_choice.ensure((size_t)n * 4));
+    CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
+    run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
+    g->call_kernels += 2;
+    const bool chunked = g->weighted || g->directed;
+    RC(chunked ? chunked_pass1(g, k, st) : bfs_pass1(g, k, st));
+    g->sq = true;
+    for (int e = 0; e < n_eps; ++e) {
+        RC(chunked ? chunked_hybrid(g, k, eps_num[e], eps_den[e], st)
+                   : bfs_hybrid(g, k, eps_num[e], eps_den[e], st));
+        FinalizeArgs fa{};
+        fa.n = n;
+        fa.k = k;
+        fa.hybrid = 1;
+        fa.sidx = g->sidx.as<int32_t>();
+        fa.pivot = g->pivot.as<int32_t>();
+        fa.delta = g->delta.as<uint32_t>();
+        fa.sum2 = g->sum2.as<uint64_t>();
+        fa.S_samp = g->Ssamp.as<uint64_t>();
+        fa.lc2 = g->lc2.as<uint64_t>();
+        fa.hp = g->hp.as<HybPrep>();
+        fa.s_hat[CC_EST_HYBRID] = g->ad_est.as<double>();
+        fa.sq_err = g->ad_sq.as<double>();
+        fa.hcse = g->hcse.as<uint64_t>();
+        fa.fdist = g->fdist.as<uint32_t>();
+        fa.dcc = g->dcc.as<uint32_t>();
+        fa.istar = g->istar.as<int32_t>();
+        run_finalize(fa, st);
+        run_adaptive_select(n, e, g->sidx.as<int32_t>(), g->ad_est.as<double>(),
+                            g->ad_sq.as<double>(), g->ad_best.as<double>(),
+                            g->ad_bsq.as<double>(), g->ad_choice.as<int32_t>(), st);
+        g->call_kernels += 2;
+    }
+    g->sq = false;
+    run_closeness(n, g->ad_best.as<double>(), g->ad_clo.as<double>(), st);
+    g->call_kernels += 1;
+    const cudaMemcpyKind kind =
+        opts->device_outputs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (s_hat) CK(cudaMemcpyAsync(s_hat, g->ad_best.p, n * 8, kind, st));
+    if (closeness) CK(cudaMemcpyAsync(closeness, g->ad_clo.p, n * 8, kind, st));
+    if (sq_err) CK(cudaMemcpyAsync(sq_err, g->ad_bsq.p, n * 8, kind, st));
+    if (choice) CK(cudaMemcpyAsync(choice, g->ad_choice.p, n * 4, kind, st));
+    CK(cudaStreamSynchronize(st));
+    return CC_OK;
 }
 
 int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)

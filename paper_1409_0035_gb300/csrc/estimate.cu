@@ -111,6 +111,44 @@ void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                                                  dcc, maxd, TN, TS, hp, npartial, sq);
 }
 
+// Adaptive hybrid (section 6): keep, per node, the estimate of the eps with
+// the smallest error estimate so far (entry e of the list; ties keep the
+// earlier one); sampled nodes keep their exact S, error 0 and choice -1.
+__global__ void k_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *est,
+                                  const double *sq, double *best_est, double *best_sq,
+                                  int32_t *choice)
+{
+    for (int64_t v = GSTART; v < n; v += GSTRIDE) {
+        if (sidx[v] >= 0) {
+            best_est[v] = est[v];
+            best_sq[v] = 0.0;
+            choice[v] = -1;
+        } else if (e == 0 || sq[v] < best_sq[v]) {
+            best_est[v] = est[v];
+            best_sq[v] = sq[v];
+            choice[v] = e;
+        }
+    }
+}
+
+__global__ void k_closeness(int64_t n, const double *s_hat, double *clo)
+{
+    for (int64_t v = GSTART; v < n; v += GSTRIDE) clo[v] = (double)(n - 1) / s_hat[v];
+}
+
+void run_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *est,
+                         const double *sq, double *best_est, double *best_sq, int32_t *choice,
+                         cudaStream_t st)
+{
+    k_adaptive_select<<<grid_for(n, 256), 256, 0, st>>>(n, e, sidx, est, sq, best_est, best_sq,
+                                                        choice);
+}
+
+void run_closeness(int64_t n, const double *s_hat, double *clo, cudaStream_t st)
+{
+    k_closeness<<<grid_for(n, 256), 256, 0, st>>>(n, s_hat, clo);
+}
+
 void run_istar(const uint32_t *dcc, int k, int32_t *istar, cudaStream_t st)
 {
     k_istar<<<(k + 127) / 128, 128, 0, st>>>(dcc, k, istar);

@@ -54,6 +54,10 @@ void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
                   const uint64_t *TS, HybPrep *hp, unsigned *npartial, const SqPrep &sq,
                   cudaStream_t st);
 void run_istar(const uint32_t *dcc, int k, int32_t *istar, cudaStream_t st);
+void run_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *est,
+                         const double *sq, double *best_est, double *best_sq, int32_t *choice,
+                         cudaStream_t st);
+void run_closeness(int64_t n, const double *s_hat, double *clo, cudaStream_t st);
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
                const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st);
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);

@@ -90,3 +90,54 @@ def test_sqerr_full_sample_is_zero(cc):
     n, s, d = synth.cycle_edges(64)
     r, _, se = run(cc, n, s, d, None, False, 64, (1, 2))
     assert not r["sq_err"].any() and not se.any()
+
+
+ADAPTIVE_CASES = [
+    ("rmat10 k=64", lambda: synth.rmat_edges(10, 8, seed=3), None, False, 64),
+    ("grid 36x28 k=40", lambda: synth.grid_edges(36, 28), None, False, 40),
+    ("ws 800 k=100", lambda: synth.watts_strogatz_edges(800, 10, 0.05, seed=6), None, False,
+     100),
+    ("rmat9 weighted k=50", lambda: synth.rmat_edges(9, 8, seed=7), "w", False, 50),
+    ("rmat9 round trips k=30", lambda: synth.rmat_edges(9, 8, seed=9), None, True, 30),
+]
+
+
+@pytest.mark.parametrize("case", ADAPTIVE_CASES, ids=[c[0] for c in ADAPTIVE_CASES])
+def test_adaptive_matches_oracle(cc, case):
+    """Adaptive hybrid (section 6) over the paper's eps list: the chosen eps
+    bit-exact, estimate and error within 1e-12."""
+    _, gen, wkind, directed, k = case
+    n, s, d = gen()
+    w = synth.random_weights(s.size, 1, 9, seed=8) if wkind else None
+    g, _ = cc.cc_graph_from_edges(n, s, d, w, directed=directed, keep_component=True)
+    og = orc.csr_from_edges(n, s, d, w=w, directed=directed, keep_component=True)
+    try:
+        C = orc.choose_sample(og.n, k, 2)
+        o = cc.cc_opts_default(k)
+        o.roundtrip = int(directed)
+        r = cc.cc_estimate_adaptive(g, C, o)
+    finally:
+        cc.cc_graph_free(g)
+    T = orc.dist_table(og, C, roundtrip=directed)
+    s_hat, se, choice = orc.adaptive_from_table(T, C)
+    assert (r["choice"] == choice).all()
+    assert close(r["s_hat"], s_hat).all()
+    assert close(r["sq_err"], se).all()
+    assert close(r["closeness"], (og.n - 1) / s_hat).all()
+    assert len(set(choice[choice >= 0].tolist())) >= 2  # more than one eps wins somewhere
+
+
+def test_adaptive_custom_list_single_eps_is_fixed_hybrid(cc):
+    """A one-entry list is the fixed-eps hybrid with its error estimate."""
+    n, s, d = synth.rmat_edges(10, 8, seed=11)
+    g, _ = cc.cc_graph_from_edges(n, s, d, keep_component=True)
+    try:
+        C = orc.choose_sample(cc.cc_graph_info(g)[0], 80, 4)
+        ad = cc.cc_estimate_adaptive(g, C, eps_list=[(1, 3)])
+        o = cc.cc_opts_default(80)
+        o.eps_num, o.eps_den = 1, 3
+        fx = cc.cc_estimate(g, C, o, want_sqerr=True)
+    finally:
+        cc.cc_graph_free(g)
+    assert np.array_equal(ad["s_hat"], fx["s_hat"][3])
+    assert np.array_equal(ad["sq_err"], fx["sq_err"])
