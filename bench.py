@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--pool", default="default", choices=["default", "paper"],
                     help="serve workload: graph pool (paper: R-MAT to scale 22, grids to 4096^2)")
     ap.add_argument("--workload", default="rmat20",
-                    choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve"],
+                    choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive"],
                     help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
@@ -524,6 +524,31 @@ def run_extra(args):
             "warmup": args.warmup, "data": "synthetic", "workload": args.workload}
     if args.workload == "serve":
         line.update(run_serve(args, cc))
+    elif args.workload == "adaptive":
+        # The headline graph and sample under the error estimate (one eps)
+        # and the adaptive hybrid (seven eps values), against the plain
+        # hybrid: what SqErrEst and Hyb.-ad cost on top of eq. (4).
+        n, s, d = synth.rmat_edges(SCALE, EF, seed=GSEED)
+        g, _ = cc.cc_graph_from_edges(n, s, d)
+        nn, arcs, _, _ = cc.cc_graph_info(g)
+        m = arcs // 2
+        C = cc.cc_sample_choose(g, K, SSEED)
+        o = cc.cc_opts_default(K)
+        plain = _time_steps(lambda: cc.cc_estimate(g, C, o), args.steps, args.warmup, flush)
+        sq = _time_steps(lambda: cc.cc_estimate(g, C, o, want_sqerr=True), args.steps,
+                         args.warmup, flush)
+        ad = _time_steps(lambda: cc.cc_estimate_adaptive(g, C, o), args.steps, args.warmup,
+                         flush)
+        ch = cc.cc_estimate_adaptive(g, C, o)["choice"]
+        line.update(metric="all-node estimates/s", unit="estimates/s",
+                    value=nn / (ad / 1e3), ms_per_step=ad,
+                    plain_hybrid_ms=plain, with_sqerr_ms=sq, adaptive_ms=ad,
+                    eps_chosen={str(e): int((ch == i).sum())
+                                for i, e in enumerate(cc.ADAPTIVE_EPS)},
+                    note="host outputs; each call includes the device-to-host copies",
+                    config={"workload": "adaptive", "graph": f"R-MAT scale {SCALE}, edge "
+                            f"factor {EF}, seed {GSEED}, LCC", "n": nn, "m": m, "k": K})
+        cc.cc_graph_free(g)
     elif args.workload == "batch64":
         specs = batch64_graphs()
         handles, samples, work, kinds = [], [], 0, []
