@@ -11,9 +11,16 @@
 namespace ccg {
 
 constexpr int kBlock = 256;          // threads per CTA of the traversal kernel
-constexpr int kLightMaxDeg = 32;     // thread-per-(node, word) scan
-constexpr int kMediumMaxDeg = 256;   // warp-per-node scan
-constexpr int kChunk = 256;          // CSR entries per heavy-node warp task
+// Degree classes of the traversal (build-time tunables).
+#ifndef CC_MEDIUM_MAX_DEG
+#define CC_MEDIUM_MAX_DEG 128
+#endif
+#ifndef CC_CHUNK
+#define CC_CHUNK 256
+#endif
+constexpr int kLightMaxDeg = 32;                 // thread-per-(node, word) scan
+constexpr int kMediumMaxDeg = CC_MEDIUM_MAX_DEG;  // warp-per-node scan
+constexpr int kChunk = CC_CHUNK;                 // CSR entries per heavy-node warp task
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 
 // Reductions a traversal pass performs (bit set).

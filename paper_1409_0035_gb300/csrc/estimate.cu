@@ -26,7 +26,7 @@ __global__ void k_scatter_sidx(int32_t *sidx, const int32_t *src, int k)
 __global__ void k_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc,
                             uint64_t *S)
 {
-    d_S_sampled(hist, D, k, dcc, S, GSTART, GSTRIDE);
+    d_S_sampled(hist, D, k, dcc, S, GSTART >> 5, GSTRIDE >> 5);
 }
 
 __global__ void k_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS)
@@ -36,7 +36,7 @@ __global__ void k_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uin
 
 __global__ void k_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd)
 {
-    d_maxdelta(dcc, k, maxd, GSTART, GSTRIDE);
+    d_maxdelta(dcc, k, maxd, GSTART >> 5, GSTRIDE >> 5);
 }
 
 __global__ void k_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
@@ -87,7 +87,7 @@ void run_scatter_sidx(int32_t *sidx, const int32_t *src, int k, cudaStream_t st)
 void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint64_t *S,
                    cudaStream_t st)
 {
-    k_S_sampled<<<(k + 127) / 128, 128, 0, st>>>(hist, D, k, dcc, S);
+    k_S_sampled<<<(k + 7) / 8, 256, 0, st>>>(hist, D, k, dcc, S);
 }
 
 void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS,
@@ -98,7 +98,7 @@ void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS
 
 void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
 {
-    k_maxdelta<<<(k + 127) / 128, 128, 0, st>>>(dcc, k, maxd);
+    k_maxdelta<<<(k + 7) / 8, 256, 0, st>>>(dcc, k, maxd);
 }
 
 void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,

@@ -43,16 +43,20 @@ __device__ __forceinline__ void d_scatter_sidx(int32_t *sidx, const int32_t *src
 }
 
 // S(c_i) = sum over levels l of l * |{v not in C at distance l}| plus the
-// distances to the sampled nodes (row i of delta_cc).
+// distances to the sampled nodes (row i of delta_cc).  A warp per source
+// (warp w0 of nw), lanes striding over the levels and the row.
 __device__ __forceinline__ void d_S_sampled(const uint32_t *hist, int D, int k,
-                                            const uint32_t *dcc, uint64_t *S, int64_t i0,
-                                            int64_t stride)
+                                            const uint32_t *dcc, uint64_t *S, int64_t w0,
+                                            int64_t nw)
 {
-    for (int64_t i = i0; i < k; i += stride) {
-        uint64_t s = 0;
-        for (int l = 1; l <= D; ++l) s += (uint64_t)l * hist[(int64_t)l * k + i];
-        for (int j = 0; j < k; ++j) s += dcc[i * k + j];
-        S[i] = s;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = w0; i < k; i += nw) {
+        unsigned long long s = 0;
+        for (int l = 1 + lane; l <= D; l += 32) s += (uint64_t)l * hist[(int64_t)l * k + i];
+        for (int j = lane; j < k; j += 32) s += dcc[i * k + j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) S[i] = s;
     }
 }
 
@@ -91,13 +95,18 @@ __device__ __forceinline__ void d_tail_source(const uint32_t *hist, int64_t D, i
     }
 }
 
+// maxd[p] = largest distance from c_p to a sampled node: a warp per row
+// (warp w0 of nw).
 __device__ __forceinline__ void d_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd,
-                                           int64_t i0, int64_t stride)
+                                           int64_t w0, int64_t nw)
 {
-    for (int64_t p = i0; p < k; p += stride) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t p = w0; p < k; p += nw) {
         uint32_t m = 0;
-        for (int i = 0; i < k; ++i) m = max(m, dcc[p * k + i]);
-        maxd[p] = m;
+        for (int i = lane; i < k; i += 32) m = max(m, dcc[p * k + i]);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if (lane == 0) maxd[p] = m;
     }
 }
 

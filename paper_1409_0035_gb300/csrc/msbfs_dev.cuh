@@ -13,10 +13,21 @@ namespace {
 
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
+// Independent gathers in flight per lane and step: top-down pushes and
+// bottom-up scans of light nodes (kUnroll), of medium nodes (kUnrollM) and
+// of heavy chunk tasks (kUnrollH); build-time tunables.
 #ifndef CC_MSBFS_UNROLL
 #define CC_MSBFS_UNROLL 4
 #endif
-constexpr int kUnroll = CC_MSBFS_UNROLL;  // independent gathers in flight per lane and step
+#ifndef CC_MSBFS_UNROLL_M
+#define CC_MSBFS_UNROLL_M 4
+#endif
+#ifndef CC_MSBFS_UNROLL_H
+#define CC_MSBFS_UNROLL_H 4
+#endif
+constexpr int kUnroll = CC_MSBFS_UNROLL;
+constexpr int kUnrollM = CC_MSBFS_UNROLL_M;
+constexpr int kUnrollH = CC_MSBFS_UNROLL_H;
 
 __device__ __forceinline__ uint64_t gtimer()
 {
@@ -238,7 +249,7 @@ __device__ __forceinline__ void load_cols(const int32_t *__restrict__ col, int64
 // independent, so they are all in flight together.
 template <int W, int U>
 __device__ __forceinline__ uint64_t gather_cols(const uint64_t *Fin, const int (&c)[U], int w,
-                                                unsigned long long &words)
+                                                unsigned &words)
 {
     uint64_t f = 0;
 #pragma unroll
@@ -248,6 +259,19 @@ __device__ __forceinline__ uint64_t gather_cols(const uint64_t *Fin, const int (
             words += 1;
         }
     return f;
+}
+
+// Column indices row[x], row[x+stride], ... (U of them; -1 from len on),
+// with 32-bit offsets inside one row.
+template <int U>
+__device__ __forceinline__ void load_row(const int32_t *__restrict__ row, int x, int len,
+                                         int stride, int (&c)[U])
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int ee = x + u * stride;
+        c[u] = ee < len ? __ldg(row + ee) : -1;
+    }
 }
 
 // OR of the frontier words (word w) of the neighbours col[base + off],
@@ -262,17 +286,22 @@ __device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
                                                 int64_t e, int stride, int w,
                                                 unsigned long long &words, Done done)
 {
+    // Offsets inside the row are 32-bit (a degree is below 2^31).
+    const int32_t *row = col + base;
+    const int len = (int)(e - base);
     uint64_t acc = 0;
+    unsigned wl = 0;
     int c[U];
-    load_cols<U>(col, base + off, e, stride, c);
-    for (; base < e; base += (int64_t)U * stride) {
+    load_row<U>(row, off, len, stride, c);
+    for (int t = 0; t < len; t += U * stride) {
         int cn[U];
-        load_cols<U>(col, base + off + (int64_t)U * stride, e, stride, cn);
-        acc |= gather_cols<W, U>(Fin, c, w, words);
+        load_row<U>(row, t + off + U * stride, len, stride, cn);
+        acc |= gather_cols<W, U>(Fin, c, w, wl);
         if (done(acc)) break;
 #pragma unroll
         for (int u = 0; u < U; ++u) c[u] = cn[u];
     }
+    words += wl;
     return acc;
 }
 
@@ -697,7 +726,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t visw = J.vis[(int64_t)v * W + w];
                 if (__all_sync(FULL, visw == ~0ull)) continue;
                 const int64_t b = prp[v], e = prp[v + 1];
-                const uint64_t acc = gather_scan<W, kUnroll>(
+                const uint64_t acc = gather_scan<W, kUnrollM>(
                     pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
                         return __all_sync(FULL, (or_same_word<W>(a) | visw) == ~0ull);
                     });
@@ -716,7 +745,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
-                const uint64_t acc = gather_scan<W, kUnroll>(
+                const uint64_t acc = gather_scan<W, kUnrollH>(
                     pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
                         return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);
                     });
