@@ -233,18 +233,6 @@ __device__ __forceinline__ uint64_t or_same_word(uint64_t x)
     return x;
 }
 
-// Column indices of the U CSR entries x, x+stride, ... (-1 from e on).
-template <int U>
-__device__ __forceinline__ void load_cols(const int32_t *__restrict__ col, int64_t x, int64_t e,
-                                          int stride, int (&c)[U])
-{
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int64_t ee = x + (int64_t)u * stride;
-        c[u] = ee < e ? __ldg(col + ee) : -1;
-    }
-}
-
 // OR of the frontier words (slot w) of the columns in c; the U gathers are
 // independent, so they are all in flight together.
 template <int W, int U>
@@ -276,15 +264,16 @@ __device__ __forceinline__ void load_row(const int32_t *__restrict__ row, int x,
 
 // OR of the frontier words (word w) of the neighbours col[base + off],
 // col[base + off + stride], ... below e, U per step, until `done(acc)`
-// holds.  The step count depends on base, e, stride and `done` only, so it
-// is uniform over lanes that share them (`done` may be warp-collective).
-// The column indices of the next step are loaded while the current frontier
+// holds, tested after every chk-th step (a later test only scans more).
+// The step count depends on base, e, stride and `done` only, so it is
+// uniform over lanes that share them (`done` may be warp-collective).  The
+// column indices of the next step are loaded while the current frontier
 // words are in flight: a step costs one dependent round trip, not two.
 template <int W, int U, class Done>
 __device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
                                                 const uint64_t *Fin, int64_t base, int off,
                                                 int64_t e, int stride, int w,
-                                                unsigned long long &words, Done done)
+                                                unsigned long long &words, int chk, Done done)
 {
     // Offsets inside the row are 32-bit (a degree is below 2^31).
     const int32_t *row = col + base;
@@ -293,11 +282,15 @@ __device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
     unsigned wl = 0;
     int c[U];
     load_row<U>(row, off, len, stride, c);
+    int step = 0;
     for (int t = 0; t < len; t += U * stride) {
         int cn[U];
         load_row<U>(row, t + off + U * stride, len, stride, cn);
         acc |= gather_cols<W, U>(Fin, c, w, wl);
-        if (done(acc)) break;
+        if (++step == chk) {
+            step = 0;
+            if (done(acc)) break;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) c[u] = cn[u];
     }
@@ -427,15 +420,18 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
     const int grp = lane / W;
     if (f == 0ull) return;
     // The next step's column indices load while this step's visited words
-    // are in flight.
+    // are in flight; offsets inside the row are 32-bit.
+    const int32_t *row = col + b;
+    const int len = (int)(e - b);
+    unsigned wl = 0;
     int vn[kUnroll];
-    load_cols<kUnroll>(col, b + grp, e, NPW, vn);
-    for (int64_t base = b + grp; base < e; base += NPW * kUnroll) {
+    load_row<kUnroll>(row, grp, len, NPW, vn);
+    for (int t = grp; t < len; t += NPW * kUnroll) {
         int vv[kUnroll];
         uint64_t vs[kUnroll];
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) vv[q] = vn[q];
-        load_cols<kUnroll>(col, base + (int64_t)NPW * kUnroll, e, NPW, vn);
+        load_row<kUnroll>(row, t + NPW * kUnroll, len, NPW, vn);
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q)
             vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + w] : ~0ull;
@@ -443,7 +439,7 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
         for (int q = 0; q < kUnroll; ++q) {
             if (vv[q] < 0) continue;
             const int v = vv[q];
-            A.words += 1;
+            wl += 1;
             const uint64_t nbits = f & ~vs[q];
             if (!nbits) continue;
             const uint64_t old =
@@ -452,6 +448,7 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
                 stage_push(stage, v, Tout, &C->tlen);
         }
     }
+    A.words += wl;
 }
 
 // One traversal pass of job J on the team (team_rank, team_size); barriers
@@ -567,6 +564,10 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         const unsigned tprev = P->tlen;
         const unsigned long long ef = P->ef;
         eu -= (long long)P->eu_dec;
+        // The warp-wide completion test of the medium and heavy scans (a
+        // shuffle reduction) runs every 4th step while the last level
+        // completed no node, every step once nodes complete.
+        const int chk = P->ninc_dec == 0 ? 4 : 1;
         ninc -= (long long)P->ninc_dec;
         if (qprev > 0) last = l - 1;
         if (qprev == 0 || ninc == 0) break;
@@ -713,7 +714,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 if (valid) { b = prp[v]; e = prp[v + 1]; }
                 uint64_t acc = 0;
                 if (vis != ~0ull)
-                    acc = gather_scan<W, kUnroll>(pcol, Fin, b, 0, e, 1, w, A.words,
+                    acc = gather_scan<W, kUnroll>(pcol, Fin, b, 0, e, 1, w, A.words, 1,
                                                   [&](uint64_t a) { return (a | vis) == ~0ull; });
                 __syncwarp();
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, e - b, Fout, A, s_hist,
@@ -727,7 +728,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 if (__all_sync(FULL, visw == ~0ull)) continue;
                 const int64_t b = prp[v], e = prp[v + 1];
                 const uint64_t acc = gather_scan<W, kUnrollM>(
-                    pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
+                    pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
                         return __all_sync(FULL, (or_same_word<W>(a) | visw) == ~0ull);
                     });
                 const uint64_t r = or_same_word<W>(acc);
@@ -746,7 +747,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) continue;
                 const uint64_t acc = gather_scan<W, kUnrollH>(
-                    pcol, Fin, b, grp, e, NPW, w, A.words, [&](uint64_t a) {
+                    pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
                         return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);
                     });
                 const uint64_t nbits = or_same_word<W>(acc) & ~visw & ~cur;
