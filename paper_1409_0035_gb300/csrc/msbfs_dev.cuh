@@ -721,19 +721,38 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                                false);
             }
             lap(CC_PH_BU_LIGHT);
-            // A2: medium nodes, one warp per node.
-            for (int64_t t = gwarp; t < ml_len; t += nwarps) {
-                const int v = MLcur[t];
-                const uint64_t visw = J.vis[(int64_t)v * W + w];
-                if (__all_sync(FULL, visw == ~0ull)) continue;
-                const int64_t b = prp[v], e = prp[v + 1];
-                const uint64_t acc = gather_scan<W, kUnrollM>(
-                    pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
-                        return __all_sync(FULL, (or_same_word<W>(a) | visw) == ~0ull);
-                    });
-                const uint64_t r = or_same_word<W>(acc);
-                tile_reduce<W>(J, l, lane < W, v, visw, r & ~visw, e - b, Fout, A, s_hist,
-                               false);
+            // A2: medium nodes, a warp per node.  The warp scans NPW of its
+            // nodes one after another, lane group g keeping node g's words,
+            // then one fused reduction covers all NPW.
+            for (int64_t t0 = gwarp; t0 < ml_len; t0 += (int64_t)NPW * nwarps) {
+                int myv = 0;
+                uint64_t myvis = ~0ull, myres = 0;
+                int64_t mydeg = 0;
+                bool myvalid = false;
+                for (int g = 0; g < NPW; ++g) {
+                    const int64_t t = t0 + (int64_t)g * nwarps;
+                    if (t >= ml_len) break;
+                    const int v = MLcur[t];
+                    const uint64_t visw = J.vis[(int64_t)v * W + w];
+                    const int64_t b = prp[v], e = prp[v + 1];
+                    uint64_t r = 0;
+                    if (!__all_sync(FULL, visw == ~0ull)) {
+                        const uint64_t acc = gather_scan<W, kUnrollM>(
+                            pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
+                                return __all_sync(FULL, (or_same_word<W>(a) | visw) == ~0ull);
+                            });
+                        r = or_same_word<W>(acc);
+                    }
+                    if (grp == g) {
+                        myv = v;
+                        myvis = visw;
+                        myres = r;
+                        mydeg = e - b;
+                        myvalid = true;
+                    }
+                }
+                tile_reduce<W>(J, l, myvalid, myv, myvis, myres & ~myvis, mydeg, Fout, A,
+                               s_hist, false);
             }
             lap(CC_PH_BU_MEDIUM);
             // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.
