@@ -407,8 +407,10 @@ __device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsig
 // Top-down push of one frontier node's words f (slot w per lane) to the
 // CSR entries [b, e): new bits are OR-ed into nxt and each node reached for
 // the first time this level is appended (once) to the touched list.  Called
-// by a whole warp; lane groups of W take NPW entries per step, kUnroll steps
-// at a time.
+// by a whole warp.  When every word has bits, lane groups of W take NPW
+// entries per step; otherwise the words with bits are pushed one after
+// another by all 32 lanes (a word per lane group would leave the lanes of
+// empty words idle).  kUnroll entries per lane and step.
 template <int W>
 __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restrict__ col,
                                         uint64_t f, int64_t b, int64_t e, LevelCtl *C,
@@ -418,12 +420,46 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
     const int lane = threadIdx.x & 31;
     const int w = lane & (W - 1);
     const int grp = lane / W;
-    if (f == 0ull) return;
-    // The next step's column indices load while this step's visited words
-    // are in flight; offsets inside the row are 32-bit.
     const int32_t *row = col + b;
     const int len = (int)(e - b);
     unsigned wl = 0;
+    const unsigned S = __ballot_sync(FULL, f != 0ull) &
+                       (W == 32 ? 0xFFFFFFFFu : ((1u << W) - 1u));
+    if (S == 0u) return;
+    if (__popc(S) < W) {
+        for (unsigned s = S; s; s &= s - 1) {
+            const int ww = __ffs(s) - 1;
+            const uint64_t fw = __shfl_sync(FULL, f, ww);
+            int vn[kUnroll];
+            load_row<kUnroll>(row, lane, len, 32, vn);
+            for (int t = lane; t < len; t += 32 * kUnroll) {
+                int vv[kUnroll];
+                uint64_t vs[kUnroll];
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) vv[q] = vn[q];
+                load_row<kUnroll>(row, t + 32 * kUnroll, len, 32, vn);
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q)
+                    vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + ww] : ~0ull;
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    if (vv[q] < 0) continue;
+                    const int v = vv[q];
+                    wl += 1;
+                    const uint64_t nbits = fw & ~vs[q];
+                    if (!nbits) continue;
+                    const uint64_t old =
+                        atomicOr((unsigned long long *)&J.nxt[(int64_t)v * W + ww], nbits);
+                    if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u)
+                        stage_push(stage, v, Tout, &C->tlen);
+                }
+            }
+        }
+        A.words += wl;
+        return;
+    }
+    // The next step's column indices load while this step's visited words
+    // are in flight; offsets inside the row are 32-bit.
     int vn[kUnroll];
     load_row<kUnroll>(row, grp, len, NPW, vn);
     for (int t = grp; t < len; t += NPW * kUnroll) {
@@ -614,14 +650,28 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t f = Fin[(int64_t)u * W + w];
                 td_push<W>(J, col, f, b, e, C, Tout, A, stage);
             }
-            for (int64_t t = gwarp; t < J.ntH; t += nwarps) {
-                const int u = J.tHn[t];
-                if (J.fstamp[u] != (unsigned)(l - 1)) continue;
-                const uint64_t f = Fin[(int64_t)u * W + w];
-                if (__all_sync(FULL, f == 0ull)) continue;
-                const int64_t b = J.tHb[t];
-                td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[u + 1]), C, Tout, A,
-                           stage);
+            // Heavy frontier nodes: the warp's chunk tasks (every nwarps-th)
+            // are tested 32 at a time, a lane each, and only those of nodes
+            // that gained bits last level are pushed, by the whole warp.
+            for (int64_t j0 = 0; gwarp + j0 * nwarps < J.ntH; j0 += 32) {
+                const int64_t t = gwarp + (j0 + lane) * nwarps;
+                int u = 0;
+                bool act = false;
+                if (t < J.ntH) {
+                    u = J.tHn[t];
+                    act = J.fstamp[u] == (unsigned)(l - 1);
+                }
+                unsigned m = __ballot_sync(FULL, act);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int uu = __shfl_sync(FULL, u, src);
+                    const uint64_t f = Fin[(int64_t)uu * W + w];
+                    if (__all_sync(FULL, f == 0ull)) continue;
+                    const int64_t b = J.tHb[gwarp + (j0 + src) * nwarps];
+                    td_push<W>(J, col, f, b, min(b + (int64_t)kChunk, rp[uu + 1]), C, Tout,
+                               A, stage);
+                }
             }
             stage_flush(stage, Tout, &C->tlen);
             if (!sync_after(CC_PH_TD_PUSH)) return;
