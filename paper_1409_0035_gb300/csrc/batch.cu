@@ -83,10 +83,10 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
     d_S_sampled(B.hist, D, k, B.j.dcc, B.Ssamp, gtid >> 5, gthreads >> 5);
     if (B.want_hybrid) {
         for (int i = (int)rank; i < k; i += (int)size)
-            d_tail_source(B.hist, D, k, B.TN, B.TS, i);
+            d_tail_source(B.hist, D, k, B.TN, B.TS, i, D + 1);
         d_maxdelta(B.j.dcc, k, B.maxd, gtid >> 5, gthreads >> 5);
         if (!grid_sync(bar, rank, size, to)) return;
-        d_hyb_prep(3, n, k, D, B.a, B.b, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.maxd,
+        d_hyb_prep(3, n, k, D, D + 1, B.a, B.b, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.maxd,
                    B.TN, B.TS, B.hp, B.npartial, SqPrep{nullptr}, gtid, gthreads);
         if (!grid_sync(bar, rank, size, to)) return;
         if (*(volatile unsigned *)B.npartial > 0) {

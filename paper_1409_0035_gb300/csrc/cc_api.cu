@@ -83,6 +83,14 @@ struct cc_graph {
     int call_launches = 0, call_kernels = 0;
     double call_ms = 0.0, call_bytes = 0.0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // Traversal passes queued without waiting (slot 0: first pass, slot 1:
+    // second pass): their control blocks land in pinned hctl[slot] and are
+    // read once the call synchronises.
+    DevBuf ctl2;
+    Ctl *hctl = nullptr;
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int pend = 0, pend_W[2] = {0, 0};
+    uint32_t pend_red[2] = {0, 0};
 };
 
 namespace {
@@ -254,28 +262,58 @@ double pass_bytes(const Ctl &c, int64_t n, int W, uint32_t red)
            (double)c.td_levels * (n + 1) * 8.0 + (double)n * R;
 }
 
+// Queue one pass in slot 0 or 1 without waiting: its control block (slot
+// 1: g->ctl2) is cleared before and copied to the pinned g->hctl[slot]
+// after, between two events.  settle_passes reads them.
+int queue_pass(cc_graph *g, int slot, int W, BfsJob j, cudaStream_t st)
+{
+    if (!g->hctl) CK(cudaMallocHost(&g->hctl, 2 * sizeof(Ctl)));
+    for (cudaEvent_t &e : g->pev)
+        if (!e) CK(cudaEventCreate(&e));
+    if (slot == 1) RC(g->ctl2.ensure(sizeof(Ctl)));
+    Ctl *dctl = slot == 0 ? g->ctl.as<Ctl>() : g->ctl2.as<Ctl>();
+    j.ctl = dctl;
+    CK(cudaMemsetAsync(dctl, 0, sizeof(Ctl), st));
+    CK(cudaEventRecord(g->pev[2 * slot], st));
+    RC(launch_msbfs(W, j, st, nullptr));
+    CK(cudaEventRecord(g->pev[2 * slot + 1], st));
+    CK(cudaMemcpyAsync(&g->hctl[slot], dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    g->pend |= 1 << slot;
+    g->pend_W[slot] = W;
+    g->pend_red[slot] = j.red;
+    g->call_kernels += 1;
+    return CC_OK;
+}
+
+// After the stream has been synchronised: account the queued passes (a
+// second pass whose gate skipped it left a zero control block) and copy the
+// last one that ran to g->last.  Returns the first negative error code.
+int settle_passes(cc_graph *g)
+{
+    int rc = CC_OK;
+    for (int slot = 0; slot < 2; ++slot) {
+        if (!(g->pend & (1 << slot))) continue;
+        const Ctl &c = g->hctl[slot];
+        if (slot == 1 && c.levels == 0 && c.words == 0) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->pev[2 * slot], g->pev[2 * slot + 1]));
+        g->last = c;
+        g->last.edges = c.words / (unsigned long long)g->pend_W[slot];
+        g->call_launches += 1;
+        g->call_ms += ms;
+        g->call_bytes += pass_bytes(c, g->n, g->pend_W[slot], g->pend_red[slot]);
+        if (c.err < 0 && rc == CC_OK) rc = c.err;
+    }
+    g->pend = 0;
+    return rc;
+}
+
 // Launch one pass and wait for it; copies the control block to g->last.
 int run_pass(cc_graph *g, int W, const BfsJob &j, cudaStream_t st)
 {
-    if (!g->ev0) {
-        CK(cudaEventCreate(&g->ev0));
-        CK(cudaEventCreate(&g->ev1));
-    }
-    CK(cudaMemsetAsync(g->ctl.p, 0, sizeof(Ctl), st));
-    CK(cudaEventRecord(g->ev0, st));
-    RC(launch_msbfs(W, j, st, nullptr));
-    CK(cudaEventRecord(g->ev1, st));
-    CK(cudaMemcpyAsync(&g->last, g->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    RC(queue_pass(g, 0, W, j, st));
     CK(cudaStreamSynchronize(st));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
-    g->last.edges = g->last.words / (unsigned long long)W;
-    g->call_launches += 1;
-    g->call_kernels += 1;
-    g->call_ms += ms;
-    g->call_bytes += pass_bytes(g->last, g->n, W, j.red);
-    if (g->last.err < 0) return g->last.err;
-    return CC_OK;
+    return settle_passes(g);
 }
 
 int validate_sample(const cc_graph *g, const int32_t *sample, int32_t k)
@@ -342,6 +380,9 @@ void free_graph(cc_graph *g)
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     g->ev0 = g->ev1 = nullptr;
+    for (cudaEvent_t &e : g->pev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    if (g->hctl) { cudaFreeHost(g->hctl); g->hctl = nullptr; }
 }
 
 
@@ -378,28 +419,39 @@ int bfs_pass1(cc_graph *g, int k, cudaStream_t st)
     j.delta = g->delta.as<uint32_t>();
     j.dcc = g->dcc.as<uint32_t>();
     j.dcc_k = k;
-    for (;;) {
-        RC(g->hist.ensure((size_t)g->hist_cap * k * 4));
-        j.hist = g->hist.as<uint32_t>();
-        j.hist_cap = g->hist_cap;
-        CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
-        CK(cudaMemsetAsync(g->hist.p, 0, (size_t)g->hist_cap * k * 4, st));
-        CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
-        RC(run_pass(g, W, j, st));
-        if (g->last.err == 1) {  // histogram too short: grow and rerun
-            if (g->hist_cap > n) return CC_ERR_TOO_LARGE;
-            g->hist_cap = (int)std::min<int64_t>(n + 1, (int64_t)g->hist_cap * 4);
-            continue;
-        }
-        break;
-    }
-    if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
-    const int D = g->last.levels;
-    g->dist_max = D;
-    g->D1 = D;
-    run_S_sampled(g->hist.as<uint32_t>(), D, k, g->dcc.as<uint32_t>(),
-                  g->Ssamp.as<uint64_t>(), st);
+    // Queued without waiting: the kernels after it read the level count
+    // from the control block on the device, and check_pass1 looks at the
+    // outcome once the call has synchronised.
+    RC(g->hist.ensure((size_t)g->hist_cap * k * 4));
+    j.hist = g->hist.as<uint32_t>();
+    j.hist_cap = g->hist_cap;
+    CK(cudaMemsetAsync(g->sum2.p, 0, n * 16, st));
+    CK(cudaMemsetAsync(g->hist.p, 0, (size_t)g->hist_cap * k * 4, st));
+    CK(cudaMemsetAsync(g->dcc.p, 0, (size_t)k * k * 4, st));
+    RC(queue_pass(g, 0, W, j, st));
+    run_S_sampled(g->hist.as<uint32_t>(), DevCount{&g->ctl.as<Ctl>()->levels, 0}, k,
+                  g->dcc.as<uint32_t>(), g->Ssamp.as<uint64_t>(), st);
     g->call_kernels += 1;
+    return CC_OK;
+}
+
+// Outcome of the queued first pass, after the stream synchronised:
+// CC_ERR_DISCONNECTED when some node was never reached, 1 when the level
+// histogram was too short (the caller grows it and runs the call again).
+int check_pass1(cc_graph *g, bool hybrid, int k)
+{
+    const Ctl &c = g->hctl[0];
+    if (c.err == 1) {
+        if (g->hist_cap > g->n) return CC_ERR_TOO_LARGE;
+        g->hist_cap = (int)std::min<int64_t>(g->n + 1, (int64_t)g->hist_cap * 4);
+        return 1;
+    }
+    if (c.ninc_final != 0) return CC_ERR_DISCONNECTED;
+    g->dist_max = c.levels;
+    g->D1 = c.levels;
+    // Sums of squared levels (LCsumSq, the squared errors) stay in 64 bits.
+    if (hybrid && (double)c.levels * (double)c.levels * (double)k >= 1.8e19)
+        return CC_ERR_TOO_LARGE;
     return CC_OK;
 }
 
@@ -410,41 +462,41 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
-    const int64_t D = g->D1;
-    RC(g->TN.ensure((size_t)k * (D + 1) * 8));
-    RC(g->TS.ensure((size_t)k * (D + 1) * 8));
+    // The level count D of the first pass stays on the device; the tail
+    // tables have hist_cap >= D + 1 entries per source.
+    const DevCount D{&g->ctl.as<Ctl>()->levels, 0};
+    const int64_t stride = g->hist_cap;
+    RC(g->TN.ensure((size_t)k * stride * 8));
+    RC(g->TS.ensure((size_t)k * stride * 8));
     RC(g->maxd.ensure((size_t)k * 4));
     RC(g->hp.ensure((size_t)n * sizeof(HybPrep)));
     RC(g->npartial.ensure(8));
     CK(cudaMemsetAsync(g->npartial.p, 0, 8, st));
-    // Sums of squared levels (LCsumSq, the squared errors) stay in 64 bits.
-    if ((double)D * (double)D * (double)k >= 1.8e19) return CC_ERR_TOO_LARGE;
-    run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
+    run_tail(g->hist.as<uint32_t>(), D, stride, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
+             st);
     run_maxdelta(g->dcc.as<uint32_t>(), k, g->maxd.as<uint32_t>(), st);
     SqPrep sq{nullptr};
     if (g->sq) {
         RC(prepare_sq(g, k, st));
         sq.flag = g->sqflag.as<uint8_t>();
     }
-    run_hyb_prep(3, n, k, D, a, b, g->sidx.as<int32_t>(),
+    run_hyb_prep(3, n, k, D, stride, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
                  g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), sq, st);
     g->call_kernels += 3;
-    unsigned npart[2] = {0, 0};
-    CK(cudaMemcpyAsync(npart, g->npartial.p, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
     RC(g->lc2.ensure(n * 16));
     // The second pass gathers LCsum for nodes whose L(v) misses a sampled
     // node and, for the error estimate, the squared errors over HC(v) or
-    // the distance to the farthest sample where HC(v) is empty.
-    if (npart[0] == 0 && npart[1] == 0) return CC_OK;
+    // the distance to the farthest sample where HC(v) is empty.  It is
+    // queued regardless and exits at once (like the L-mask kernel) when the
+    // preparation counted no such node.
     RC(g->Lmask.ensure((size_t)n * W * 8));
     run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
-              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
+              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), g->npartial.as<unsigned>(), st);
     g->call_kernels += 1;
-    CK(cudaMemsetAsync(g->lc2.p, 0, n * 16, st));
     BfsJob j2 = base_job(g, W, g->fw, g->fw);
+    j2.gate = g->npartial.as<unsigned>();
     j2.k = k;
     j2.sources = g->sources.as<int32_t>();
     j2.red = RED_LC;
@@ -460,7 +512,7 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
         j2.hcse = g->hcse.as<uint64_t>();
         j2.fdist = g->fdist.as<uint32_t>();
     }
-    return run_pass(g, W, j2, st);
+    return queue_pass(g, 1, W, j2, st);
 }
 
 int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
@@ -625,12 +677,12 @@ int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
         RC(prepare_sq(g, k, st));
         sq.flag = g->sqflag.as<uint8_t>();
     }
-    run_hyb_prep(1, n, k, D, a, b, g->sidx.as<int32_t>(),
+    run_hyb_prep(1, n, k, DevCount{nullptr, D}, D + 1, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), nullptr, nullptr, g->hp.as<HybPrep>(),
                  g->npartial.as<unsigned>(), sq, st);
     run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
-              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), st);
+              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), nullptr, st);
     g->call_kernels += 3;
     r.hist = g->hist.as<uint32_t>();
     r.Lmask = g->Lmask.as<uint64_t>();
@@ -650,8 +702,9 @@ int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
         run_reduce2(r, st);
         g->call_kernels += 1;
     }
-    run_tail(g->hist.as<uint32_t>(), D, k, g->TN.as<uint64_t>(), g->TS.as<uint64_t>(), st);
-    run_hyb_prep(2, n, k, D, a, b, g->sidx.as<int32_t>(),
+    run_tail(g->hist.as<uint32_t>(), DevCount{nullptr, D}, D + 1, k, g->TN.as<uint64_t>(),
+             g->TS.as<uint64_t>(), st);
+    run_hyb_prep(2, n, k, DevCount{nullptr, D}, D + 1, a, b, g->sidx.as<int32_t>(),
                  g->pivot.as<int32_t>(), g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(),
                  g->maxd.as<uint32_t>(), g->TN.as<uint64_t>(), g->TS.as<uint64_t>(),
                  g->hp.as<HybPrep>(), g->npartial.as<unsigned>(), SqPrep{nullptr}, st);
@@ -1034,10 +1087,22 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *o
     g->call_kernels += 2;
     const bool hyb = opts->want_hybrid != 0;
     g->sq = hyb && out->sq_err != nullptr;
-    const int rc = (g->weighted || g->directed) ? estimate_chunked(g, k, opts, st)
-                                                : estimate_bfs(g, k, opts, st);
+    const bool chunked = g->weighted || g->directed;
+    int rc = chunked ? estimate_chunked(g, k, opts, st) : estimate_bfs(g, k, opts, st);
+    if (rc == CC_OK) rc = finish_outputs(g, k, hyb, opts, out, st);  // synchronises
+    if (rc != CC_OK) {
+        cudaStreamSynchronize(st);
+        g->pend = 0;
+        return rc;
+    }
+    if (chunked) return CC_OK;
+    // The bit-packed passes were queued without waiting: account them and
+    // check the first pass now.
+    rc = settle_passes(g);
+    const int c1 = check_pass1(g, hyb, k);
     if (rc != CC_OK) return rc;
-    return finish_outputs(g, k, hyb, opts, out, st);
+    if (c1 == 1) return cc_estimate(g, sample, k, opts, out);  // histogram grown: again
+    return c1;
 }
 
 int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *opts,
@@ -1080,11 +1145,27 @@ int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k, const c
     run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
     g->call_kernels += 2;
     const bool chunked = g->weighted || g->directed;
-    RC(chunked ? chunked_pass1(g, k, st) : bfs_pass1(g, k, st));
+    if (chunked) {
+        RC(chunked_pass1(g, k, st));
+    } else {
+        for (;;) {
+            RC(bfs_pass1(g, k, st));
+            CK(cudaStreamSynchronize(st));
+            RC(settle_passes(g));
+            const int c1 = check_pass1(g, true, k);
+            if (c1 == 1) continue;  // histogram grown: run the first pass again
+            RC(c1);
+            break;
+        }
+    }
     g->sq = true;
     for (int e = 0; e < n_eps; ++e) {
         RC(chunked ? chunked_hybrid(g, k, eps_num[e], eps_den[e], st)
                    : bfs_hybrid(g, k, eps_num[e], eps_den[e], st));
+        if (!chunked) {
+            CK(cudaStreamSynchronize(st));
+            RC(settle_passes(g));
+        }
         FinalizeArgs fa{};
         fa.n = n;
         fa.k = k;

@@ -113,7 +113,10 @@ struct BfsJob {
     uint32_t *hist;      // hist_cap x k (level-major)
     int hist_cap;
     const uint64_t *Lmask;  // n*W
-    uint64_t *lc2;          // n x 2: {LCsum, LCsumSq}
+    uint64_t *lc2;          // n x 2: {LCsum, LCsumSq}; zeroed by the pass (RED_LC)
+    // When set, the pass does nothing if gate[0] = gate[1] = 0 (the hybrid
+    // preparation found no node needing the second pass).
+    const unsigned *gate;
     uint32_t *dist_out;     // RED_LEVELS: n x 32 chunk of levels
     const uint8_t *sqflag;  // RED_SQ: per node, 1 = accumulate hcse, 2 = record fdist
     const int32_t *istar;   // RED_SQ: per sample index, the farthest other sample

@@ -23,15 +23,18 @@ __global__ void k_scatter_sidx(int32_t *sidx, const int32_t *src, int k)
     d_scatter_sidx(sidx, src, k, GSTART, GSTRIDE);
 }
 
-__global__ void k_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc,
+__device__ __forceinline__ int64_t count_of(DevCount c) { return c.p ? (int64_t)*c.p : c.h; }
+
+__global__ void k_S_sampled(const uint32_t *hist, DevCount D, int k, const uint32_t *dcc,
                             uint64_t *S)
 {
-    d_S_sampled(hist, D, k, dcc, S, GSTART >> 5, GSTRIDE >> 5);
+    d_S_sampled(hist, (int)count_of(D), k, dcc, S, GSTART >> 5, GSTRIDE >> 5);
 }
 
-__global__ void k_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS)
+__global__ void k_tail(const uint32_t *hist, DevCount D, int64_t stride, int k, uint64_t *TN,
+                       uint64_t *TS)
 {
-    d_tail_source(hist, D, k, TN, TS, blockIdx.x);
+    d_tail_source(hist, count_of(D), k, TN, TS, blockIdx.x, stride);
 }
 
 __global__ void k_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd)
@@ -39,14 +42,14 @@ __global__ void k_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd)
     d_maxdelta(dcc, k, maxd, GSTART >> 5, GSTRIDE >> 5);
 }
 
-__global__ void k_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
-                           const int32_t *sidx, const int32_t *pivot,
+__global__ void k_hyb_prep(int mode, int64_t n, int k, DevCount D, int64_t stride, uint32_t a,
+                           uint32_t b, const int32_t *sidx, const int32_t *pivot,
                            const uint32_t *delta, const uint32_t *dcc,
                            const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
                            HybPrep *hp, unsigned *npartial, SqPrep sq)
 {
-    d_hyb_prep(mode, n, k, D, a, b, sidx, pivot, delta, dcc, maxd, TN, TS, hp, npartial, sq,
-               GSTART, GSTRIDE);
+    d_hyb_prep(mode, n, k, count_of(D), stride, a, b, sidx, pivot, delta, dcc, maxd, TN, TS,
+               hp, npartial, sq, GSTART, GSTRIDE);
 }
 
 __global__ void k_istar(const uint32_t *dcc, int k, int32_t *istar)
@@ -55,8 +58,10 @@ __global__ void k_istar(const uint32_t *dcc, int k, int32_t *istar)
 }
 
 __global__ void k_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
-                        const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask)
+                        const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask,
+                        const unsigned *gate)
 {
+    if (gate && gate[0] == 0u && gate[1] == 0u) return;
     d_lmask(n, W, k, sidx, pivot, dcc, hp, Lmask, GSTART, GSTRIDE);
 }
 
@@ -84,16 +89,16 @@ void run_scatter_sidx(int32_t *sidx, const int32_t *src, int k, cudaStream_t st)
     k_scatter_sidx<<<(k + 255) / 256, 256, 0, st>>>(sidx, src, k);
 }
 
-void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint64_t *S,
+void run_S_sampled(const uint32_t *hist, DevCount D, int k, const uint32_t *dcc, uint64_t *S,
                    cudaStream_t st)
 {
     k_S_sampled<<<(k + 7) / 8, 256, 0, st>>>(hist, D, k, dcc, S);
 }
 
-void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS,
-              cudaStream_t st)
+void run_tail(const uint32_t *hist, DevCount D, int64_t stride, int k, uint64_t *TN,
+              uint64_t *TS, cudaStream_t st)
 {
-    k_tail<<<k, kTailThreads, 0, st>>>(hist, D, k, TN, TS);
+    k_tail<<<k, kTailThreads, 0, st>>>(hist, D, stride, k, TN, TS);
 }
 
 void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
@@ -101,14 +106,14 @@ void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st)
     k_maxdelta<<<(k + 7) / 8, 256, 0, st>>>(dcc, k, maxd);
 }
 
-void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
-                  const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
+void run_hyb_prep(int mode, int64_t n, int k, DevCount D, int64_t stride, uint32_t a,
+                  uint32_t b, const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
                   const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
                   const uint64_t *TS, HybPrep *hp, unsigned *npartial, const SqPrep &sq,
                   cudaStream_t st)
 {
-    k_hyb_prep<<<grid_for(n, 256), 256, 0, st>>>(mode, n, k, D, a, b, sidx, pivot, delta,
-                                                 dcc, maxd, TN, TS, hp, npartial, sq);
+    k_hyb_prep<<<grid_for(n, 256), 256, 0, st>>>(mode, n, k, D, stride, a, b, sidx, pivot,
+                                                 delta, dcc, maxd, TN, TS, hp, npartial, sq);
 }
 
 // Adaptive hybrid (section 6): keep, per node, the estimate of the eps with
@@ -155,9 +160,10 @@ void run_istar(const uint32_t *dcc, int k, int32_t *istar, cudaStream_t st)
 }
 
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
-               const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st)
+               const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, const unsigned *gate,
+               cudaStream_t st)
 {
-    k_lmask<<<grid_for(n * W, 256), 256, 0, st>>>(n, W, k, sidx, pivot, dcc, hp, Lmask);
+    k_lmask<<<grid_for(n * W, 256), 256, 0, st>>>(n, W, k, sidx, pivot, dcc, hp, Lmask, gate);
 }
 
 void run_finalize(const FinalizeArgs &a, cudaStream_t st)

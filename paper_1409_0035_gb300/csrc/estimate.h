@@ -16,6 +16,13 @@ struct HybPrep {
     uint64_t Hsum, Hnum, thr, LCnum;
 };
 
+// A level count known on the device (p: the traversal's control block, so
+// the host need not wait for it) or on the host (h, when p is null).
+struct DevCount {
+    const int *p;
+    int64_t h;
+};
+
 // Error-estimate input flags written by the hybrid preparation (null: the
 // error estimate is not wanted).
 struct SqPrep {
@@ -43,12 +50,13 @@ struct FinalizeArgs {
 
 void run_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
 void run_scatter_sidx(int32_t *sidx, const int32_t *src, int k, cudaStream_t st);
-void run_S_sampled(const uint32_t *hist, int D, int k, const uint32_t *dcc, uint64_t *S,
+void run_S_sampled(const uint32_t *hist, DevCount D, int k, const uint32_t *dcc, uint64_t *S,
                    cudaStream_t st);
-void run_tail(const uint32_t *hist, int64_t D, int k, uint64_t *TN, uint64_t *TS,
-              cudaStream_t st);
+// TN / TS rows of `stride` >= D + 1 entries.
+void run_tail(const uint32_t *hist, DevCount D, int64_t stride, int k, uint64_t *TN,
+              uint64_t *TS, cudaStream_t st);
 void run_maxdelta(const uint32_t *dcc, int k, uint32_t *maxd, cudaStream_t st);
-void run_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
+void run_hyb_prep(int mode, int64_t n, int k, DevCount D, int64_t stride, uint32_t a, uint32_t b,
                   const int32_t *sidx, const int32_t *pivot, const uint32_t *delta,
                   const uint32_t *dcc, const uint32_t *maxd, const uint64_t *TN,
                   const uint64_t *TS, HybPrep *hp, unsigned *npartial, const SqPrep &sq,
@@ -58,8 +66,11 @@ void run_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *es
                          const double *sq, double *best_est, double *best_sq, int32_t *choice,
                          cudaStream_t st);
 void run_closeness(int64_t n, const double *s_hat, double *clo, cudaStream_t st);
+// gate (may be null): skip when gate[0] = gate[1] = 0 (no node needs the
+// second pass).
 void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivot,
-               const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, cudaStream_t st);
+               const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, const unsigned *gate,
+               cudaStream_t st);
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);
 
 }  // namespace ccg

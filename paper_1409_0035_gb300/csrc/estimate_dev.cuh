@@ -62,11 +62,12 @@ __device__ __forceinline__ void d_S_sampled(const uint32_t *hist, int D, int k,
 
 // Tail tables of the per-source distance histogram: TN[i][t] = number of
 // nodes of V \ C farther than t from c_i, TS[i][t] = the sum of their
-// distances, t = 0..D.  (Role of Algorithm 1's reverse scan of the
+// distances, t = 0..D (row stride `stride` >= D + 1).  (Role of Algorithm 1's reverse scan of the
 // bin/count arrays.)  One CTA per source scans the histogram downwards in
 // tiles with a shared-memory suffix scan.
 __device__ __forceinline__ void d_tail_source(const uint32_t *hist, int64_t D, int k,
-                                              uint64_t *TN, uint64_t *TS, int i)
+                                              uint64_t *TN, uint64_t *TS, int i,
+                                              int64_t stride)
 {
     __shared__ unsigned long long sN[kTailThreads], sS[kTailThreads];
     const int tid = threadIdx.x;
@@ -86,8 +87,8 @@ __device__ __forceinline__ void d_tail_source(const uint32_t *hist, int64_t D, i
             __syncthreads();
         }
         if (t >= 0) {
-            TN[(int64_t)i * (D + 1) + t] = cn + sN[tid] - h;
-            TS[(int64_t)i * (D + 1) + t] = cs + sS[tid] - (unsigned long long)t * h;
+            TN[(int64_t)i * stride + t] = cn + sN[tid] - h;
+            TS[(int64_t)i * stride + t] = cs + sS[tid] - (unsigned long long)t * h;
         }
         cn += sN[kTailThreads - 1];
         cs += sS[kTailThreads - 1];
@@ -135,7 +136,8 @@ __device__ __forceinline__ void d_istar(const uint32_t *dcc, int k, int32_t *ist
 // squared errors over them), 2 when none is (the distance to the farthest
 // sampled node from the pivot) -- with mode 3 only where H(v) is not empty;
 // npartial[1] counts the 2s.
-__device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D, uint32_t a, uint32_t b,
+__device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D,
+                           int64_t tstride, uint32_t a, uint32_t b,
                            const int32_t *sidx, const int32_t *pivot,
                            const uint32_t *delta, const uint32_t *dcc,
                            const uint32_t *maxd, const uint64_t *TN, const uint64_t *TS,
@@ -150,8 +152,8 @@ __device__ __forceinline__ void d_hyb_prep(int mode, int64_t n, int k, int64_t D
             const uint64_t t = (uint64_t)delta[v] * b / a;
             if (mode & 2) {
                 const int64_t tt = t < (uint64_t)D ? (int64_t)t : D;
-                h.Hnum = TN[(int64_t)p * (D + 1) + tt];
-                h.Hsum = TS[(int64_t)p * (D + 1) + tt];
+                h.Hnum = TN[(int64_t)p * tstride + tt];
+                h.Hsum = TS[(int64_t)p * tstride + tt];
             }
             if (mode & 1) {
                 h.thr = t;

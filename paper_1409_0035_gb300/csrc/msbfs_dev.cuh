@@ -540,6 +540,8 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     A.ef = A.eu_dec = A.words = 0;
     A.ninc_dec = A.nfront = 0;
 
+    if (J.gate && J.gate[0] == 0u && J.gate[1] == 0u) return;  // uniform: no barrier yet
+
     // ---- level 0: clear the state, seed the sources -----------------------
     for (int64_t i = gtid; i < n * W; i += gthreads) {
         J.vis[i] = pad_mask(J.k, (int)(i & (W - 1)));
@@ -552,6 +554,8 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         J.fstamp[v] = kInf;
     }
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
+    if (J.red & RED_LC)
+        for (int64_t i = gtid; i < 2 * n; i += gthreads) J.lc2[i] = 0;
     if (J.red & RED_LEVELS)
         for (int64_t i = gtid; i < n * 32; i += gthreads) J.dist_out[i] = kInf;
     if (!sync_after(CC_PH_INIT)) return;

@@ -236,7 +236,7 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     if (h.err < 0) return h.err;
     if (h.err == 1) return CC_ERR_TOO_LARGE;  // more levels than the fixed histogram
     if (h.ninc_final != 0) return CC_ERR_DISCONNECTED;
-    run_S_sampled(hist, h.levels, k, dcc, d_S_sampled, st);
+    run_S_sampled(hist, DevCount{nullptr, h.levels}, k, dcc, d_S_sampled, st);
     k_take_sum<<<grid_of(n), 256, 0, st>>>(sum2, d_sample_sum, n);
     NA_CK(cudaStreamSynchronize(st));
     NA_CK(cudaGetLastError());
