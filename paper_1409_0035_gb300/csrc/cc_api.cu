@@ -70,6 +70,7 @@ struct cc_graph {
     DevBuf hcse, fdist, sqflag, istar, sqe;
     // adaptive hybrid: one eps's estimate and error, the best so far, choice
     DevBuf ad_est, ad_sq, ad_best, ad_bsq, ad_clo, ad_choice;
+    DevBuf pt_clo1, pt_est2, pt_clo2, pt_clo0;  // estimator tables of the finalisation
     bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t D1 = 0;        // levels (largest distance) of the last first pass
     int64_t dist_max = 0;  // largest distance seen by the last estimate
@@ -375,7 +376,8 @@ void free_graph(cc_graph *g)
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
                      &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
-                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice};
+                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
+                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -760,6 +762,31 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
             fa.sample_sum = g->ssum.as<uint64_t>();
         }
     }
+    // Division-free shortcuts (bit-identical): exact scaling by 1/k for a
+    // power-of-two k, and tables of the pivoting estimators over (c, Delta).
+    if ((k & (k - 1)) == 0) fa.inv_k = 1.0 / (double)k;
+    {
+        const bool chunked = g->weighted || g->directed;
+        const int64_t ts = std::min<int64_t>(chunked ? g->D1 + 1 : g->hist_cap, 256);
+        RC(g->pt_clo1.ensure((size_t)k * 8));
+        RC(g->pt_est2.ensure((size_t)k * ts * 8));
+        RC(g->pt_clo2.ensure((size_t)k * ts * 8));
+        const DevCount D = chunked ? DevCount{nullptr, g->D1}
+                                   : DevCount{&g->ctl.as<Ctl>()->levels, 0};
+        // Sums of the bit-packed path are at most k * D < k * hist_cap.
+        const int64_t c0 = chunked ? 0 : std::min<int64_t>((int64_t)k * g->hist_cap, 1 << 20);
+        if (c0) RC(g->pt_clo0.ensure((size_t)c0 * 8));
+        run_pivot_tables(n, k, g->Ssamp.as<uint64_t>(), D, ts, g->pt_clo1.as<double>(),
+                         g->pt_est2.as<double>(), g->pt_clo2.as<double>(), fa.inv_k, c0,
+                         c0 ? g->pt_clo0.as<double>() : nullptr, st);
+        g->call_kernels += 1;
+        fa.clo1 = g->pt_clo1.as<double>();
+        fa.est2t = g->pt_est2.as<double>();
+        fa.clo2t = g->pt_clo2.as<double>();
+        fa.tstride = ts;
+        fa.clo0t = c0 ? g->pt_clo0.as<double>() : nullptr;
+        fa.c0len = c0;
+    }
     if (g->sq && hyb) {
         if (dev_out) {
             fa.sq_err = out->sq_err;
@@ -836,7 +863,8 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
                           &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
-                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice};
+                     &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
+                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;

@@ -149,6 +149,44 @@ void run_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *es
                                                         choice);
 }
 
+// clo1[p] = (n-1)/S(c_p); est2t / clo2t[p * tstride + d] = S(c_p) + (n-1) d
+// and its closeness, for d <= D (the pivoting estimators take only these
+// values); clo0t[s] = the sampling estimate's closeness for sum s (0 < s <
+// c0len, s <= k D), computed exactly as the finalisation would.
+__global__ void k_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCount D,
+                               int64_t tstride, double *clo1, double *est2t, double *clo2t,
+                               double inv_k, int64_t c0len, double *clo0t)
+{
+    const int64_t Dv = count_of(D);
+    const uint64_t nm1 = (uint64_t)(n - 1);
+    const int64_t smax = min(c0len, (int64_t)k * Dv + 1);
+    for (int64_t s = GSTART + 1; s < smax; s += GSTRIDE) {
+        const double x0 = u128_to_double((u128)nm1 * (uint64_t)s);
+        const double e0 = inv_k != 0.0 ? x0 * inv_k : x0 / (double)k;
+        clo0t[s] = (double)nm1 / e0;
+    }
+    const int64_t dn = min(tstride, Dv + 1);  // distances 0 .. dn-1 per pivot
+    for (int64_t q = GSTART; q < (int64_t)k * dn; q += GSTRIDE) {
+        const int64_t p = q / dn, d = q % dn;
+        const int64_t i = p * tstride + d;
+        const uint64_t Sp = S_samp[p];
+        const double e2 = u128_to_double((u128)Sp + (u128)nm1 * (uint64_t)d);
+        est2t[i] = e2;
+        clo2t[i] = (double)nm1 / e2;
+        if (d == 0) clo1[p] = (double)nm1 / (double)Sp;
+    }
+}
+
+void run_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCount D, int64_t tstride,
+                      double *clo1, double *est2t, double *clo2t, double inv_k,
+                      int64_t c0len, double *clo0t, cudaStream_t st)
+{
+    // The ranges depend on the level count, read on the device: a fixed
+    // grid strides over them.
+    k_pivot_tables<<<152 * 2, 256, 0, st>>>(n, k, S_samp, D, tstride, clo1, est2t, clo2t,
+                                            inv_k, c0len, clo0t);
+}
+
 void run_closeness(int64_t n, const double *s_hat, double *clo, cudaStream_t st)
 {
     k_closeness<<<grid_for(n, 256), 256, 0, st>>>(n, s_hat, clo);

@@ -46,6 +46,16 @@ struct FinalizeArgs {
     const uint64_t *hcse;  // n x 2: 128-bit sum of squared errors over HC(v)
     const uint32_t *fdist, *dcc;
     const int32_t *istar;
+    // Optional shortcuts, bit-identical to the divisions they replace:
+    // inv_k = 1/k when k is a power of two (then x/k = x * inv_k exactly);
+    // clo1[p] = (n-1)/S(c_p); est2t / clo2t[p * tstride + d] = the pivoting
+    // upper bound S(c_p) + (n-1) d and its closeness, for d < tstride.
+    double inv_k;
+    const double *clo1, *est2t, *clo2t;
+    int64_t tstride;
+    // clo0t[s] = the sampling estimate's closeness for sum s < c0len.
+    const double *clo0t;
+    int64_t c0len;
 };
 
 void run_fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t st);
@@ -72,5 +82,9 @@ void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivo
                const uint32_t *dcc, const HybPrep *hp, uint64_t *Lmask, const unsigned *gate,
                cudaStream_t st);
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);
+// Tables of the pivoting estimators for FinalizeArgs (d <= D only).
+void run_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCount D, int64_t tstride,
+                      double *clo1, double *est2t, double *clo2t, double inv_k,
+                      int64_t c0len, double *clo0t, cudaStream_t st);
 
 }  // namespace ccg

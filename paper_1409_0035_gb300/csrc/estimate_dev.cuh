@@ -211,18 +211,35 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
         const uint64_t nm1 = (uint64_t)(A.n - 1);
         const int j = A.sidx[v];
         const uint64_t sum = A.sum2[2 * v];
-        double est[CC_NUM_EST];
+        double est[CC_NUM_EST], clo[CC_NUM_EST];
         uint64_t h6[6] = {0, 0, 0, 0, 0, 0};
         if (j >= 0) {
             const double ex = (double)A.S_samp[j];
             est[0] = est[1] = est[2] = est[3] = ex;
+            clo[0] = clo[1] = clo[2] = clo[3] = (double)nm1 / ex;
         } else {
             const int p = A.pivot[v];
             const uint64_t Sp = A.S_samp[p];
-            est[0] = u128_to_double((u128)nm1 * sum) / (double)A.k;
+            const double x0 = u128_to_double((u128)nm1 * sum);
+            est[0] = A.inv_k != 0.0 ? x0 * A.inv_k : x0 / (double)A.k;
+            // closeness of the sampling estimate, also reused by the hybrid
+            auto clo_sampling = [&]() {
+                return (A.clo0t && sum < (uint64_t)A.c0len) ? A.clo0t[sum]
+                                                            : (double)nm1 / est[0];
+            };
+            clo[0] = A.clo[0] ? clo_sampling() : 0.0;
             est[1] = (double)Sp;
-            est[2] = u128_to_double((u128)Sp + (u128)nm1 * A.delta[v]);
+            clo[1] = A.clo1 ? A.clo1[p] : (A.clo[1] ? (double)nm1 / est[1] : 0.0);
+            const uint32_t d = A.delta[v];
+            if (A.est2t && d < A.tstride) {
+                est[2] = A.est2t[(int64_t)p * A.tstride + d];
+                clo[2] = A.clo2t[(int64_t)p * A.tstride + d];
+            } else {
+                est[2] = u128_to_double((u128)Sp + (u128)nm1 * d);
+                clo[2] = A.clo[2] ? (double)nm1 / est[2] : 0.0;
+            }
             est[3] = 0.0;
+            clo[3] = 0.0;
             if (A.hybrid) {
                 const HybPrep h = A.hp[v];
                 const uint64_t LCnum = h.LCnum & ~kPartialBit;
@@ -233,7 +250,16 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
                 const uint64_t HCnum = (uint64_t)A.k - LCnum;
                 const uint64_t Lnum = nm1 - h.Hnum - HCnum;
                 const u128 N = (u128)(h.Hsum + HCsum) * LCnum + (u128)LCsum * Lnum;
-                est[3] = u128_to_double(N) / (double)LCnum;
+                if (LCnum == (uint64_t)A.k && h.Hnum == 0) {
+                    // N = sum * (n-1): the sampling estimate, bit for bit.
+                    est[3] = est[0];
+                    clo[3] = A.clo[3] ? (A.clo[0] ? clo[0] : clo_sampling()) : 0.0;
+                } else {
+                    const double xN = u128_to_double(N);
+                    est[3] = (LCnum == (uint64_t)A.k && A.inv_k != 0.0) ? xN * A.inv_k
+                                                                         : xN / (double)LCnum;
+                    clo[3] = A.clo[3] ? (double)nm1 / est[3] : 0.0;
+                }
                 h6[0] = h.Hsum; h6[1] = h.Hnum; h6[2] = HCsum;
                 h6[3] = LCsum; h6[4] = LCnum; h6[5] = LCsq;
                 if (A.sq_err) {
@@ -262,7 +288,7 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
         for (int e = 0; e < CC_NUM_EST; ++e) {
             if (e == CC_EST_HYBRID && !A.hybrid) continue;
             if (A.s_hat[e]) A.s_hat[e][v] = est[e];
-            if (A.clo[e]) A.clo[e][v] = (double)nm1 / est[e];
+            if (A.clo[e]) A.clo[e][v] = clo[e];
         }
         if (A.hyb_int && A.hybrid)
             for (int q = 0; q < 6; ++q) A.hyb_int[6 * v + q] = h6[q];
