@@ -339,6 +339,21 @@ int finish_graph(cc_graph *g, HostCSR &h)
     return CC_OK;
 }
 
+// G^T of a directed graph built on the device into g->rv.
+int adopt_device_reverse(cc_graph *g, DeviceCSR &d)
+{
+    g->rv.rp.p = d.rp;
+    g->rv.rp.cap = (size_t)(d.n + 1) * 8;
+    g->rv.col.p = d.col;
+    g->rv.col.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
+    if (d.w) {
+        g->rv.w.p = d.w;
+        g->rv.w.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
+    }
+    d.rp = d.col = d.w = nullptr;
+    return build_classes(d.rp_host, d.n, g->rv.cls);
+}
+
 // Take ownership of a CSR built on the device.
 int adopt_device_csr(cc_graph *g, DeviceCSR &d)
 {
@@ -957,11 +972,29 @@ int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_
         if (d.w) cudaFree(d.w);
         old_id.swap(d.old_id);
     } else {
-        // Directed: strongly connected components on the host (Tarjan).
-        HostCSR h;
-        rc = build_host_csr(n, m, src, dst, w, true, keep_component != 0, h);
-        if (rc == CC_OK) rc = finish_graph(g, h);
-        old_id.swap(h.old_id);
+        // Directed: sort, merge, G and G^T and the largest strongly connected
+        // component (forward-backward search) on the device; a graph whose
+        // largest component holds no more than half of the nodes is decided
+        // by the host's full decomposition (Tarjan).
+        DeviceCSR F, R;
+        bool decided = false;
+        rc = build_csr_device_directed(n, m, src, dst, w, keep_component != 0, F, R, &decided);
+        if (rc == CC_OK && decided) {
+            rc = adopt_device_csr(g, F);
+            if (rc == CC_OK) rc = adopt_device_reverse(g, R);
+            old_id.swap(F.old_id);
+        }
+        for (DeviceCSR *d : {&F, &R}) {
+            if (d->rp) cudaFree(d->rp);
+            if (d->col) cudaFree(d->col);
+            if (d->w) cudaFree(d->w);
+        }
+        if (rc == CC_OK && !decided) {
+            HostCSR h;
+            rc = build_host_csr(n, m, src, dst, w, true, keep_component != 0, h);
+            if (rc == CC_OK) rc = finish_graph(g, h);
+            old_id.swap(h.old_id);
+        }
     }
     if (rc != CC_OK) {
         free_graph(g);

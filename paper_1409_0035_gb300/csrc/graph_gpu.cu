@@ -159,9 +159,11 @@ __global__ void k_digit_scatter(const uint64_t *keys, const uint32_t *vals, int6
 
 // ---------------------------------------------------------------- arcs
 
+// Arc keys (tail << b | head) with their lengths: both ways for undirected
+// input, one way (second slot unused) for directed input.
 __global__ void k_make_arcs(const uint32_t *src, const uint32_t *dst, const uint32_t *w,
                             int64_t m, int64_t n, int b, uint64_t *keys, uint32_t *vals,
-                            uint64_t *flags, int *err)
+                            uint64_t *flags, int *err, int both)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -175,7 +177,7 @@ __global__ void k_make_arcs(const uint32_t *src, const uint32_t *dst, const uint
         vals[2 * e] = ww;
         vals[2 * e + 1] = ww;
         flags[2 * e] = keep;
-        flags[2 * e + 1] = keep;
+        flags[2 * e + 1] = both ? keep : 0;
     }
 }
 
@@ -252,11 +254,13 @@ __global__ void k_iota32(int32_t *p, int64_t n)
 }
 
 // Union of the endpoints of every arc u -> v with u < v.
+// A warp per node, a lane per arc (hub rows no longer run on one thread).
 __global__ void k_hook(const int64_t *rp, const int32_t *col, int64_t n, int32_t *parent)
 {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        for (int64_t e = rp[u] + lane; e < rp[u + 1]; e += 32) {
             const int32_t v = col[e];
             if (v <= u) continue;
             int32_t a = find_root(parent, (int32_t)u), b = find_root(parent, v);
@@ -326,15 +330,129 @@ __global__ void k_rewrite_rows(const int64_t *rp, const int32_t *col, const uint
                                const uint64_t *nrp, int64_t nk, int32_t *ncol, uint32_t *nw,
                                int *err)
 {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nk;
-         x += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < nk;
+         x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t v = old_id[x];
-        int64_t o = (int64_t)nrp[x];
-        for (int64_t e = rp[v]; e < rp[v + 1]; ++e, ++o) {
+        const int64_t b = rp[v], o = (int64_t)nrp[x];
+        for (int64_t e = b + lane; e < rp[v + 1]; e += 32) {
             const int32_t y = newid[col[e]];
             if (y < 0) atomicExch(err, CC_ERR_GRAPH);
-            ncol[o] = y < 0 ? 0 : y;
-            if (w) nw[o] = w[e];
+            ncol[o + (e - b)] = y < 0 ? 0 : y;
+            if (w) nw[o + (e - b)] = w[e];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- directed
+
+// Reverse arc keys (head << b | tail) with the lengths.
+__global__ void k_swap_keys(const uint64_t *keys, const uint32_t *vals, int64_t a, int b,
+                            uint64_t *okeys, uint32_t *ovals)
+{
+    const uint64_t mask = (1ull << b) - 1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t u = keys[e] >> b, v = keys[e] & mask;
+        okeys[e] = (v << b) | u;
+        ovals[e] = vals[e];
+    }
+}
+
+// Pivot of the forward-backward search: the largest out-degree x in-degree
+// (a node on many paths), ties to the smallest id.  Two passes: the score,
+// then the smallest node holding it.
+__global__ void k_pivot_score(const int64_t *rp, const int64_t *rrp, int64_t n,
+                              unsigned long long *best)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(best, (unsigned long long)(rp[v + 1] - rp[v]) *
+                            (unsigned long long)(rrp[v + 1] - rrp[v]));
+}
+
+__global__ void k_pivot_pick(const int64_t *rp, const int64_t *rrp, int64_t n,
+                             const unsigned long long *best, unsigned *pick)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if ((unsigned long long)(rp[v + 1] - rp[v]) * (unsigned long long)(rrp[v + 1] - rrp[v]) ==
+            *best)
+            atomicMin(pick, (unsigned)v);
+}
+
+// One level of a breadth-first search: a warp per frontier node, a lane per
+// arc; the first to reach a node queues it.
+__global__ void k_bfs_step(const int64_t *rp, const int32_t *col, const int32_t *qin,
+                           int64_t nin, int32_t *qout, unsigned long long *nout, unsigned *vis)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < nin;
+         t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t u = qin[t];
+        for (int64_t e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int32_t v = col[e];
+            if (vis[v] == 0u && atomicExch(&vis[v], 1u) == 0u)
+                qout[atomicAdd(nout, 1ull)] = v;
+        }
+    }
+}
+
+__global__ void k_both_flags(const unsigned *fv, const unsigned *bv, int64_t n, uint64_t *flags)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        flags[v] = (fv[v] && bv[v]) ? 1 : 0;
+}
+
+// Kept nodes: new ids, and per kept row the arcs whose head is kept too (a
+// warp per row).
+__global__ void k_kept_arcs(const int64_t *rp, const int32_t *col, const uint64_t *flags,
+                            const uint64_t *pos, int64_t n, uint64_t *deg, int32_t *newid,
+                            int32_t *old_id)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        if (!flags[v]) {
+            if (lane == 0) newid[v] = -1;
+            continue;
+        }
+        unsigned c = 0;
+        for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) c += flags[col[e]] ? 1u : 0u;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        if (lane == 0) {
+            deg[pos[v]] = c;
+            newid[v] = (int32_t)pos[v];
+            old_id[pos[v]] = (int32_t)v;
+        }
+    }
+}
+
+// Kept rows with their kept arcs, in order (ballot compaction per 32 arcs).
+__global__ void k_rewrite_kept(const int64_t *rp, const int32_t *col, const uint32_t *w,
+                               const uint64_t *flags, const int32_t *old_id,
+                               const int32_t *newid, const uint64_t *nrp, int64_t nk,
+                               int32_t *ncol, uint32_t *nw)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < nk;
+         x += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int32_t v = old_id[x];
+        int64_t o = (int64_t)nrp[x];
+        for (int64_t e0 = rp[v]; e0 < rp[v + 1]; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const bool in = e < rp[v + 1];
+            const int32_t u = in ? col[e] : 0;
+            const bool keep = in && flags[u];
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) {
+                const int64_t q = o + __popc(bal & ((1u << lane) - 1u));
+                ncol[q] = newid[u];
+                if (w) nw[q] = w[e];
+            }
+            o += __popc(bal);
         }
     }
 }
@@ -474,7 +592,7 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
         k_make_arcs<<<gsz(m), 256, 0, st>>>(dsrc.as<uint32_t>(), ddst.as<uint32_t>(),
                                             h_w ? dw.as<uint32_t>() : nullptr, m, n, b,
                                             k0.as<uint64_t>(), v0.as<uint32_t>(),
-                                            fl.as<uint64_t>(), err.as<int>());
+                                            fl.as<uint64_t>(), err.as<int>(), 1);
     int herr = 0;
     G_CK(cudaMemcpy(&herr, err.p, 4, cudaMemcpyDeviceToHost));
     if (herr) return herr;
@@ -522,7 +640,7 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
         G_CK(cudaMemset(size.p, 0, n * 4));
         G_CK(cudaMemset(best.p, 0, 8));
         k_iota32<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n);
-        k_hook<<<gsz(n), 256, 0, st>>>(frp, fcol, n, parent.as<int32_t>());
+        k_hook<<<gsz(n * 32), 256, 0, st>>>(frp, fcol, n, parent.as<int32_t>());
         G_RC(label.alloc(n * 4));
         k_label_count<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, label.as<int32_t>(),
                                               size.as<uint32_t>());
@@ -551,7 +669,7 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
         if (h_w) G_RC(nw.alloc(std::max<uint64_t>(arcs, 1) * 4));
         k_u64_to_i64<<<gsz(nk + 1), 256, 0, st>>>(degs.as<uint64_t>(), nk + 1,
                                                   nrp.as<int64_t>());
-        k_rewrite_rows<<<gsz(nk), 256, 0, st>>>(frp, fcol, fw, oldid.as<int32_t>(),
+        k_rewrite_rows<<<gsz(nk * 32), 256, 0, st>>>(frp, fcol, fw, oldid.as<int32_t>(),
                                                 newid.as<int32_t>(), degs.as<uint64_t>(), nk,
                                                 ncol.as<int32_t>(),
                                                 h_w ? nw.as<uint32_t>() : nullptr, err.as<int>());
@@ -579,6 +697,210 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t
     out.rp_host.resize(nk + 1);
     G_CK(cudaMemcpy(out.rp_host.data(), out.rp, (nk + 1) * 8, cudaMemcpyDeviceToHost));
     G_CK(cudaDeviceSynchronize());
+    return CC_OK;
+}
+
+// Sorted, merged arcs (keys tail << b | head, lengths) -> CSR over n nodes.
+static int csr_from_sorted(const uint64_t *keys, const uint32_t *vals, int64_t a, int64_t n, int b,
+                           bool weighted, Buf &rp, Buf &col, Buf &w, cudaStream_t st)
+{
+    G_RC(rp.alloc((n + 1) * 8));
+    G_RC(col.alloc(std::max<int64_t>(a, 1) * 4));
+    k_row_ptr<<<gsz(a + 1), 256, 0, st>>>(keys, a, n, b, rp.as<int64_t>());
+    if (a > 0) k_heads<<<gsz(a), 256, 0, st>>>(keys, a, b, col.as<int32_t>());
+    if (weighted) {
+        G_RC(w.alloc(std::max<int64_t>(a, 1) * 4));
+        if (a > 0) G_CK(cudaMemcpyAsync(w.p, vals, a * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return CC_OK;
+}
+
+// Rows of the kept nodes with their kept arcs, renumbered.
+static int filter_csr(const int64_t *rp, const int32_t *col, const uint32_t *w, int64_t n,
+                      const uint64_t *flags, const uint64_t *pos, int64_t nk, Buf &newid,
+                      Buf &oldid, DeviceCSR &out, cudaStream_t st)
+{
+    Buf degs, nrp, ncol, nw;
+    G_RC(degs.alloc((nk + 1) * 8));
+    k_kept_arcs<<<gsz(n * 32), 256, 0, st>>>(rp, col, flags, pos, n, degs.as<uint64_t>(),
+                                             newid.as<int32_t>(), oldid.as<int32_t>());
+    uint64_t arcs = 0;
+    G_RC(scan_u64(degs.as<uint64_t>(), degs.as<uint64_t>(), nk, &arcs, st));
+    G_CK(cudaMemcpy(degs.as<uint64_t>() + nk, &arcs, 8, cudaMemcpyHostToDevice));
+    G_RC(nrp.alloc((nk + 1) * 8));
+    G_RC(ncol.alloc(std::max<uint64_t>(arcs, 1) * 4));
+    if (w) G_RC(nw.alloc(std::max<uint64_t>(arcs, 1) * 4));
+    k_u64_to_i64<<<gsz(nk + 1), 256, 0, st>>>(degs.as<uint64_t>(), nk + 1, nrp.as<int64_t>());
+    k_rewrite_kept<<<gsz(nk * 32), 256, 0, st>>>(rp, col, w, flags, oldid.as<int32_t>(),
+                                                 newid.as<int32_t>(), degs.as<uint64_t>(), nk,
+                                                 ncol.as<int32_t>(), w ? nw.as<uint32_t>() : nullptr);
+    out.n = nk;
+    out.arcs = (int64_t)arcs;
+    std::swap(out.rp, nrp.p);
+    std::swap(out.col, ncol.p);
+    if (w) std::swap(out.w, nw.p);
+    out.rp_host.resize(nk + 1);
+    G_CK(cudaMemcpy(out.rp_host.data(), out.rp, (nk + 1) * 8, cudaMemcpyDeviceToHost));
+    return CC_OK;
+}
+
+// Breadth-first reachability from `root` over (rp, col) into vis (0/1).
+static int reach(const int64_t *rp, const int32_t *col, int64_t n, int32_t root, unsigned *vis,
+                 Buf &q0, Buf &q1, Buf &cnt, cudaStream_t st)
+{
+    G_CK(cudaMemsetAsync(vis, 0, n * 4, st));
+    const unsigned one = 1u;
+    G_CK(cudaMemcpyAsync(vis + root, &one, 4, cudaMemcpyHostToDevice, st));
+    G_CK(cudaMemcpyAsync(q0.p, &root, 4, cudaMemcpyHostToDevice, st));
+    int32_t *qin = q0.as<int32_t>(), *qout = q1.as<int32_t>();
+    int64_t nin = 1;
+    while (nin > 0) {
+        G_CK(cudaMemsetAsync(cnt.p, 0, 8, st));
+        k_bfs_step<<<gsz(nin * 32), 256, 0, st>>>(rp, col, qin, nin, qout,
+                                                  cnt.as<unsigned long long>(), vis);
+        unsigned long long h = 0;
+        G_CK(cudaMemcpyAsync(&h, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+        G_CK(cudaStreamSynchronize(st));
+        nin = (int64_t)h;
+        std::swap(qin, qout);
+    }
+    return CC_OK;
+}
+
+int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t *h_dst,
+                              const uint32_t *h_w, bool keep_component, DeviceCSR &F,
+                              DeviceCSR &R, bool *decided)
+{
+    *decided = false;
+    if (n < 2 || m < 0 || (m > 0 && (!h_src || !h_dst))) return CC_ERR_ARG;
+    if (n > 0x7FFFFFFFLL || m > 0x7FFFFFFFLL) return CC_ERR_TOO_LARGE;
+    cudaStream_t st = 0;
+    int b = 1;
+    while ((1ll << b) < n) ++b;
+    const int64_t A0 = 2 * m;  // k_make_arcs writes two slots per input edge
+    Buf dsrc, ddst, dw, k0, v0, k1, v1, fl, pos, err;
+    G_RC(dsrc.alloc(m * 4));
+    G_RC(ddst.alloc(m * 4));
+    if (h_w) G_RC(dw.alloc(m * 4));
+    G_RC(k0.alloc(std::max<int64_t>(A0, 1) * 8));
+    G_RC(v0.alloc(std::max<int64_t>(A0, 1) * 4));
+    G_RC(k1.alloc(std::max<int64_t>(A0, 1) * 8));
+    G_RC(v1.alloc(std::max<int64_t>(A0, 1) * 4));
+    const int64_t FL = std::max<int64_t>(A0, n) + 1;
+    G_RC(fl.alloc(FL * 8));
+    G_RC(pos.alloc(FL * 8));
+    G_RC(err.alloc(4));
+    if (m > 0) {
+        G_CK(cudaMemcpy(dsrc.p, h_src, m * 4, cudaMemcpyHostToDevice));
+        G_CK(cudaMemcpy(ddst.p, h_dst, m * 4, cudaMemcpyHostToDevice));
+        if (h_w) G_CK(cudaMemcpy(dw.p, h_w, m * 4, cudaMemcpyHostToDevice));
+    }
+    G_CK(cudaMemset(err.p, 0, 4));
+    // 1. arcs one way, self-loops dropped; sorted by (tail, head); parallel
+    //    arcs merged (smallest length)
+    if (m > 0)
+        k_make_arcs<<<gsz(m), 256, 0, st>>>(dsrc.as<uint32_t>(), ddst.as<uint32_t>(),
+                                            h_w ? dw.as<uint32_t>() : nullptr, m, n, b,
+                                            k0.as<uint64_t>(), v0.as<uint32_t>(),
+                                            fl.as<uint64_t>(), err.as<int>(), 0);
+    int herr = 0;
+    G_CK(cudaMemcpy(&herr, err.p, 4, cudaMemcpyDeviceToHost));
+    if (herr) return herr;
+    uint64_t A1 = 0;
+    G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), A0, &A1, st));
+    if (A0 > 0)
+        k_compact<<<gsz(A0), 256, 0, st>>>(k0.as<uint64_t>(), v0.as<uint32_t>(),
+                                           fl.as<uint64_t>(), pos.as<uint64_t>(), A0,
+                                           k1.as<uint64_t>(), v1.as<uint32_t>());
+    bool in_tmp = false;
+    if (A1 > 0)
+        G_RC(radix_sort(k1.as<uint64_t>(), v1.as<uint32_t>(), (int64_t)A1, 2 * b,
+                        k0.as<uint64_t>(), v0.as<uint32_t>(), st, &in_tmp));
+    uint64_t *ks = in_tmp ? k0.as<uint64_t>() : k1.as<uint64_t>();
+    uint32_t *vs = in_tmp ? v0.as<uint32_t>() : v1.as<uint32_t>();
+    uint64_t *ko = in_tmp ? k1.as<uint64_t>() : k0.as<uint64_t>();
+    uint32_t *vo = in_tmp ? v1.as<uint32_t>() : v0.as<uint32_t>();
+    uint64_t A2 = 0;
+    if (A1 > 0) {
+        k_first_of_run<<<gsz(A1), 256, 0, st>>>(ks, (int64_t)A1, fl.as<uint64_t>());
+        k_run_min<<<gsz(A1), 256, 0, st>>>(ks, vs, fl.as<uint64_t>(), (int64_t)A1);
+        G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), (int64_t)A1, &A2, st));
+        k_compact<<<gsz(A1), 256, 0, st>>>(ks, vs, fl.as<uint64_t>(), pos.as<uint64_t>(),
+                                           (int64_t)A1, ko, vo);
+    }
+    // 2. forward CSR (G) and reverse CSR (G^T, from the swapped keys)
+    Buf frp, fcol, fw, rrp, rcol, rw;
+    G_RC(csr_from_sorted(ko, vo, (int64_t)A2, n, b, h_w != nullptr, frp, fcol, fw, st));
+    if (A2 > 0) {
+        k_swap_keys<<<gsz(A2), 256, 0, st>>>(ko, vo, (int64_t)A2, b, ks, vs);
+        G_RC(radix_sort(ks, vs, (int64_t)A2, 2 * b, ko, vo, st, &in_tmp));
+    }
+    const uint64_t *rks = (A2 > 0 && in_tmp) ? ko : ks;
+    const uint32_t *rvs = (A2 > 0 && in_tmp) ? vo : vs;
+    G_RC(csr_from_sorted(rks, rvs, (int64_t)A2, n, b, h_w != nullptr, rrp, rcol, rw, st));
+    // 3. largest strongly connected component: the forward-backward search
+    //    from a pivot gives the pivot's component; holding more than half of
+    //    the nodes, it is the largest.  Otherwise the caller decides on the
+    //    host.
+    if (!keep_component) {
+        std::vector<int32_t> ids(n);
+        for (int64_t v = 0; v < n; ++v) ids[v] = (int32_t)v;
+        for (DeviceCSR *o : {&F, &R}) {
+            o->n = n;
+            o->arcs = (int64_t)A2;
+            o->old_id = ids;
+            o->rp_host.resize(n + 1);
+        }
+        std::swap(F.rp, frp.p); std::swap(F.col, fcol.p); if (h_w) std::swap(F.w, fw.p);
+        std::swap(R.rp, rrp.p); std::swap(R.col, rcol.p); if (h_w) std::swap(R.w, rw.p);
+        G_CK(cudaMemcpy(F.rp_host.data(), F.rp, (n + 1) * 8, cudaMemcpyDeviceToHost));
+        G_CK(cudaMemcpy(R.rp_host.data(), R.rp, (n + 1) * 8, cudaMemcpyDeviceToHost));
+        *decided = true;
+        return CC_OK;
+    }
+    Buf best, pick, fvis, bvis, q0, q1, cnt;
+    G_RC(best.alloc(8));
+    G_RC(pick.alloc(4));
+    G_CK(cudaMemset(best.p, 0, 8));
+    G_CK(cudaMemset(pick.p, 0xFF, 4));
+    k_pivot_score<<<gsz(n), 256, 0, st>>>(frp.as<int64_t>(), rrp.as<int64_t>(), n,
+                                          best.as<unsigned long long>());
+    k_pivot_pick<<<gsz(n), 256, 0, st>>>(frp.as<int64_t>(), rrp.as<int64_t>(), n,
+                                         best.as<unsigned long long>(), pick.as<unsigned>());
+    unsigned piv = 0;
+    G_CK(cudaMemcpy(&piv, pick.p, 4, cudaMemcpyDeviceToHost));
+    G_RC(fvis.alloc(n * 4));
+    G_RC(bvis.alloc(n * 4));
+    G_RC(q0.alloc(n * 4));
+    G_RC(q1.alloc(n * 4));
+    G_RC(cnt.alloc(8));
+    G_RC(reach(frp.as<int64_t>(), fcol.as<int32_t>(), n, (int32_t)piv, fvis.as<unsigned>(), q0,
+               q1, cnt, st));
+    G_RC(reach(rrp.as<int64_t>(), rcol.as<int32_t>(), n, (int32_t)piv, bvis.as<unsigned>(), q0,
+               q1, cnt, st));
+    k_both_flags<<<gsz(n), 256, 0, st>>>(fvis.as<unsigned>(), bvis.as<unsigned>(), n,
+                                         fl.as<uint64_t>());
+    uint64_t kept = 0;
+    G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), n, &kept, st));
+    const int64_t nk = (int64_t)kept;
+    if (nk <= n - nk) return CC_OK;  // no majority component: not decided here
+    if (nk < 2) return CC_ERR_GRAPH;
+    // 4. renumber the kept nodes (increasing original id) and keep the arcs
+    //    between them, in G and in G^T
+    Buf newid, oldid, newid2, oldid2;
+    G_RC(newid.alloc(n * 4));
+    G_RC(oldid.alloc(nk * 4));
+    G_RC(newid2.alloc(n * 4));
+    G_RC(oldid2.alloc(nk * 4));
+    G_RC(filter_csr(frp.as<int64_t>(), fcol.as<int32_t>(), h_w ? fw.as<uint32_t>() : nullptr, n,
+                    fl.as<uint64_t>(), pos.as<uint64_t>(), nk, newid, oldid, F, st));
+    G_RC(filter_csr(rrp.as<int64_t>(), rcol.as<int32_t>(), h_w ? rw.as<uint32_t>() : nullptr, n,
+                    fl.as<uint64_t>(), pos.as<uint64_t>(), nk, newid2, oldid2, R, st));
+    F.old_id.resize(nk);
+    G_CK(cudaMemcpy(F.old_id.data(), oldid.p, nk * 4, cudaMemcpyDeviceToHost));
+    R.old_id = F.old_id;
+    G_CK(cudaDeviceSynchronize());
+    *decided = true;
     return CC_OK;
 }
 

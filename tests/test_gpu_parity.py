@@ -114,6 +114,46 @@ def test_graph_build_weighted_directed(cc):
             cc.cc_graph_free(g)
 
 
+def _check_directed_build(cc, n, s, d, w=None, keep=True):
+    g, old, og = both(cc, n, s, d, w, directed=True, keep=keep)
+    try:
+        for rev, (orp, ocol, ow) in ((False, (og.row_ptr, og.col, og.w)),
+                                     (True, (og.rrow_ptr, og.rcol, og.rw))):
+            rp, col, ww = cc.cc_graph_copy_csr(g, reverse=rev)
+            assert (rp == orp).all() and (col == ocol).all()
+            if w is not None:
+                assert (ww == ow).all()
+        assert (old == og.old_id).all()
+    finally:
+        cc.cc_graph_free(g)
+
+
+@pytest.mark.parametrize("scale,ef,weighted", [(14, 16, False), (15, 8, True)])
+def test_directed_build_device_scc(cc, scale, ef, weighted):
+    """Directed R-MAT: merged arcs, G and G^T and the largest strongly
+    connected component (a majority component: found on the device)."""
+    n, s, d = synth.rmat_edges(scale, ef, seed=scale + 3)
+    w = synth.random_weights(s.size, 1, 50, seed=4) if weighted else None
+    _check_directed_build(cc, n, s, d, w)
+
+
+def test_directed_build_without_majority_component(cc):
+    """Two directed 40-cycles joined by a 30-node path: the largest
+    components tie (the one holding node 0 wins) and none holds half the
+    nodes, so the full decomposition decides."""
+    c1 = synth.cycle_edges(40)
+    a = np.concatenate([c1[1], c1[1] + 70, np.arange(40, 69, dtype=np.uint32), [39]])
+    b = np.concatenate([c1[2], c1[2] + 70, np.arange(41, 70, dtype=np.uint32), [40]])
+    a = np.append(a, np.uint32(69))
+    b = np.append(b, np.uint32(70))
+    _check_directed_build(cc, 110, a.astype(np.uint32), b.astype(np.uint32))
+
+
+def test_directed_build_all_nodes(cc):
+    n, s, d = synth.rmat_edges(11, 4, seed=21)
+    _check_directed_build(cc, n, s, d, keep=False)
+
+
 @pytest.mark.parametrize("n,k,seed", [(10, 3, 0), (1000, 64, 2), (5000, 1, 7),
                                       (3000, 2048, 5), (70000, 256, 11), (300, 300, 1)])
 def test_sample_choose_matches_oracle(cc, n, k, seed):
