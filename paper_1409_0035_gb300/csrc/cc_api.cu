@@ -73,6 +73,7 @@ struct cc_graph {
     DevBuf pt_clo1, pt_est2, pt_clo2, pt_clo0;  // estimator tables of the finalisation
     bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t D1 = 0;        // levels (largest distance) of the last first pass
+    int cw = 32;           // sources per chunk of the last chunked first pass
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
@@ -542,18 +543,39 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 // One 32-source chunk of shortest paths (forward, and reversed for round
 // trips) into g->distF / g->distR.  Unit lengths use the bit-packed
 // traversal writing levels; arc lengths the label-correcting kernel.
-int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, cudaStream_t st)
+// Sources per chunk: 32 for shortest paths (one 128-byte row per node);
+// for unit lengths up to 128 (two bit-packed words per node) so that fewer,
+// wider traversals fill the rows, while the distance rows (one or two
+// n x cw tables) take at most a third of the free device memory.
+int chunk_width(cc_graph *g, int64_t k)
+{
+    if (g->weighted) return kChunkSrc;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return kChunkSrc;
+    }
+    const double tables = g->directed ? 2.0 : 1.0;
+    int cw = 128;
+    while (cw > kChunkSrc && (double)g->n * cw * 4.0 * tables > (double)free_b / 3.0) cw /= 2;
+    while (cw > kChunkSrc && cw / 2 >= k) cw /= 2;
+    return cw;
+}
+
+int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_t st)
 {
     const int64_t n = g->n;
     if (!g->weighted) {
-        RC(ensure_state(g, 1));
+        const int W = pow2_words(kc);
+        RC(ensure_state(g, W));
         for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
-            BfsJob j = base_job(g, 1, dir ? g->rv : g->fw, dir ? g->fw : g->rv);
+            BfsJob j = base_job(g, W, dir ? g->rv : g->fw, dir ? g->fw : g->rv);
             j.k = kc;
             j.sources = d_sources;
             j.red = RED_LEVELS;
             j.dist_out = (dir ? g->distR : g->distF).as<uint32_t>();
-            RC(run_pass(g, 1, j, st));
+            j.dist_ld = cw;
+            RC(run_pass(g, W, j, st));
             if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
         }
         return CC_OK;
@@ -626,8 +648,10 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
-    RC(g->distF.ensure((size_t)n * kChunkSrc * 4));
-    if (g->directed) RC(g->distR.ensure((size_t)n * kChunkSrc * 4));
+    const int cw = chunk_width(g, k);
+    g->cw = cw;
+    RC(g->distF.ensure((size_t)n * cw * 4));
+    if (g->directed) RC(g->distR.ensure((size_t)n * cw * 4));
     RC(g->mask.ensure(n * 4));
     RC(g->Q0.ensure(n * 4));
     RC(g->Q1.ensure(n * 4));
@@ -642,13 +666,17 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st)
     CK(cudaMemsetAsync(g->errflag.p, 0, 4, st));
     const int32_t *src = g->sources.as<int32_t>();
     ReduceJob r = base_reduce(g, k, W);
-    for (int base = 0; base < k; base += kChunkSrc) {
-        const int kc = std::min(kChunkSrc, k - base);
-        RC(run_chunk(g, src + base, kc, st));
-        r.base = base;
-        r.kc = kc;
-        run_reduce1(r, st);
-        g->call_kernels += 1;
+    r.ld = cw;
+    for (int base = 0; base < k; base += cw) {
+        const int kc = std::min(cw, k - base);
+        RC(run_chunk(g, src + base, kc, cw, st));
+        for (int s = 0; s < kc; s += 32) {  // one reduction per 32 columns
+            r.base = base + s;
+            r.sub = s;
+            r.kc = std::min(32, kc - s);
+            run_reduce1(r, st);
+            g->call_kernels += 1;
+        }
     }
     unsigned long long dmax = 0;
     int err = 0;
@@ -702,6 +730,7 @@ int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
               g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), nullptr, st);
     g->call_kernels += 3;
     r.hist = g->hist.as<uint32_t>();
+    r.D = D;
     r.Lmask = g->Lmask.as<uint64_t>();
     r.lc2 = g->lc2.as<uint64_t>();
     if (g->sq) {
@@ -711,13 +740,18 @@ int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
         r.hcse = g->hcse.as<uint64_t>();
         r.fdist = g->fdist.as<uint32_t>();
     }
-    for (int base = 0; base < k; base += kChunkSrc) {
-        const int kc = std::min(kChunkSrc, k - base);
-        RC(run_chunk(g, src + base, kc, st));
-        r.base = base;
-        r.kc = kc;
-        run_reduce2(r, st);
-        g->call_kernels += 1;
+    const int cw = g->cw;
+    r.ld = cw;
+    for (int base = 0; base < k; base += cw) {
+        const int kc = std::min(cw, k - base);
+        RC(run_chunk(g, src + base, kc, cw, st));
+        for (int s = 0; s < kc; s += 32) {
+            r.base = base + s;
+            r.sub = s;
+            r.kc = std::min(32, kc - s);
+            run_reduce2(r, st);
+            g->call_kernels += 1;
+        }
     }
     run_tail(g->hist.as<uint32_t>(), DevCount{nullptr, D}, D + 1, k, g->TN.as<uint64_t>(),
              g->TS.as<uint64_t>(), st);
@@ -1276,8 +1310,9 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
         RC(g->sum2.ensure(n * 16));
         RC(g->ctl.ensure(sizeof(Ctl)));
         RC(g->sources.ensure((size_t)n * 4));
-        RC(g->distF.ensure((size_t)n * kChunkSrc * 4));
-        if (g->directed) RC(g->distR.ensure((size_t)n * kChunkSrc * 4));
+        const int cw = chunk_width(g, n);
+        RC(g->distF.ensure((size_t)n * cw * 4));
+        if (g->directed) RC(g->distR.ensure((size_t)n * cw * 4));
         RC(g->mask.ensure(n * 4));
         RC(g->Q0.ensure(n * 4));
         RC(g->Q1.ensure(n * 4));
@@ -1298,12 +1333,16 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
         r.sum2 = g->sum2.as<uint64_t>();
         r.err = g->errflag.as<int>();
         r.sum_only = 1;
-        for (int64_t base = 0; base < n; base += kChunkSrc) {
-            const int kc = (int)std::min<int64_t>(kChunkSrc, n - base);
-            RC(run_chunk(g, g->sources.as<int32_t>() + base, kc, st));
-            r.base = (int)base;
-            r.kc = kc;
-            run_reduce1(r, st);
+        r.ld = cw;
+        for (int64_t base = 0; base < n; base += cw) {
+            const int kc = (int)std::min<int64_t>(cw, n - base);
+            RC(run_chunk(g, g->sources.as<int32_t>() + base, kc, cw, st));
+            for (int s = 0; s < kc; s += 32) {
+                r.base = (int)base + s;
+                r.sub = s;
+                r.kc = std::min(32, kc - s);
+                run_reduce1(r, st);
+            }
         }
         int err = 0;
         CK(cudaMemcpy(&err, g->errflag.p, 4, cudaMemcpyDeviceToHost));

@@ -30,7 +30,7 @@ enum : uint32_t {
     RED_DCC = 4u,    // delta_cc[i][j] for sampled nodes
     RED_HIST = 8u,   // per-source level histogram over V \ C
     RED_LC = 16u,    // hybrid pass: lc[v] += d, d^2 over sources in Lmask(v)
-    RED_LEVELS = 32u, // k <= 32: dist_out[v * 32 + i] = level of v from source i
+    RED_LEVELS = 32u, // dist_out[v * dist_ld + i] = level of v from source i
     // hybrid pass with the error estimate: for nodes flagged in sqflag,
     // hcse[v] += (d(c_i, v) - d(c(v), c_i))^2 over c_i beyond the threshold
     // (flag 1: not in Lmask; 128-bit {lo, hi}), and fdist[v] = d(c_i, v) for
@@ -117,7 +117,8 @@ struct BfsJob {
     // When set, the pass does nothing if gate[0] = gate[1] = 0 (the hybrid
     // preparation found no node needing the second pass).
     const unsigned *gate;
-    uint32_t *dist_out;     // RED_LEVELS: n x 32 chunk of levels
+    uint32_t *dist_out;     // RED_LEVELS: n x dist_ld chunk of levels
+    int dist_ld;            // RED_LEVELS: row stride of dist_out (>= k)
     const uint8_t *sqflag;  // RED_SQ: per node, 1 = accumulate hcse, 2 = record fdist
     const int32_t *istar;   // RED_SQ: per sample index, the farthest other sample
     uint64_t *hcse;         // RED_SQ: n x 2

@@ -365,10 +365,14 @@ __global__ void k_swap_keys(const uint64_t *keys, const uint32_t *vals, int64_t 
 __global__ void k_pivot_score(const int64_t *rp, const int64_t *rrp, int64_t n,
                               unsigned long long *best)
 {
+    unsigned long long m = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        atomicMax(best, (unsigned long long)(rp[v + 1] - rp[v]) *
-                            (unsigned long long)(rrp[v + 1] - rrp[v]));
+        m = max(m, (unsigned long long)(rp[v + 1] - rp[v]) *
+                       (unsigned long long)(rrp[v + 1] - rrp[v]));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(best, m);  // one atomic per warp
 }
 
 __global__ void k_pivot_pick(const int64_t *rp, const int64_t *rrp, int64_t n,

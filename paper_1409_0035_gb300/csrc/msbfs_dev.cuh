@@ -165,7 +165,7 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         while (b) {
             const int i = w * 64 + __ffsll((long long)b) - 1;
             b &= b - 1;
-            J.dist_out[(int64_t)v * 32 + i] = (uint32_t)l;
+            J.dist_out[(int64_t)v * J.dist_ld + i] = (uint32_t)l;
         }
     }
     if ((J.red & RED_DCC) && sx >= 0 && nw) {
@@ -557,7 +557,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     if (J.red & RED_LC)
         for (int64_t i = gtid; i < 2 * n; i += gthreads) J.lc2[i] = 0;
     if (J.red & RED_LEVELS)
-        for (int64_t i = gtid; i < n * 32; i += gthreads) J.dist_out[i] = kInf;
+        for (int64_t i = gtid; i < n * J.dist_ld; i += gthreads) J.dist_out[i] = kInf;
     if (!sync_after(CC_PH_INIT)) return;
     for (int64_t i = gtid; i < J.k; i += gthreads) {
         const int v = J.sources[i];
@@ -566,7 +566,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         atomicOr((unsigned long long *)&J.vis[vw], bit);
         atomicOr((unsigned long long *)&J.F0[vw], bit);
         J.fstamp[v] = 0u;
-        if (J.red & RED_LEVELS) J.dist_out[(int64_t)v * 32 + i] = 0u;
+        if (J.red & RED_LEVELS) J.dist_out[(int64_t)v * J.dist_ld + i] = 0u;
         if (J.red & RED_PIVOT) { J.pivot[v] = (int)i; J.delta[v] = 0; }
         if (J.red & RED_DCC) J.dcc[i * J.dcc_k + J.sidx[v]] = 0;
         const unsigned long long d = (unsigned long long)(rp[v + 1] - rp[v]);

@@ -122,9 +122,9 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x)
 __device__ __forceinline__ uint64_t chunk_dist(const ReduceJob &R, int64_t v, int lane)
 {
     if (lane >= R.kc) return (uint64_t)kInf;
-    const uint64_t a = R.distF[v * kChunkSrc + lane];
+    const uint64_t a = R.distF[v * R.ld + R.sub + lane];
     if (!R.distR) return a;
-    const uint64_t b = R.distR[v * kChunkSrc + lane];
+    const uint64_t b = R.distR[v * R.ld + R.sub + lane];
     if (a == kInf || b == kInf) return (uint64_t)kInf;
     return a + b;
 }
@@ -172,17 +172,31 @@ __global__ void k_reduce1(ReduceJob R)
 
 // Pass-2 reduction of one chunk for the hybrid estimator: per-source
 // distance histogram over V \ C and the sums over the sources in L(v).
+// The histogram of this chunk's columns is accumulated per CTA in shared
+// memory when the distances are small (D < kSmemHistRows), then added to the
+// global one: many nodes share a (distance, source) cell.
+constexpr int kSmemHistRows = 256;
+
 __global__ void k_reduce2(ReduceJob R)
 {
+    extern __shared__ unsigned sh[];  // (D+1) x 32 when D < kSmemHistRows
+    const bool local = R.D < kSmemHistRows;
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int gi = R.base + lane;
+    if (local) {
+        for (int i = threadIdx.x; i < (R.D + 1) * 32; i += blockDim.x) sh[i] = 0u;
+        __syncthreads();
+    }
     for (int64_t v = gwarp; v < R.n; v += nwarps) {
         if (R.sidx[v] >= 0) continue;
         const bool valid = lane < R.kc;
         const uint64_t d = valid ? chunk_dist(R, v, lane) : 0;
-        if (valid) atomicAdd(&R.hist[(int64_t)d * R.k + gi], 1u);
+        if (valid) {
+            if (local) atomicAdd(&sh[d * 32 + lane], 1u);
+            else atomicAdd(&R.hist[(int64_t)d * R.k + gi], 1u);
+        }
         bool inL = false;
         if (valid) {
             const uint64_t m = R.Lmask[v * R.W + (gi >> 6)];
@@ -220,6 +234,13 @@ __global__ void k_reduce2(ReduceJob R)
                 }
             }
             if ((f & 2) && valid && gi == R.istar[p]) R.fdist[v] = (uint32_t)d;
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < (R.D + 1) * 32; i += blockDim.x) {
+            const int l = i >> 5, c = i & 31;
+            if (c < R.kc && sh[i]) atomicAdd(&R.hist[(int64_t)l * R.k + R.base + c], sh[i]);
         }
     }
 }
@@ -292,7 +313,8 @@ void run_reduce1(const ReduceJob &r, cudaStream_t st)
 
 void run_reduce2(const ReduceJob &r, cudaStream_t st)
 {
-    k_reduce2<<<grid_of(r.n * 32), 256, 0, st>>>(r);
+    const size_t smem = r.D < kSmemHistRows ? (size_t)(r.D + 1) * 32 * 4 : 0;
+    k_reduce2<<<grid_of(r.n * 32), 256, smem, st>>>(r);
 }
 
 void run_unpack_pivot(int64_t n, const unsigned long long *best, int32_t *pivot,

@@ -29,7 +29,8 @@ struct ReduceJob {
     int64_t n;
     int k, kc, base, W;
     int sum_only;                   // exact mode: only sum2 and the reachability check
-    const uint32_t *distF, *distR;  // n x 32 each (distR NULL unless round trip)
+    const uint32_t *distF, *distR;  // n x ld each (distR NULL unless round trip)
+    int ld, sub;                    // row stride; this job's first column
     const int32_t *sidx;
     uint64_t *sum2;                 // n x 2
     unsigned long long *best;       // n: (distance << 32 | sample index) minimum
@@ -38,6 +39,7 @@ struct ReduceJob {
     unsigned long long *dmax;       // 1
     int *err;                       // 1
     uint32_t *hist;                 // (D+1) x k
+    int64_t D;                      // largest distance (hist has D+1 rows)
     const uint64_t *Lmask;          // n x W
     uint64_t *lc2;                  // n x 2
     // error estimate (null sqflag: not wanted): per node flag 1 adds
