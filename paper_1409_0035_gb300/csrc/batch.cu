@@ -380,7 +380,7 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         b->k.push_back(k);
         b->W.push_back(W);
         auto &bf = b->bufs[i];
-        bf.resize(32);
+        bf.resize(40);
         int q = 0;
         auto take = [&](size_t bytes) -> void * {
             if (dalloc(bf[q], bytes) != CC_OK) return nullptr;
@@ -396,6 +396,7 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         j.k = k;
         j.Llist = v.L; j.Mlist = v.M; j.Hlist = v.H;
         j.nL = v.nL; j.nM = v.nM; j.nH = v.nH;
+        j.Tlist = v.T; j.Tadj = v.Tadj; j.nT = v.nT;
         j.Hch_node = v.Hn; j.Hch_begin = v.Hb; j.nHch = v.nHch;
         j.tHn = v.Hn; j.tHb = v.Hb; j.ntH = v.nHch;
         j.prp = v.rp; j.pcol = v.col;
@@ -417,7 +418,11 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         j.sources = (int32_t *)p[16];
         j.ACH0 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nHch) * 4);
         j.ACH1 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nHch) * 4);
-        if (!j.ACH0 || !j.ACH1) return CC_ERR_OOM;
+        j.AT0 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nT) * 4);
+        j.AT1 = (int32_t *)take((size_t)std::max<int64_t>(1, v.nT) * 4);
+        j.ATa0 = (int4 *)take((size_t)std::max<int64_t>(1, v.nT) * 16);
+        j.ATa1 = (int4 *)take((size_t)std::max<int64_t>(1, v.nT) * 16);
+        if (!j.ACH0 || !j.ACH1 || !j.AT0 || !j.AT1 || !j.ATa0 || !j.ATa1) return CC_ERR_OOM;
         B_CK(cudaMemcpy(p[16], samples[i], (size_t)k * 4, cudaMemcpyHostToDevice));
         j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
         j.timeout_ns = 10ull * 1000 * 1000 * 1000;

@@ -46,9 +46,27 @@ struct DevBuf {
 
 // Degree classes of one CSR for the bottom-up scan.
 struct Classes {
-    DevBuf L, M, H, Hn, Hb;
-    int64_t nL = 0, nM = 0, nH = 0, nHch = 0;
+    DevBuf L, M, H, Hn, Hb, T, Tadj;
+    int64_t nL = 0, nM = 0, nH = 0, nHch = 0, nT = 0;
 };
+
+// Inline adjacency of the tiny nodes (degree <= kTinyMaxDeg): their
+// neighbours as one int4, -1 where the row is shorter.
+__global__ void k_tiny_adj(const int32_t *T, int64_t nT, const int64_t *rp, const int32_t *col,
+                           int4 *adj)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nT;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = T[t];
+        const int64_t b = rp[v], d = rp[v + 1] - b;
+        int4 a = make_int4(-1, -1, -1, -1);
+        if (d > 0) a.x = col[b];
+        if (d > 1) a.y = col[b + 1];
+        if (d > 2) a.z = col[b + 2];
+        if (d > 3) a.w = col[b + 3];
+        adj[t] = a;
+    }
+}
 
 struct DevCSR {
     DevBuf rp, col, w;
@@ -64,7 +82,8 @@ struct cc_graph {
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
-        distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp;
+        distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp, AT0, AT1, ATa0,
+        ATa1;
     // error estimate of the hybrid (SqErrEst): squared errors, fallback
     // distances, per-node flags, farthest-sample table, staged output
     DevBuf hcse, fdist, sqflag, istar, sqe;
@@ -115,26 +134,31 @@ int upload(DevBuf &b, const void *src, size_t bytes)
     return CC_OK;
 }
 
-int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c)
+int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c, const int64_t *drp,
+                  const int32_t *dcol)
 {
-    // Light and medium nodes are ordered by degree (stable counting sort,
-    // ties by id).  A warp scans W-lane groups of light nodes in lock step,
+    // Tiny, light and medium nodes are ordered by degree (stable counting
+    // sort, ties by id).  A warp scans W-lane groups of nodes in lock step,
     // so equal degrees keep its lanes busy for the same number of steps; and
     // warps take every nwarps-th entry of a list, so a sorted list hands
-    // every warp about the same number of CSR entries.
+    // every warp about the same number of CSR entries.  Tiny nodes (degree
+    // <= kTinyMaxDeg) carry their neighbours inline (one int4), which takes
+    // two dependent loads out of their scan.
     std::vector<int64_t> start(kMediumMaxDeg + 2, 0);
     for (int64_t v = 0; v < n; ++v) {
         const int64_t d = rp[v + 1] - rp[v];
         if (d <= kMediumMaxDeg) start[d + 1] += 1;
     }
     for (int d = 0; d <= kMediumMaxDeg; ++d) start[d + 1] += start[d];
+    const int64_t ntiny = start[kTinyMaxDeg + 1];
     const int64_t nlight = start[kLightMaxDeg + 1];
-    std::vector<int32_t> L((size_t)nlight), M((size_t)(start[kMediumMaxDeg + 1] - nlight)), H,
-        Hn;
+    std::vector<int32_t> T((size_t)ntiny), L((size_t)(nlight - ntiny)),
+        M((size_t)(start[kMediumMaxDeg + 1] - nlight)), H, Hn;
     std::vector<int64_t> Hb;
     for (int64_t v = 0; v < n; ++v) {
         const int64_t d = rp[v + 1] - rp[v];
-        if (d <= kLightMaxDeg) L[(size_t)start[d]++] = (int32_t)v;
+        if (d <= kTinyMaxDeg) T[(size_t)start[d]++] = (int32_t)v;
+        else if (d <= kLightMaxDeg) L[(size_t)(start[d]++ - ntiny)] = (int32_t)v;
         else if (d <= kMediumMaxDeg) M[(size_t)(start[d]++ - nlight)] = (int32_t)v;
         else {
             H.push_back((int32_t)v);
@@ -146,6 +170,15 @@ int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c)
     }
     c.nL = (int64_t)L.size(); c.nM = (int64_t)M.size(); c.nH = (int64_t)H.size();
     c.nHch = (int64_t)Hn.size();
+    c.nT = (int64_t)T.size();
+    RC(upload(c.T, T.data(), T.size() * 4));
+    RC(c.Tadj.ensure((size_t)std::max<int64_t>(c.nT, 1) * 16));
+    if (c.nT > 0) {
+        const int64_t g = std::min<int64_t>((c.nT + 255) / 256, 152 * 32);
+        k_tiny_adj<<<(int)g, 256>>>(c.T.as<int32_t>(), c.nT, drp, dcol, c.Tadj.as<int4>());
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());  // estimates may run on other streams
+    }
     RC(upload(c.L, L.data(), L.size() * 4));
     RC(upload(c.M, M.data(), M.size() * 4));
     RC(upload(c.H, H.data(), H.size() * 4));
@@ -160,7 +193,7 @@ int upload_csr(DevCSR &d, int64_t n, const std::vector<int64_t> &rp,
     RC(upload(d.rp, rp.data(), rp.size() * 8));
     RC(upload(d.col, col.data(), col.size() * 4));
     if (!w.empty()) RC(upload(d.w, w.data(), w.size() * 4));
-    return build_classes(rp, n, d.cls);
+    return build_classes(rp, n, d.cls, d.rp.as<int64_t>(), d.col.as<int32_t>());
 }
 
 int pow2_words(int k)
@@ -187,6 +220,11 @@ int ensure_state(cc_graph *g, int W)
     const int64_t nch = std::max(g->fw.cls.nHch, g->rv.cls.nHch);
     RC(g->ACH0.ensure((size_t)nch * 4));
     RC(g->ACH1.ensure((size_t)nch * 4));
+    const int64_t nt = std::max<int64_t>(std::max(g->fw.cls.nT, g->rv.cls.nT), 1);
+    RC(g->AT0.ensure((size_t)nt * 4));
+    RC(g->AT1.ensure((size_t)nt * 4));
+    RC(g->ATa0.ensure((size_t)nt * 16));
+    RC(g->ATa1.ensure((size_t)nt * 16));
     RC(g->fstamp.ensure(n * 4));
     RC(g->tflag.ensure(n * 4));
     RC(g->sidx.ensure(n * 4));
@@ -232,6 +270,13 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
     j.AL1 = g->AL1.as<int32_t>();
     j.ACH0 = g->ACH0.as<int32_t>();
     j.ACH1 = g->ACH1.as<int32_t>();
+    j.Tlist = csr.cls.T.as<int32_t>();
+    j.Tadj = csr.cls.Tadj.as<int4>();
+    j.nT = csr.cls.nT;
+    j.AT0 = g->AT0.as<int32_t>();
+    j.AT1 = g->AT1.as<int32_t>();
+    j.ATa0 = g->ATa0.as<int4>();
+    j.ATa1 = g->ATa1.as<int4>();
     j.fstamp = g->fstamp.as<uint32_t>();
     j.tflag = g->tflag.as<unsigned>();
     j.sidx = g->sidx.as<int32_t>();
@@ -352,7 +397,8 @@ int adopt_device_reverse(cc_graph *g, DeviceCSR &d)
         g->rv.w.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
     }
     d.rp = d.col = d.w = nullptr;
-    return build_classes(d.rp_host, d.n, g->rv.cls);
+    return build_classes(d.rp_host, d.n, g->rv.cls, g->rv.rp.as<int64_t>(),
+                         g->rv.col.as<int32_t>());
 }
 
 // Take ownership of a CSR built on the device.
@@ -370,27 +416,31 @@ int adopt_device_csr(cc_graph *g, DeviceCSR &d)
         g->fw.w.cap = (size_t)std::max<int64_t>(d.arcs, 1) * 4;
     }
     d.rp = d.col = d.w = nullptr;
-    return build_classes(d.rp_host, d.n, g->fw.cls);
+    return build_classes(d.rp_host, d.n, g->fw.cls, g->fw.rp.as<int64_t>(),
+                         g->fw.col.as<int32_t>());
 }
 
 void free_graph(cc_graph *g)
 {
     if (g->borrowed) {  // drop the borrowed CSR pointers unfreed
         DevBuf *csr[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
-                         &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->rv.rp, &g->rv.col,
+                         &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->fw.cls.T, &g->fw.cls.Tadj,
+                     &g->rv.rp, &g->rv.col,
                          &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
-                         &g->rv.cls.Hb};
+                         &g->rv.cls.Hb, &g->rv.cls.T, &g->rv.cls.Tadj};
         for (DevBuf *b : csr) { b->p = nullptr; b->cap = 0; }
     }
     DevBuf *all[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
-                     &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->rv.rp, &g->rv.col,
+                     &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->fw.cls.T, &g->fw.cls.Tadj,
+                     &g->rv.rp, &g->rv.col,
                      &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
-                     &g->rv.cls.Hb, &g->vis, &g->F0, &g->F1, &g->nxt, &g->Q0, &g->Q1,
+                     &g->rv.cls.Hb, &g->rv.cls.T, &g->rv.cls.Tadj, &g->vis, &g->F0, &g->F1, &g->nxt, &g->Q0, &g->Q1,
                      &g->T, &g->tflag, &g->sidx, &g->sum2, &g->pivot, &g->delta, &g->lc2,
                      &g->Lmask, &g->hp, &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp,
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
-                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
+                     &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
+                     &g->ATa0, &g->ATa1,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
@@ -894,7 +944,8 @@ int ccg::graph_borrow(cc_graph_t dst, cc_graph_t src)
         Classes &c = d ? dst->rv.cls : dst->fw.cls;
         const Classes &s = d ? src->rv.cls : src->fw.cls;
         cp(c.L, s.L); cp(c.M, s.M); cp(c.H, s.H); cp(c.Hn, s.Hn); cp(c.Hb, s.Hb);
-        c.nL = s.nL; c.nM = s.nM; c.nH = s.nH; c.nHch = s.nHch;
+        cp(c.T, s.T); cp(c.Tadj, s.Tadj);
+        c.nL = s.nL; c.nM = s.nM; c.nH = s.nH; c.nHch = s.nHch; c.nT = s.nT;
     }
     dst->alpha = src->alpha;
     dst->borrowed = true;
@@ -910,7 +961,8 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->dcc, &g->hist, &g->TN, &g->TS, &g->Ssamp, &g->maxd, &g->sources,
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
-                          &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp,
+                          &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
+                     &g->ATa0, &g->ATa1,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
@@ -931,6 +983,9 @@ int ccg::graph_view(cc_graph_t g, GraphView *v)
     v->rp = g->fw.rp.as<int64_t>();
     v->col = g->fw.col.as<int32_t>();
     v->L = g->fw.cls.L.as<int32_t>();
+    v->T = g->fw.cls.T.as<int32_t>();
+    v->Tadj = g->fw.cls.Tadj.as<int4>();
+    v->nT = g->fw.cls.nT;
     v->M = g->fw.cls.M.as<int32_t>();
     v->H = g->fw.cls.H.as<int32_t>();
     v->Hn = g->fw.cls.Hn.as<int32_t>();

@@ -18,6 +18,10 @@ constexpr int kBlock = 256;          // threads per CTA of the traversal kernel
 #ifndef CC_CHUNK
 #define CC_CHUNK 256
 #endif
+#ifndef CC_TINY_MAX_DEG
+#define CC_TINY_MAX_DEG 4
+#endif
+constexpr int kTinyMaxDeg = CC_TINY_MAX_DEG;     // neighbours inline (one int4)
 constexpr int kLightMaxDeg = 32;                 // thread-per-(node, word) scan
 constexpr int kMediumMaxDeg = CC_MEDIUM_MAX_DEG;  // warp-per-node scan
 constexpr int kChunk = CC_CHUNK;                 // CSR entries per heavy-node warp task
@@ -49,6 +53,8 @@ struct LevelCtl {
     unsigned int mlen;          // rebuilt medium list length (bottom-up)
     unsigned int hlen;          // rebuilt heavy list length (bottom-up)
     unsigned int hclen;         // rebuilt heavy chunk list length (bottom-up)
+    unsigned int tlen2;         // rebuilt tiny list length (bottom-up)
+    unsigned int pad_;
     unsigned long long ef;      // sum of degrees of the frontier nodes
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
@@ -102,6 +108,13 @@ struct BfsJob {
     // entry 0, medium from nL, heavy from nL + nM.
     int32_t *AL0, *AL1;
     int32_t *ACH0, *ACH1;           // nHch each: active heavy chunk tasks
+    // Tiny nodes (degree <= kTinyMaxDeg, pull side) with their neighbours
+    // inline, and the active copies of both.
+    const int32_t *Tlist;
+    const int4 *Tadj;
+    int64_t nT;
+    int32_t *AT0, *AT1;             // nT each
+    int4 *ATa0, *ATa1;              // nT each
     uint32_t *fstamp;               // n: last level a node got new bits
     unsigned int *tflag;            // n
     uint32_t red;
@@ -145,9 +158,10 @@ struct GraphView {
     bool directed, weighted;
     const int64_t *rp;
     const int32_t *col;
-    const int32_t *L, *M, *H, *Hn;
+    const int32_t *L, *M, *H, *Hn, *T;
+    const int4 *Tadj;
     const int64_t *Hb;
-    int64_t nL, nM, nH, nHch;
+    int64_t nL, nM, nH, nHch, nT;
     int alpha;
 };
 int graph_view(cc_graph_t g, GraphView *v);

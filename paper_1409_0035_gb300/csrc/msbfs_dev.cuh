@@ -364,10 +364,10 @@ __device__ void flush_level(const BfsJob &J, int l, LevelCtl *C, LaneAcc<W> &A,
 
 // Order-preserving stream compaction over [0, N) by all CTAs: each CTA
 // takes a contiguous slice, counts its keepers, reserves their slots with
-// one atomicAdd on *counter, then writes them in slice order.
-template <class Keep, class Get>
-__device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsigned *counter,
-                              unsigned team_rank, unsigned team_size)
+// one atomicAdd on *counter, then calls put(slot, i) for them in slice order.
+template <class Keep, class Put>
+__device__ void block_compact_put(int64_t N, Keep keep, Put put, unsigned *counter,
+                                  unsigned team_rank, unsigned team_size)
 {
     __shared__ unsigned s_w[kBlock / 32];
     __shared__ unsigned s_base;
@@ -398,10 +398,20 @@ __device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsig
             if (q < wid) off += s_w[q];
             tot += s_w[q];
         }
-        if (k) out[base + off + __popc(bal & ((1u << lane) - 1u))] = get(i);
+        if (k) put(base + off + __popc(bal & ((1u << lane) - 1u)), i);
         base += tot;
         __syncthreads();
     }
+}
+
+// The same, writing out[slot] = get(i).
+template <class Keep, class Get>
+__device__ void block_compact(int64_t N, Keep keep, Get get, int32_t *out, unsigned *counter,
+                              unsigned team_rank, unsigned team_size)
+{
+    block_compact_put(
+        N, keep, [&](unsigned slot, int64_t i) { out[slot] = get(i); }, counter, team_rank,
+        team_size);
 }
 
 // Top-down push of one frontier node's words f (slot w per lane) to the
@@ -592,6 +602,11 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     const int32_t *HCcur = nullptr;
     int64_t al_len = J.nL, ml_len = J.nM, hl_len = J.nH, hc_len = J.nHch;
     int al_next = 0, ml_next = 0, hl_next = 0;
+    // Tiny nodes: the node list and the inline neighbours, compacted together.
+    const int32_t *TLcur = J.Tlist;
+    const int4 *TAcur = J.Tadj;
+    int64_t tl_len = J.nT;
+    int tl_next = 0;
     // Queue of a top-down level: the previous level's touched list when that
     // level was top-down (level 0 "touched" the sources), else built from
     // the frontier stamps.
@@ -626,7 +641,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
         if (gtid == 0) {
             LevelCtl *Z = &ctl->lev[(l + 1) & 3];
             Z->qlen = 0; Z->tlen = 0; Z->ninc_dec = 0; Z->ef = 0; Z->eu_dec = 0;
-            Z->alen = 0; Z->qcnt = 0; Z->mlen = 0; Z->hlen = 0; Z->hclen = 0;
+            Z->alen = 0; Z->qcnt = 0; Z->mlen = 0; Z->hlen = 0; Z->hclen = 0; Z->tlen2 = 0;
         }
         uint64_t *Fin = (l & 1) ? J.F0 : J.F1;
         uint64_t *Fout = (l & 1) ? J.F1 : J.F0;
@@ -708,15 +723,34 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             // ninc bounds the incomplete nodes of every class; the medium and
             // heavy lists are rebuilt with the light list (heavy nodes complete
             // early) or on their own bound.
-            const bool rb_l = 2 * ninc < al_len;
+            // The tiny and light lists are rebuilt together, once fewer than
+            // half of their entries can still be incomplete.
+            const bool rb_tl = 2 * ninc < al_len + tl_len;
+            const bool rb_t = rb_tl && tl_len > 0;
+            const bool rb_l = rb_tl && al_len > 0;
             const bool rb_m = ml_len > 0 && (rb_l || 2 * ninc < ml_len);
             const bool rb_h = hl_len > 0 && (rb_l || 2 * ninc < hl_len);
-            if (rb_l || rb_m || rb_h) {
+            if (rb_t || rb_l || rb_m || rb_h) {
                 auto incomplete = [&](int64_t v) {
                     bool inc = false;
                     for (int q = 0; q < W; ++q) inc |= J.vis[v * W + q] != ~0ull;
                     return inc;
                 };
+                if (rb_t) {
+                    int32_t *out = tl_next ? J.AT1 : J.AT0;
+                    int4 *aout = tl_next ? J.ATa1 : J.ATa0;
+                    const int32_t *in = TLcur;
+                    const int4 *ain = TAcur;
+                    block_compact_put(
+                        tl_len, [&](int64_t i) { return incomplete(in[i]); },
+                        [&](unsigned slot, int64_t i) {
+                            out[slot] = in[i];
+                            aout[slot] = ain[i];
+                        },
+                        &C->tlen2, team_rank, team_size);
+                    TLcur = out;
+                    TAcur = aout;
+                }
                 if (rb_l) {
                     int32_t *out = al_next ? J.AL1 : J.AL0;
                     const int32_t *in = ALcur;
@@ -753,9 +787,30 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 }
                 if (!sync_after(CC_PH_BU_REBUILD)) return;
                 const volatile LevelCtl *VC = C;
+                if (rb_t) { tl_len = VC->tlen2; tl_next ^= 1; }
                 if (rb_l) { al_len = VC->alen; al_next ^= 1; }
                 if (rb_m) { ml_len = VC->mlen; ml_next ^= 1; }
                 if (rb_h) { hl_len = VC->hlen; hc_len = VC->hclen; hl_next ^= 1; }
+            }
+            // A0: tiny nodes, one thread per (node, word); the neighbours come
+            // with the list entry, so every frontier word is gathered at once.
+            for (int64_t t = gwarp; t * NPW < tl_len; t += nwarps) {
+                const int64_t li = t * NPW + grp;
+                const bool valid = li < tl_len;
+                const int v = valid ? TLcur[li] : 0;
+                const int4 nb = valid ? TAcur[li] : make_int4(-1, -1, -1, -1);
+                const int64_t vw = (int64_t)v * W + w;
+                const uint64_t vis = valid ? J.vis[vw] : ~0ull;
+                const int deg = (nb.x >= 0) + (nb.y >= 0) + (nb.z >= 0) + (nb.w >= 0);
+                uint64_t acc = 0;
+                if (vis != ~0ull) {
+                    const int c4[4] = {nb.x, nb.y, nb.z, nb.w};
+                    unsigned wl = 0;
+                    acc = gather_cols<W, 4>(Fin, c4, w, wl);
+                    A.words += wl;
+                }
+                __syncwarp();
+                tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, false);
             }
             // A1: light nodes of the active list, one thread per (node, word).
             for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
