@@ -794,11 +794,24 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             // A0: tiny nodes, one thread per (node, word); the neighbours come
             // with the list entry, so every frontier word is gathered at once.
+            // The next tile's entries load while this tile's words are in
+            // flight.
+            int vnext = 0;
+            int4 nbnext = make_int4(-1, -1, -1, -1);
+            if (gwarp * NPW + grp < tl_len) {
+                vnext = TLcur[gwarp * NPW + grp];
+                nbnext = TAcur[gwarp * NPW + grp];
+            }
             for (int64_t t = gwarp; t * NPW < tl_len; t += nwarps) {
                 const int64_t li = t * NPW + grp;
                 const bool valid = li < tl_len;
-                const int v = valid ? TLcur[li] : 0;
-                const int4 nb = valid ? TAcur[li] : make_int4(-1, -1, -1, -1);
+                const int v = vnext;
+                const int4 nb = nbnext;
+                const int64_t ln = li + nwarps * NPW;
+                if (ln < tl_len) {
+                    vnext = TLcur[ln];
+                    nbnext = TAcur[ln];
+                }
                 const int64_t vw = (int64_t)v * W + w;
                 const uint64_t vis = valid ? J.vis[vw] : ~0ull;
                 const int deg = (nb.x >= 0) + (nb.y >= 0) + (nb.z >= 0) + (nb.w >= 0);
@@ -813,10 +826,12 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 tile_reduce<W>(J, l, valid, v, vis, acc & ~vis, deg, Fout, A, s_hist, false);
             }
             // A1: light nodes of the active list, one thread per (node, word).
+            int anext = gwarp * NPW + grp < al_len ? ALcur[gwarp * NPW + grp] : 0;
             for (int64_t t = gwarp; t * NPW < al_len; t += nwarps) {
                 const int64_t li = t * NPW + grp;
                 const bool valid = li < al_len;
-                const int v = valid ? ALcur[li] : 0;
+                const int v = valid ? anext : 0;
+                if (li + nwarps * NPW < al_len) anext = ALcur[li + nwarps * NPW];
                 const int64_t vw = (int64_t)v * W + w;
                 uint64_t vis = valid ? J.vis[vw] : ~0ull;
                 int64_t b = 0, e = 0;
