@@ -533,19 +533,42 @@ def run_extra(args):
         nn, arcs, _, _ = cc.cc_graph_info(g)
         m = arcs // 2
         C = cc.cc_sample_choose(g, K, SSEED)
+        # Device outputs throughout: the hybrid estimate and closeness, its
+        # error estimate, the adaptive choice.
+        dev = torch.device("cuda", 0)
+        st = torch.cuda.current_stream()
+        shat = torch.empty(nn, dtype=torch.float64, device=dev)
+        clo = torch.empty(nn, dtype=torch.float64, device=dev)
+        sqe = torch.empty(nn, dtype=torch.float64, device=dev)
+        choice = torch.empty(nn, dtype=torch.int32, device=dev)
         o = cc.cc_opts_default(K)
-        plain = _time_steps(lambda: cc.cc_estimate(g, C, o), args.steps, args.warmup, flush)
-        sq = _time_steps(lambda: cc.cc_estimate(g, C, o, want_sqerr=True), args.steps,
-                         args.warmup, flush)
-        ad = _time_steps(lambda: cc.cc_estimate_adaptive(g, C, o), args.steps, args.warmup,
+        o.device_outputs = 1
+        o.stream = st.cuda_stream
+        out_plain = cc.cc_out()
+        out_plain.s_hat[3], out_plain.closeness[3] = shat.data_ptr(), clo.data_ptr()
+        out_sq = cc.cc_out()
+        out_sq.s_hat[3], out_sq.closeness[3] = shat.data_ptr(), clo.data_ptr()
+        out_sq.sq_err = sqe.data_ptr()
+        plain = _time_steps(lambda: cc.cc_estimate(g, C, o, out_plain), args.steps,
+                            args.warmup, flush)
+        sq = _time_steps(lambda: cc.cc_estimate(g, C, o, out_sq), args.steps, args.warmup,
                          flush)
-        ch = cc.cc_estimate_adaptive(g, C, o)["choice"]
+        Cd = np.ascontiguousarray(C, dtype=np.int32)
+
+        def adaptive():
+            cc._chk(cc.lib().cc_estimate_adaptive(
+                g, Cd.ctypes.data_as(cc.ctypes.c_void_p), K, cc.ctypes.byref(o), 0, None,
+                None, shat.data_ptr(), clo.data_ptr(), sqe.data_ptr(), choice.data_ptr()),
+                "cc_estimate_adaptive")
+
+        ad = _time_steps(adaptive, args.steps, args.warmup, flush)
+        ch = choice.cpu().numpy()
         line.update(metric="all-node estimates/s", unit="estimates/s",
                     value=nn / (ad / 1e3), ms_per_step=ad,
                     plain_hybrid_ms=plain, with_sqerr_ms=sq, adaptive_ms=ad,
                     eps_chosen={str(e): int((ch == i).sum())
                                 for i, e in enumerate(cc.ADAPTIVE_EPS)},
-                    note="host outputs; each call includes the device-to-host copies",
+                    note="device outputs (hybrid estimate and closeness, error, choice)",
                     config={"workload": "adaptive", "graph": f"R-MAT scale {SCALE}, edge "
                             f"factor {EF}, seed {GSEED}, LCC", "n": nn, "m": m, "k": K})
         cc.cc_graph_free(g)
