@@ -10,7 +10,10 @@ Pieces:
   * the sample chooser, written from its definition (bottom-k of splitmix64
     keys);
   * ctypes calls into cc_oracle.c for BFS / Dijkstra, the k x n distance
-    table and the estimators of section 2 (eqs. (1), (3), (4)).
+    table and the estimators of section 2 (eqs. (1), (3), (4));
+  * node-weighted closeness (section 5) in plain Python integers: the
+    threshold tau, the exact-size weighted sample and the sampling and
+    hybrid estimates of S_beta from a distance table.
 """
 from __future__ import annotations
 
@@ -379,3 +382,159 @@ def default_eps(k: int):
     """eps = 1/sqrt(k) as the rational 1/round(sqrt(k)) (section 7 uses
     eps = sqrt(1/k); the garbled "eps = sqrt k" of section 2 is read so)."""
     return (1, max(1, int(round(k ** 0.5))))
+
+
+# --------------------------------------------------------------------------
+# Node-weighted closeness (section 5, "Weighted Centrality")
+# --------------------------------------------------------------------------
+#
+# Node weights beta(v) >= 0 (integers here).  S_beta(v) = sum over u != v of
+# beta(u) d(v, u) and the closeness is (sum of beta - beta(v)) / S_beta(v)
+# (eq. (2) read with the weight of the other endpoint j, as the text after it
+# computes the numerator).  The sample has exactly k nodes; node v is in it
+# with probability min(1, beta(v) / tau) and counts with the adjusted weight
+# max(tau, beta(v)).  tau is kept as the exact rational tn / td.
+
+
+def varopt_threshold(beta, k: int):
+    """The threshold tau = tn / td of section 5: the value with
+    sum over v of min(1, beta(v) / tau) = k.  With the weights sorted
+    b_0 >= b_1 >= ..., the h largest are taken with certainty and the rest in
+    proportion to weight, tau = (b_h + b_{h+1} + ...) / (k - h), for the
+    smallest h at which b_h < tau (then b_{h-1} >= tau holds too).  When
+    exactly k weights are positive every one of them is certain and
+    tau = (smallest positive weight) / 1."""
+    b = sorted((int(x) for x in beta if int(x) > 0), reverse=True)
+    if not 0 < k <= len(b):
+        raise ValueError("need 0 < k <= number of positive weights")
+    if len(b) == k:
+        return b[-1], 1
+    rest = sum(b)                      # b_h + b_{h+1} + ..., for h = 0
+    for h in range(k):
+        if b[h] * (k - h) < rest:      # b_h < rest / (k - h)
+            return rest, k - h
+        rest -= b[h]
+    raise AssertionError("unreachable: more than k positive weights")
+
+
+def is_certain(b: int, tau) -> bool:
+    """beta >= tau (inclusion probability 1), for a positive weight."""
+    return b * tau[1] >= tau[0]
+
+
+def systematic_pick(order, beta, tau, u: int):
+    """Systematic sampling with unequal probabilities (Madow 1949) of the
+    uncertain nodes along `order`: node v occupies the interval of length
+    beta(v) * td in a line of total length td * tn, and the td points
+    u, u + tn, u + 2 tn, ... (0 <= u < tn) pick the nodes whose interval
+    holds one; an interval shorter than tn holds at most one point, so node v
+    is picked for exactly beta(v) * td of the tn offsets u -- probability
+    beta(v) / tau.  Certain nodes are always picked, zero weights never.
+    Returns the picked nodes in `order`."""
+    tn, td = tau
+    picked = []
+    pos = 0
+
+    def points_below(x):               # points u + t tn (t >= 0) below x
+        return 0 if x <= u else (x - u + tn - 1) // tn
+
+    for v in order:
+        b = int(beta[v])
+        if b == 0:
+            continue
+        if is_certain(b, tau):
+            picked.append(int(v))
+            continue
+        lo, pos = pos, pos + b * td
+        if points_below(pos) > points_below(lo):
+            picked.append(int(v))
+    return picked
+
+
+def sample_order(n: int, seed: int) -> np.ndarray:
+    """Nodes in increasing (splitmix64_key(seed, v), v): a uniformly random
+    order, the same keys as choose_sample."""
+    keys = np.array([splitmix64_key(seed, v) for v in range(n)], dtype=np.uint64) \
+        if n <= 4096 else _keys_vec(seed, n)
+    return np.lexsort((np.arange(n), keys))
+
+
+def sample_varopt(beta, k: int, seed: int):
+    """Weighted sample of exactly k nodes (section 5): inclusion probability
+    min(1, beta(v) / tau) by systematic sampling along a random order; the
+    offset u is splitmix64 output number n of the stream `seed` scaled to
+    [0, tn) by a 64 x 64 -> 128-bit product (its high half).  Returns
+    (sample as int32 in the order's sequence, (tn, td))."""
+    beta = np.asarray(beta)
+    n = beta.size
+    tau = varopt_threshold(beta, k)
+    u = (splitmix64_key(seed, n) * tau[0]) >> 64
+    C = systematic_pick(sample_order(n, seed), beta, tau, u)
+    assert len(C) == k
+    return np.asarray(C, dtype=np.int32), tau
+
+
+def node_weighted_from_table(table: np.ndarray, sources, beta, tau, eps=(1, 8)):
+    """Node-weighted estimates of S_beta from a k x n metric table (section
+    5 and its modification of Algorithm 1).
+
+    Sampled node c_i: exact S_beta(c_i) = sum_u beta(u) d(c_i, u).
+    Other node v, with pivot p = c(v) (nearest sampled node, smallest index
+    on ties) and Delta = d(p, v); x is "beyond" when x a > Delta b (eps =
+    a/b):
+      sampling (inverse-probability) estimate:
+          sum over c in C of max(tau, beta(c)) d(c, v);
+      hybrid: every non-sampled w beyond from p counts beta(w) d(p, w)
+          (the H tail), every sampled c_i with d(p, c_i) beyond counts
+          beta(c_i) d(c_i, v) (HC), and the other sampled nodes count
+          max(tau, beta(c_i)) d(c_i, v) (the estimate of L).
+    Returns dict(S_samp (k, exact integers), num (2 x n numerators over td,
+    Python ints; sampled nodes hold S * td), s_hat (2 x n), closeness
+    (2 x n)), rows in the order sampling, hybrid."""
+    T = np.asarray(table, dtype=np.int64)
+    k, n = T.shape
+    C = [int(c) for c in sources]
+    beta = [int(x) for x in beta]
+    tn, td = int(tau[0]), int(tau[1])
+    a, b = int(eps[0]), int(eps[1])
+    bC = np.array([beta[c] for c in C], dtype=np.int64)
+    certain = np.array([is_certain(x, (tn, td)) for x in bC.tolist()], dtype=bool)
+    bvec = np.array(beta, dtype=np.int64)
+    S_samp = [int((bvec * T[i]).sum()) for i in range(k)]
+    sidx = {c: i for i, c in enumerate(C)}
+    notC = np.ones(n, dtype=bool)
+    notC[C] = False
+    total = sum(beta)
+    num = [[0] * n, [0] * n]
+    for v in range(n):
+        if v in sidx:
+            num[0][v] = num[1][v] = S_samp[sidx[v]] * td
+            continue
+        col = T[:, v]
+        # tau * sum of d over uncertain samples + beta * d over certain ones
+        num[0][v] = (tn * int(col[~certain].sum()) +
+                     td * int((bC[certain] * col[certain]).sum()))
+        p = int(np.argmin(col))          # first minimum: smallest index
+        delta = int(col[p])
+        row = T[p]
+        H = notC & (row * a > delta * b)
+        Hsum = int((bvec[H] * row[H]).sum())
+        HC = row[C] * a > delta * b
+        HCsum = int((bC[HC] * col[HC]).sum())
+        LC = ~HC
+        Lpart = (tn * int(col[LC & ~certain].sum()) +
+                 td * int((bC[LC & certain] * col[LC & certain]).sum()))
+        num[1][v] = td * (Hsum + HCsum) + Lpart
+    from fractions import Fraction
+    s_hat = np.array([[float(Fraction(x, td)) for x in row] for row in num])
+    wsum = np.array([float(total - beta[v]) for v in range(n)])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        clo = wsum[None, :] / s_hat
+    return dict(S_samp=S_samp, num=num, s_hat=s_hat, closeness=clo)
+
+
+def exact_weighted_S(table_all: np.ndarray, beta):
+    """S_beta(v) = sum_u beta(u) d(v, u) from an n x n table (rows: v)."""
+    T = np.asarray(table_all, dtype=np.int64)
+    bvec = np.asarray([int(x) for x in beta], dtype=np.int64)
+    return [int((T[v] * bvec).sum()) for v in range(T.shape[0])]

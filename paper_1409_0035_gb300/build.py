@@ -28,7 +28,8 @@ def sources():
 
 
 def _inputs():
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [
+    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + \
+        glob.glob(os.path.join(CSRC, "*.cuh")) + [
         os.path.join(ROOT, "include", "cc.h"), os.path.abspath(__file__)]
 
 
