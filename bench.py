@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--pool", default="default", choices=["default", "paper"],
                     help="serve workload: graph pool (paper: R-MAT to scale 22, grids to 4096^2)")
     ap.add_argument("--workload", default="rmat20",
-                    choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive"],
+                    choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive",
+                             "nodeweighted"],
                     help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
@@ -571,6 +572,56 @@ def run_extra(args):
                     note="device outputs (hybrid estimate and closeness, error, choice)",
                     config={"workload": "adaptive", "graph": f"R-MAT scale {SCALE}, edge "
                             f"factor {EF}, seed {GSEED}, LCC", "n": nn, "m": m, "k": K})
+        cc.cc_graph_free(g)
+    elif args.workload == "nodeweighted":
+        # Node-weighted closeness (section 5) on the headline graph with
+        # Pareto node weights: the weighted sample, then the sampling and
+        # hybrid estimates of S_beta (device outputs), beside the unweighted
+        # estimate of the same k.
+        n, s, d = synth.rmat_edges(SCALE, EF, seed=GSEED)
+        g, _ = cc.cc_graph_from_edges(n, s, d)
+        nn, arcs, _, _ = cc.cc_graph_info(g)
+        m = arcs // 2
+        beta = synth.pareto_node_weights(nn, seed=GSEED)
+        cc.cc_graph_set_node_weights(g, beta)
+        dev = torch.device("cuda", 0)
+        st = torch.cuda.current_stream()
+        bufs = [torch.empty(nn, dtype=torch.float64, device=dev) for _ in range(4)]
+        Sd = torch.empty(K, dtype=torch.int64, device=dev)
+        box = {}
+
+        def sample():
+            box["C"], box["tau"] = cc.cc_sample_varopt(g, K, SSEED)
+
+        t_sample = _time_steps(sample, args.steps, args.warmup, flush)
+        C, tau = box["C"], box["tau"]
+        o = cc.cc_opts_default(K)
+        o.device_outputs = 1
+        o.stream = st.cuda_stream
+        w = cc.cc_wout()
+        for e in range(2):
+            w.s_hat[e], w.closeness[e] = bufs[2 * e].data_ptr(), bufs[2 * e + 1].data_ptr()
+        w.S_sampled = Sd.data_ptr()
+        t_w = _time_steps(lambda: cc.cc_estimate_node_weighted(g, C, tau, o, out=w),
+                          args.steps, args.warmup, flush)
+        o.want_hybrid = 0
+        t_ws = _time_steps(lambda: cc.cc_estimate_node_weighted(g, C, tau, o, out=w),
+                           args.steps, args.warmup, flush)
+        o.want_hybrid = 1
+        Cu = cc.cc_sample_choose(g, K, SSEED)
+        ou = cc.cc_out()
+        ou.s_hat[3], ou.closeness[3] = bufs[0].data_ptr(), bufs[1].data_ptr()
+        t_u = _time_steps(lambda: cc.cc_estimate(g, Cu, o, ou), args.steps, args.warmup, flush)
+        line.update(value=K * m / (t_w / 1e3) / 1e9, ms_per_step=t_w,
+                    sample_ms=t_sample, weighted_hybrid_ms=t_w, weighted_sampling_only_ms=t_ws,
+                    unweighted_hybrid_ms=t_u, tau=list(tau),
+                    certain=int((beta[C].astype(np.uint64) * tau[1] >= tau[0]).sum()),
+                    note="value = k m / weighted-hybrid time; the weighted estimate runs "
+                         "on chunks of distance rows (two sweeps for the hybrid)",
+                    config={"workload": "nodeweighted", "graph": f"R-MAT scale {SCALE}, "
+                            f"edge factor {EF}, seed {GSEED}, LCC", "n": nn, "m": m, "k": K,
+                            "node_weights": "Pareto(1.2) x 10 + 1, capped at 10^6",
+                            "total_weight": int(beta.astype(np.uint64).sum())})
         cc.cc_graph_free(g)
     elif args.workload == "batch64":
         specs = batch64_graphs()

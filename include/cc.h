@@ -202,6 +202,62 @@ int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k,
                          double *sq_err, int32_t *choice);
 
 /*
+ * Node-weighted closeness (section 5, "Weighted Centrality"; its
+ * modification of Algorithm 1).  With node weights beta(v) >= 0,
+ * S_beta(v) = sum over u != v of beta(u) d(v, u) and the weighted closeness
+ * is (B - beta(v)) / S_beta(v), B the sum of all weights.
+ *
+ * cc_graph_set_node_weights -- attach beta (uint32[n], host, indexed by the
+ * graph's node numbering; NULL detaches).  The library copies it.  Errors:
+ * CC_ERR_ARG (null handle), CC_ERR_TOO_LARGE (B >= 2^40), CC_ERR_OOM,
+ * CC_ERR_CUDA.
+ */
+int cc_graph_set_node_weights(cc_graph_t g, const uint32_t *beta);
+
+/*
+ * cc_sample_varopt -- weighted sample of exactly k nodes (section 5): node v
+ * is in it with probability min(1, beta(v)/tau), tau the threshold with
+ * sum over v of min(1, beta(v)/tau) = k, written to tau_out[0] / tau_out[1]
+ * as an exact fraction (numerator, denominator).  The draw is systematic
+ * sampling with unequal probabilities along the order of splitmix64 keys
+ * (output number v of stream `seed` for node v, the keys of
+ * cc_sample_choose; ties by id), with offset floor(x * tau_num / 2^64),
+ * x = output number n of the stream.  sample_out int32[k] (host) lists the
+ * sampled nodes in that order.  Errors: CC_ERR_ARG (no weights attached,
+ * k < 1 or fewer than k positive weights), CC_ERR_OOM, CC_ERR_CUDA.
+ */
+int cc_sample_varopt(cc_graph_t g, int32_t k, uint64_t seed, int32_t *sample_out,
+                     uint64_t *tau_out);
+
+typedef struct {
+    double *s_hat[2];     /* n each: estimate of S_beta(v); [0] sampling
+                             (inverse probability: sum over c in C of
+                             max(tau, beta(c)) d(c, v)), [1] hybrid; sampled
+                             nodes get their exact S_beta                   */
+    double *closeness[2]; /* n each: (B - beta(v)) / s_hat                  */
+    uint64_t *S_sampled;  /* k: exact S_beta(c_i)                           */
+} cc_wout;
+
+/*
+ * cc_estimate_node_weighted -- node-weighted estimates from a weighted
+ * sample (e.g. cc_sample_varopt's) and its threshold tau = tau[0]/tau[1].
+ * Hybrid, for v not sampled with pivot p = c(v) and Delta = d(p, v) (x is
+ * beyond when x * eps_num > Delta * eps_den): each non-sampled w beyond from
+ * p counts beta(w) d(p, w), each sampled c_i with d(p, c_i) beyond counts
+ * beta(c_i) d(c_i, v), each other sampled node max(tau, beta(c_i)) d(c_i, v).
+ * Every estimate is an integer numerator over tau[1] divided once in FP64.
+ * Runs the sources in chunks of shortest-path rows for every graph kind
+ * (a second sweep for the hybrid when opts->want_hybrid).  opts: eps,
+ * want_hybrid, roundtrip (must match the graph), device_outputs, stream.
+ * Errors: CC_ERR_ARG (no weights attached, bad sample or tau = 0/x),
+ * CC_ERR_DISCONNECTED, CC_ERR_OOM, CC_ERR_TIMEOUT, CC_ERR_CUDA,
+ * CC_ERR_TOO_LARGE (B x largest distance >= 2^63, or the adjusted weights'
+ * sum x tau[1] x largest distance >= 2^64).
+ */
+int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
+                              const uint64_t *tau, const cc_opts *opts, cc_wout *out);
+
+/*
  * cc_exact -- exact S(v) and B^-1(v) = (n-1)/S(v) for every node (eq. (1))
  * by traversals from every node, packed 64 per word.  Meant for small
  * graphs (the cost is n traversals).  closeness double[n], S uint64[n] (host,

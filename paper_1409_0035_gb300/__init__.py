@@ -38,7 +38,8 @@ EXPORTS = (
     "cc_batch_info", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
-    "cc_estimate_adaptive",
+    "cc_estimate_adaptive", "cc_graph_set_node_weights", "cc_sample_varopt",
+    "cc_estimate_node_weighted",
 )
 
 PHASES = ("init", "td_queue", "td_push", "td_final", "bu_rebuild", "bu_light",
@@ -66,6 +67,11 @@ class cc_out(ctypes.Structure):
                 ("sq_err", ctypes.c_void_p)]
 
 
+class cc_wout(ctypes.Structure):
+    _fields_ = [("s_hat", ctypes.c_void_p * 2), ("closeness", ctypes.c_void_p * 2),
+                ("S_sampled", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -90,6 +96,9 @@ def lib():
         L.cc_estimate.argtypes = [P, P, i32, P, P]
         L.cc_estimate_adaptive.argtypes = [P, P, i32, P, i32, P, P, P, P, P, P]
         L.cc_exact.argtypes = [P, P, P]
+        L.cc_graph_set_node_weights.argtypes = [P, P]
+        L.cc_sample_varopt.argtypes = [P, i32, u64, P, P]
+        L.cc_estimate_node_weighted.argtypes = [P, P, i32, P, P, P]
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_pass_phases.argtypes = [P, P]
@@ -256,6 +265,55 @@ def cc_estimate_adaptive(g, sample, opts=None, eps_list=None):
                                     _p(res["s_hat"]), _p(res["closeness"]),
                                     _p(res["sq_err"]), _p(res["choice"])),
          "cc_estimate_adaptive")
+    return res
+
+
+def cc_graph_set_node_weights(g, beta):
+    """Attach node weights beta (uint32[n], the graph's numbering; None
+    detaches) for the node-weighted estimates of section 5."""
+    if beta is None:
+        _chk(lib().cc_graph_set_node_weights(g, None), "cc_graph_set_node_weights")
+        return
+    b = np.ascontiguousarray(beta, dtype=np.uint32)
+    if b.size != cc_graph_info(g)[0]:
+        raise ValueError("need one weight per node")
+    _chk(lib().cc_graph_set_node_weights(g, _p(b)), "cc_graph_set_node_weights")
+
+
+def cc_sample_varopt(g, k, seed):
+    """Weighted sample of exactly k nodes (section 5): returns (sample int32[k],
+    tau as the fraction (numerator, denominator))."""
+    out = np.empty(int(k), np.int32)
+    tau = np.zeros(2, np.uint64)
+    _chk(lib().cc_sample_varopt(g, int(k), ctypes.c_uint64(seed & (2**64 - 1)), _p(out),
+                                _p(tau)), "cc_sample_varopt")
+    return out, (int(tau[0]), int(tau[1]))
+
+
+def cc_estimate_node_weighted(g, sample, tau, opts=None, out=None):
+    """Node-weighted estimates (section 5) from a weighted sample and its tau.
+    With `out` (a filled cc_wout) the call writes there; otherwise returns
+    a dict of host arrays s_hat (2 x n: sampling, hybrid), closeness (2 x n)
+    and S_sampled (k)."""
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    k = sample.size
+    t = np.ascontiguousarray([int(tau[0]), int(tau[1])], dtype=np.uint64)
+    if opts is None:
+        opts = cc_opts_default(k)
+    if out is not None:
+        _chk(lib().cc_estimate_node_weighted(g, _p(sample), k, _p(t), ctypes.byref(opts),
+                                             ctypes.byref(out)), "cc_estimate_node_weighted")
+        return out
+    n = cc_graph_info(g)[0]
+    res = dict(s_hat=np.zeros((2, n)), closeness=np.zeros((2, n)),
+               S_sampled=np.empty(k, np.uint64))
+    o = cc_wout()
+    for e in range(2):
+        o.s_hat[e] = _p(res["s_hat"][e])
+        o.closeness[e] = _p(res["closeness"][e])
+    o.S_sampled = _p(res["S_sampled"])
+    _chk(lib().cc_estimate_node_weighted(g, _p(sample), k, _p(t), ctypes.byref(opts),
+                                         ctypes.byref(o)), "cc_estimate_node_weighted")
     return res
 
 

@@ -10,6 +10,7 @@
 #include "cc_internal.h"
 #include "estimate.h"
 #include "graph_gpu.h"
+#include "nodew.h"
 #include "sssp.h"
 
 using namespace ccg;
@@ -90,6 +91,12 @@ struct cc_graph {
     // adaptive hybrid: one eps's estimate and error, the best so far, choice
     DevBuf ad_est, ad_sq, ad_best, ad_bsq, ad_clo, ad_choice;
     DevBuf pt_clo1, pt_est2, pt_clo2, pt_clo0;  // estimator tables of the finalisation
+    // node weights (section 5) and the node-weighted pipeline: sampler
+    // scratch, threshold, adjusted weights, sums, histogram, tails, outputs
+    DevBuf beta, nw_keys, nw_tk, nw_vals, nw_tv, nw_pre, nw_flags, nw_tau, nw_pick, nw_mu,
+        nw_bsrc, nw_msum, nw_wsum, nw_S, nw_hist, nw_TS, nw_lc, nw_out;
+    uint64_t beta_total = 0;
+    bool has_beta = false;
     bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t D1 = 0;        // levels (largest distance) of the last first pass
     int cw = 32;           // sources per chunk of the last chunked first pass
@@ -443,7 +450,11 @@ void free_graph(cc_graph *g)
                      &g->ATa0, &g->ATa1,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
-                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
+                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
+                     &g->beta, &g->nw_keys, &g->nw_tk, &g->nw_vals, &g->nw_tv, &g->nw_pre,
+                     &g->nw_flags, &g->nw_tau, &g->nw_pick, &g->nw_mu, &g->nw_bsrc,
+                     &g->nw_msum, &g->nw_wsum, &g->nw_S, &g->nw_hist, &g->nw_TS, &g->nw_lc,
+                     &g->nw_out};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -618,8 +629,10 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
     if (!g->weighted) {
         const int W = pow2_words(kc);
         RC(ensure_state(g, W));
+        // An undirected graph is its own reverse (no separate G^T is kept).
+        const DevCSR &gt = g->directed ? g->rv : g->fw;
         for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
-            BfsJob j = base_job(g, W, dir ? g->rv : g->fw, dir ? g->fw : g->rv);
+            BfsJob j = base_job(g, W, dir ? gt : g->fw, dir ? g->fw : gt);
             j.k = kc;
             j.sources = d_sources;
             j.red = RED_LEVELS;
@@ -694,7 +707,8 @@ ReduceJob base_reduce(cc_graph *g, int k, int W)
 // First pass of the chunked path (weighted graphs, round trips): 32-source
 // chunks of shortest paths reduced into sums, pivots, Delta, delta_cc and
 // the exact S of the sampled nodes.
-int chunked_pass1(cc_graph *g, int k, cudaStream_t st)
+// nw (optional): the node-weighted sums, reduced from the same rows.
+int chunked_pass1(cc_graph *g, int k, cudaStream_t st, const NwJob *nw = nullptr)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
@@ -726,6 +740,17 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st)
             r.kc = std::min(32, kc - s);
             run_reduce1(r, st);
             g->call_kernels += 1;
+            if (nw) {
+                NwJob j = *nw;
+                j.distF = g->distF.as<uint32_t>();
+                j.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+                j.base = r.base;
+                j.sub = s;
+                j.kc = r.kc;
+                j.ld = cw;
+                run_nw_reduce1(j, st);
+                g->call_kernels += 1;
+            }
         }
     }
     unsigned long long dmax = 0;
@@ -965,7 +990,11 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                      &g->ATa0, &g->ATa1,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
-                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0};
+                     &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
+                     &g->beta, &g->nw_keys, &g->nw_tk, &g->nw_vals, &g->nw_tv, &g->nw_pre,
+                     &g->nw_flags, &g->nw_tau, &g->nw_pick, &g->nw_mu, &g->nw_bsrc,
+                     &g->nw_msum, &g->nw_wsum, &g->nw_S, &g->nw_hist, &g->nw_TS, &g->nw_lc,
+                     &g->nw_out};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;
@@ -1348,6 +1377,216 @@ int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k, const c
     if (closeness) CK(cudaMemcpyAsync(closeness, g->ad_clo.p, n * 8, kind, st));
     if (sq_err) CK(cudaMemcpyAsync(sq_err, g->ad_bsq.p, n * 8, kind, st));
     if (choice) CK(cudaMemcpyAsync(choice, g->ad_choice.p, n * 4, kind, st));
+    CK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+int cc_graph_set_node_weights(cc_graph_t g, const uint32_t *beta)
+{
+    if (!g) return CC_ERR_ARG;
+    g->has_beta = false;
+    g->beta_total = 0;
+    if (!beta) {
+        g->beta.release();
+        return CC_OK;
+    }
+    RC(device_ok());
+    const int64_t n = g->n;
+    RC(g->beta.ensure((size_t)n * 4));
+    RC(g->nw_msum.ensure(16));
+    CK(cudaMemcpy(g->beta.p, beta, (size_t)n * 4, cudaMemcpyHostToDevice));
+    uint64_t B = 0;
+    RC(nw_total(g->beta.as<uint32_t>(), n, g->nw_msum.as<uint64_t>(), &B, 0));
+    if (B >= (1ull << 40)) return CC_ERR_TOO_LARGE;
+    g->beta_total = B;
+    g->has_beta = true;
+    return CC_OK;
+}
+
+namespace {
+
+int ensure_sampler_scratch(cc_graph *g)
+{
+    const size_t n = (size_t)g->n;
+    RC(g->nw_keys.ensure(n * 8));
+    RC(g->nw_tk.ensure(n * 8));
+    RC(g->nw_vals.ensure(n * 4));
+    RC(g->nw_tv.ensure(n * 4));
+    RC(g->nw_pre.ensure(n * 8));
+    RC(g->nw_flags.ensure(n * 8));
+    RC(g->nw_tau.ensure(32));
+    return CC_OK;
+}
+
+}  // namespace
+
+int cc_sample_varopt(cc_graph_t g, int32_t k, uint64_t seed, int32_t *sample_out,
+                     uint64_t *tau_out)
+{
+    if (!g || !sample_out || !tau_out || k < 1 || k > g->n || !g->has_beta) return CC_ERR_ARG;
+    RC(device_ok());
+    cudaStream_t st = 0;
+    const int64_t n = g->n;
+    RC(ensure_sampler_scratch(g));
+    RC(g->nw_pick.ensure((size_t)k * 4));
+    uint64_t *tau4 = g->nw_tau.as<uint64_t>();
+    RC(nw_threshold(g->beta.as<uint32_t>(), n, k, g->nw_keys.as<uint64_t>(),
+                    g->nw_vals.as<uint32_t>(), g->nw_tk.as<uint64_t>(), g->nw_tv.as<uint32_t>(),
+                    g->nw_pre.as<uint64_t>(), tau4, st));
+    uint64_t t4[4];
+    CK(cudaMemcpy(t4, tau4, sizeof(t4), cudaMemcpyDeviceToHost));
+    if (t4[2] < (uint64_t)k) return CC_ERR_ARG;  // fewer than k positive weights
+    if (t4[1] == 0) return CC_ERR_CUDA;           // cannot happen (see nw_threshold)
+    int64_t drawn = 0;
+    RC(nw_draw(g->beta.as<uint32_t>(), n, k, seed, tau4, g->nw_keys.as<uint64_t>(),
+               g->nw_vals.as<uint32_t>(), g->nw_tk.as<uint64_t>(), g->nw_tv.as<uint32_t>(),
+               g->nw_pre.as<uint64_t>(), g->nw_flags.as<uint64_t>(), g->nw_pick.as<int32_t>(),
+               &drawn, st));
+    // The draw picks the certain nodes and exactly k - (their number) others.
+    if (drawn != k) return CC_ERR_CUDA;
+    CK(cudaMemcpy(sample_out, g->nw_pick.p, (size_t)k * 4, cudaMemcpyDeviceToHost));
+    tau_out[0] = t4[0];
+    tau_out[1] = t4[1];
+    return CC_OK;
+}
+
+int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
+                              const uint64_t *tau, const cc_opts *opts, cc_wout *out)
+{
+    if (!g || !opts || !out || !tau || !g->has_beta) return CC_ERR_ARG;
+    if (tau[0] == 0 || tau[1] == 0) return CC_ERR_ARG;
+    const bool hyb = opts->want_hybrid != 0;
+    if (hyb && (opts->eps_num == 0 || opts->eps_num > opts->eps_den)) return CC_ERR_ARG;
+    if ((opts->roundtrip != 0) != g->directed) return CC_ERR_ARG;
+    RC(validate_sample(g, sample, k));
+    reset_timing(g);
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const int64_t n = g->n;
+    RC(g->sidx.ensure(n * 4));
+    RC(g->sum2.ensure(n * 16));
+    RC(g->pivot.ensure(n * 4));
+    RC(g->delta.ensure(n * 4));
+    RC(g->dcc.ensure((size_t)k * k * 4));
+    RC(g->Ssamp.ensure((size_t)k * 8));
+    RC(g->sources.ensure((size_t)k * 4));
+    RC(g->ctl.ensure(sizeof(Ctl)));
+    RC(g->nw_tau.ensure(32));
+    RC(g->nw_mu.ensure((size_t)k * 8));
+    RC(g->nw_bsrc.ensure((size_t)k * 4));
+    RC(g->nw_msum.ensure(16));
+    RC(g->nw_wsum.ensure((size_t)n * 8));
+    RC(g->nw_S.ensure((size_t)k * 8));
+    CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->nw_tau.p, tau, 16, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(g->nw_msum.p, 0, 16, st));
+    CK(cudaMemsetAsync(g->nw_wsum.p, 0, (size_t)n * 8, st));
+    CK(cudaMemsetAsync(g->nw_S.p, 0, (size_t)k * 8, st));
+    run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
+    run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
+    run_nw_mu(k, g->sources.as<int32_t>(), g->beta.as<uint32_t>(), g->nw_tau.as<uint64_t>(),
+              g->nw_bsrc.as<uint32_t>(), g->nw_mu.as<uint64_t>(),
+              g->nw_msum.as<unsigned long long>(), st);
+    g->call_kernels += 3;
+    NwJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = n;
+    j.k = k;
+    j.beta = g->beta.as<uint32_t>();
+    j.mu = g->nw_mu.as<uint64_t>();
+    j.bsrc = g->nw_bsrc.as<uint32_t>();
+    j.sidx = g->sidx.as<int32_t>();
+    j.wsum = g->nw_wsum.as<uint64_t>();
+    j.S = g->nw_S.as<unsigned long long>();
+    RC(chunked_pass1(g, k, st, &j));  // binds the distance rows it allocates
+    j.distF = g->distF.as<uint32_t>();
+    j.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+    uint64_t ms[2] = {0, 0};
+    CK(cudaMemcpyAsync(ms, g->nw_msum.p, 16, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ms[1]) return CC_ERR_ARG;  // a sampled node of weight 0 has probability 0
+    const int64_t D = g->D1;
+    // Every sum below stays in 64 bits: S_beta, the tails and the H and HC
+    // parts are at most B * D, the adjusted-weight sums at most ms[0] * D.
+    if ((unsigned __int128)g->beta_total * (uint64_t)D >= ((unsigned __int128)1 << 63) ||
+        (unsigned __int128)ms[0] * (uint64_t)D >= ((unsigned __int128)1 << 64))
+        return CC_ERR_TOO_LARGE;
+    if (hyb) {
+        if ((double)(D + 2) * k * 8.0 > (double)kMaxHistBytes) return CC_ERR_TOO_LARGE;
+        RC(g->nw_hist.ensure((size_t)(D + 1) * k * 8));
+        RC(g->nw_TS.ensure((size_t)(D + 2) * k * 8));
+        RC(g->nw_lc.ensure((size_t)n * 16));
+        CK(cudaMemsetAsync(g->nw_hist.p, 0, (size_t)(D + 1) * k * 8, st));
+        CK(cudaMemsetAsync(g->nw_lc.p, 0, (size_t)n * 16, st));
+        j.pivot = g->pivot.as<int32_t>();
+        j.delta = g->delta.as<uint32_t>();
+        j.dcc = g->dcc.as<uint32_t>();
+        j.a = opts->eps_num;
+        j.b = opts->eps_den;
+        j.hist = g->nw_hist.as<unsigned long long>();
+        j.lc = g->nw_lc.as<uint64_t>();
+        const int cw = g->cw;
+        j.ld = cw;
+        const int32_t *src = g->sources.as<int32_t>();
+        for (int base = 0; base < k; base += cw) {
+            const int kc = std::min(cw, k - base);
+            RC(run_chunk(g, src + base, kc, cw, st));
+            for (int s = 0; s < kc; s += 32) {
+                j.base = base + s;
+                j.sub = s;
+                j.kc = std::min(32, kc - s);
+                run_nw_reduce2(j, D, st);
+                g->call_kernels += 1;
+            }
+        }
+        run_nw_tail(g->nw_hist.as<unsigned long long>(), D, k, g->nw_TS.as<uint64_t>(), st);
+        g->call_kernels += 1;
+    }
+    const bool dev_out = opts->device_outputs != 0;
+    NwFinal f;
+    std::memset(&f, 0, sizeof(f));
+    f.n = n;
+    f.D = D;
+    f.k = k;
+    f.hybrid = hyb;
+    f.a = opts->eps_num;
+    f.b = opts->eps_den;
+    f.B = g->beta_total;
+    f.tau = g->nw_tau.as<uint64_t>();
+    f.sidx = g->sidx.as<int32_t>();
+    f.pivot = g->pivot.as<int32_t>();
+    f.delta = g->delta.as<uint32_t>();
+    f.beta = g->beta.as<uint32_t>();
+    f.S = g->nw_S.as<unsigned long long>();
+    f.wsum = g->nw_wsum.as<uint64_t>();
+    f.lc = hyb ? g->nw_lc.as<uint64_t>() : nullptr;
+    f.TS = hyb ? g->nw_TS.as<uint64_t>() : nullptr;
+    if (dev_out) {
+        for (int e = 0; e < 2; ++e) {
+            f.s_hat[e] = out->s_hat[e];
+            f.clo[e] = out->closeness[e];
+        }
+    } else {
+        RC(g->nw_out.ensure((size_t)n * 8 * 4));
+        double *stage = g->nw_out.as<double>();
+        for (int e = 0; e < 2; ++e) {
+            f.s_hat[e] = out->s_hat[e] ? stage + (size_t)(2 * e) * n : nullptr;
+            f.clo[e] = out->closeness[e] ? stage + (size_t)(2 * e + 1) * n : nullptr;
+        }
+    }
+    run_nw_finalize(f, st);
+    g->call_kernels += 1;
+    CK(cudaGetLastError());
+    const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (out->S_sampled)
+        CK(cudaMemcpyAsync(out->S_sampled, g->nw_S.p, (size_t)k * 8, kind, st));
+    if (!dev_out) {
+        for (int e = 0; e < (hyb ? 2 : 1); ++e) {
+            if (out->s_hat[e])
+                CK(cudaMemcpyAsync(out->s_hat[e], f.s_hat[e], (size_t)n * 8, kind, st));
+            if (out->closeness[e])
+                CK(cudaMemcpyAsync(out->closeness[e], f.clo[e], (size_t)n * 8, kind, st));
+        }
+    }
     CK(cudaStreamSynchronize(st));
     return CC_OK;
 }

@@ -169,6 +169,16 @@ int graph_view(cc_graph_t g, GraphView *v);
 // cc_set_tuning) for W words per node: with one word a top-down push costs
 // about as much as a gathered word, with more the atomic pushes cost more.
 inline int default_alpha(int W) { return W == 1 ? 6 : 14; }
+
+// Output number c of the splitmix64 stream `seed` (Steele, Lea and Flood
+// 2014): the counter-based generator of the samplers.
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 // Server slots: an empty handle whose workspace persists, pointed at the
 // resident CSR of another handle per request.
 cc_graph_t graph_new_empty();

@@ -561,6 +561,18 @@ int radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bits, uint64_t *tk
 
 }  // namespace
 
+int device_scan_u64(const uint64_t *in, uint64_t *out, int64_t n, uint64_t *total,
+                    cudaStream_t st)
+{
+    return scan_u64(in, out, n, total, st);
+}
+
+int device_radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bits, uint64_t *tk,
+                      uint32_t *tv, cudaStream_t st, bool *in_tmp)
+{
+    return radix_sort(keys, vals, n, bits, tk, tv, st, in_tmp);
+}
+
 // Undirected graph to CSR on the device (see the top of this file).  On
 // success the device buffers rp / col / w (w only when lengths are given)
 // are owned by the caller (cudaFree), rp_host and old_id hold host copies.

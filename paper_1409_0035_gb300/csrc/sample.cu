@@ -21,14 +21,6 @@ namespace {
 constexpr int kCap = 8192;        // candidate capacity (power of two)
 constexpr int kSortThreads = 1024;
 
-__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t c)
-{
-    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 struct Cand {
     uint64_t key;
     uint32_t v;

@@ -19,5 +19,6 @@ from .graphs import (  # noqa: F401
     cycle_edges,
     complete_edges,
     random_weights,
+    pareto_node_weights,
     edge_lengths_to_weights,
 )

@@ -161,6 +161,16 @@ def random_weights(m: int, lo: int, hi: int, seed=1) -> np.ndarray:
         np.uint32)
 
 
+def pareto_node_weights(n: int, alpha: float = 1.2, scale: int = 10, cap: int = 10**6,
+                        seed=1) -> np.ndarray:
+    """n uint32 node weights min(cap, floor(scale * x) + 1), x Pareto (Lomax)
+    of shape alpha from uniform_at(seed, v): a few heavy nodes among many
+    light ones."""
+    u = uniform_at(seed, np.arange(n, dtype=np.uint64))
+    x = (1.0 - u) ** (-1.0 / alpha) - 1.0
+    return np.minimum(np.floor(scale * x) + 1, cap).astype(np.uint32)
+
+
 def path_edges(n: int):
     """Path 0 - 1 - ... - (n-1)."""
     a = np.arange(n - 1, dtype=np.uint32)
