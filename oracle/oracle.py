@@ -13,7 +13,10 @@ Pieces:
     table and the estimators of section 2 (eqs. (1), (3), (4));
   * node-weighted closeness (section 5) in plain Python integers: the
     threshold tau, the exact-size weighted sample and the sampling and
-    hybrid estimates of S_beta from a distance table.
+    hybrid estimates of S_beta from a distance table;
+  * outbound / inbound estimates of general directed graphs (section 6.2):
+    per node the bottom-k sample of its reachability set by rank, from an
+    all-pairs table.
 """
 from __future__ import annotations
 
@@ -538,3 +541,55 @@ def exact_weighted_S(table_all: np.ndarray, beta):
     T = np.asarray(table_all, dtype=np.int64)
     bvec = np.asarray([int(x) for x in beta], dtype=np.int64)
     return [int((T[v] * bvec).sum()) for v in range(T.shape[0])]
+
+
+# --------------------------------------------------------------------------
+# Outbound / inbound estimates for general directed graphs (section 6.2,
+# Algorithm 3)
+# --------------------------------------------------------------------------
+#
+# For node v, R(v) = the nodes u != v that v reaches (outbound; inbound: that
+# reach v) and S(v) = the sum of d(v, u) over them.  With the nodes in one
+# random order (rank), v's sample is the k nodes of R(v) of smallest rank;
+# the estimates are the average distance to the sample and a bottom-k
+# estimate of |R(v)| from the rank position of the k-th sample.
+
+
+def reach_from_table(table_all: np.ndarray, order, k: int, inbound=False):
+    """Per node, from the n x n distance table (row u: d(u, .); unreachable
+    = INF): count = min(k, |R(v)|), distsum = sum of the distances to the
+    sample, T = the position (1-based, among the nodes other than v) of the
+    k-th sample in the order, 0 when count < k; avg = distsum / count (0
+    when count = 0), R_hat = count when count < k, else
+    1 + (k - 1)(n - 2) / (T - 1).  Returns a dict of arrays."""
+    D = np.asarray(table_all, dtype=np.int64)
+    n = D.shape[0]
+    order = [int(x) for x in order]
+    pos = {u: p for p, u in enumerate(order)}          # 0-based rank position
+    count = np.zeros(n, np.int32)
+    distsum = np.zeros(n, np.uint64)
+    T = np.zeros(n, np.int64)
+    avg = np.zeros(n)
+    R_hat = np.zeros(n)
+    for v in range(n):
+        dist = D[:, v] if inbound else D[v, :]
+        reach = [u for u in order if u != v and dist[u] != INF]   # rank order
+        sample = reach[:k]
+        count[v] = len(sample)
+        distsum[v] = sum(int(dist[u]) for u in sample)
+        if count[v]:
+            avg[v] = int(distsum[v]) / int(count[v])
+        if count[v] < k:
+            R_hat[v] = count[v]
+        else:
+            t = pos[sample[-1]] + 1                         # 1-based position
+            T[v] = t - 1 if pos[v] < pos[sample[-1]] else t  # not counting v
+            # k = 1: the numerator (k - 1)(n - 2) is 0 and R_hat = 1
+            R_hat[v] = 1.0 if k == 1 else 1.0 + float((k - 1) * (n - 2)) / float(T[v] - 1)
+    return dict(count=count, distsum=distsum, T=T, avg=avg, R_hat=R_hat)
+
+
+def all_pairs(g: Graph) -> np.ndarray:
+    """n x n table of d(u, v) (row u), INF where v is unreachable: one BFS
+    (Dijkstra with arc lengths) per node."""
+    return np.stack([sssp(g, u) for u in range(g.n)])

@@ -1,0 +1,163 @@
+"""Pins of the oracle's outbound / inbound estimates for general directed
+graphs (section 6.2, Algorithm 3): the average distance to a bottom-k sample
+of each node's reachability set and the bottom-k estimate of its size.
+
+The pins: closed forms on a directed path and a cycle; over every order of
+a small graph the average distance is exactly unbiased and the size estimate
+has the expectation 1 + (n-2) r / (n-1) derived by hand (r = |R(v)| >= k;
+below k the count is exact); inbound is outbound on the reversed graph; and
+the paper's own procedure -- pruned searches in rank order on the reversed
+graph, with its mark rule for T -- computed independently gives the same
+counts, sums and positions.
+"""
+from collections import deque
+from fractions import Fraction
+from itertools import permutations
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as O
+
+
+def digraph(n, arcs):
+    s = np.array([a for a, _ in arcs], np.uint32)
+    d = np.array([b for _, b in arcs], np.uint32)
+    return O.csr_from_edges(n, s, d, directed=True, keep_component=False)
+
+
+def small_dag():
+    # 7 nodes: reach sets of different sizes, two paths of unequal length
+    return digraph(7, [(0, 1), (1, 2), (2, 3), (0, 4), (4, 3), (3, 5), (6, 5), (5, 6),
+                       (1, 4)])
+
+
+@pytest.mark.parametrize("k", [3, 8, 40])
+def test_directed_path_closed_form(k):
+    n = 12
+    g = digraph(n, [(i, i + 1) for i in range(n - 1)])
+    r = O.reach_from_table(O.all_pairs(g), O.sample_order(n, 4), k)
+    for v in range(n):
+        reach = n - 1 - v
+        if reach <= k:  # every reachable node sampled: exact sums
+            assert r["count"][v] == reach
+            assert int(r["distsum"][v]) == reach * (reach + 1) // 2
+            if reach < k:  # fewer than k: the count is the size
+                assert r["R_hat"][v] == reach
+        else:
+            assert r["count"][v] == k
+
+
+def test_cycle_with_k_all_others_is_exact():
+    # k = n - 1 on a directed cycle: every node reaches all n-1 others at
+    # distances 1..n-1 (mean n/2), and the k-th sample is the last other
+    # node in the order (T = n - 1), so R_hat = 1 + (n-2)(n-2)/(n-2) = n-1.
+    n = 9
+    g = digraph(n, [(i, (i + 1) % n) for i in range(n)])
+    r = O.reach_from_table(O.all_pairs(g), O.sample_order(n, 1), n - 1)
+    assert (r["T"] == n - 1).all()
+    assert np.array_equal(r["R_hat"], np.full(n, n - 1.0))
+    assert np.array_equal(r["avg"], np.full(n, n / 2))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_expectation_over_every_order(k):
+    # Averaged over all 7! orders: avg is the exact mean distance over R(v)
+    # (the sample is a uniform k-subset of R(v)); R_hat has expectation
+    # 1 + (n-2) r/(n-1), from E[(k-1)/(T-1)] = r/(n-1) for the position T
+    # of the k-th of r marked nodes among the n-1 others.
+    g = small_dag()
+    n = g.n
+    D = O.all_pairs(g)
+    acc_avg = [Fraction(0)] * n
+    acc_R = [Fraction(0)] * n
+    perms = list(permutations(range(n)))
+    for order in perms:
+        r = O.reach_from_table(D, order, k)
+        for v in range(n):
+            if r["count"][v] == k:
+                acc_avg[v] += Fraction(int(r["distsum"][v]), k)
+                acc_R[v] += 1 + Fraction((k - 1) * (n - 2), int(r["T"][v]) - 1)
+            else:
+                acc_R[v] += int(r["count"][v])
+    for v in range(n):
+        reach = [u for u in range(n) if u != v and D[v, u] != O.INF]
+        rr = len(reach)
+        if rr >= k:
+            assert acc_avg[v] / len(perms) == Fraction(sum(int(D[v, u]) for u in reach), rr)
+            assert acc_R[v] / len(perms) == 1 + Fraction((n - 2) * rr, n - 1)
+        else:
+            assert acc_R[v] / len(perms) == rr
+
+
+def test_inbound_is_outbound_of_the_reversed_graph():
+    n, s, d = synth.rmat_edges(7, 4, seed=5)
+    g = O.csr_from_edges(n, s, d, directed=True, keep_component=False)
+    gr = O.csr_from_edges(n, d, s, directed=True, keep_component=False)
+    order = O.sample_order(g.n, 3)
+    a = O.reach_from_table(O.all_pairs(g), order, 5, inbound=True)
+    b = O.reach_from_table(O.all_pairs(gr), order, 5)
+    for key in ("count", "distsum", "T"):
+        assert np.array_equal(a[key], b[key])
+
+
+def _pruned_searches(g, order, k):
+    """Algorithm 3's procedure: BFS from each node in rank order on the
+    reversed graph, pruned at saturated nodes, with the mark rule for T.
+    The pruning counts the searches that reached a node including its own
+    and prunes at k + 1: then a node x it stops at holds k + 1 nodes of
+    smaller rank than u among x and its reachability set, and every node
+    reaching x already has k of them other than itself."""
+    n = g.n
+    rp, col = g.rrow_ptr, g.rcol
+    count = [0] * n
+    seen = [0] * n  # searches that reached the node, its own included
+    dsum = [0] * n
+    T = [0] * n
+    mark = [False] * n
+    for t, u in enumerate(order, start=1):
+        mark[u] = True
+        dist = {u: 0}
+        q = deque([u])
+        while q:
+            v = q.popleft()
+            if seen[v] == k + 1:
+                continue  # pruned: not scanned further
+            seen[v] += 1
+            if v != u and count[v] < k:
+                dsum[v] += dist[v]
+                count[v] += 1
+                if count[v] == k:
+                    T[v] = t - 1 if mark[v] else t
+            for e in range(rp[v], rp[v + 1]):
+                w = int(col[e])
+                if w not in dist:
+                    dist[w] = dist[v] + 1
+                    q.append(w)
+    return count, dsum, T
+
+
+def test_pruning_on_other_nodes_alone_can_lose_a_sample():
+    # The procedure as printed prunes at a node x once k nodes other than x
+    # reached it.  On this graph with k = 1: 0 <-> 1, 2 -> 1, order 1, 0,
+    # 2 ...: the search from 1 reaches 0 (0's sample {1}) and 2; the search
+    # from 0 is pruned at 0 itself (full), so 1 -- whose reachability set
+    # is {0} -- never receives 0.  The definition gives 1 the sample {0}.
+    g = digraph(3, [(0, 1), (1, 0), (2, 1)])
+    r = O.reach_from_table(O.all_pairs(g), [1, 0, 2], 1)
+    assert r["count"].tolist() == [1, 1, 1]
+    count, _, _ = _pruned_searches(g, [1, 0, 2], 1)
+    assert count == [1, 1, 1]
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_definition_matches_the_pruned_search(k):
+    n, s, d = synth.rmat_edges(7, 3, seed=9)
+    g = O.csr_from_edges(n, s, d, directed=True, keep_component=False)
+    order = O.sample_order(g.n, 2)
+    r = O.reach_from_table(O.all_pairs(g), order, k)
+    count, dsum, T = _pruned_searches(g, [int(x) for x in order], k)
+    assert r["count"].tolist() == count
+    assert [int(x) for x in r["distsum"]] == dsum
+    assert r["T"].tolist() == T
