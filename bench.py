@@ -54,7 +54,7 @@ def parse():
                     help="serve workload: graph pool (paper: R-MAT to scale 22, grids to 4096^2)")
     ap.add_argument("--workload", default="rmat20",
                     choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive",
-                             "nodeweighted"],
+                             "nodeweighted", "reach"],
                     help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
@@ -622,6 +622,30 @@ def run_extra(args):
                             f"edge factor {EF}, seed {GSEED}, LCC", "n": nn, "m": m, "k": K,
                             "node_weights": "Pareto(1.2) x 10 + 1, capped at 10^6",
                             "total_weight": int(beta.astype(np.uint64).sum())})
+        cc.cc_graph_free(g)
+    elif args.workload == "reach":
+        # Outbound and inbound estimates (section 6.2) on a directed R-MAT
+        # graph kept whole (not strongly connected): every node's bottom-k
+        # reachability sample, k = 64.
+        kr = 64
+        n, s, d = synth.rmat_edges(SCALE, EF, seed=GSEED)
+        g, _ = cc.cc_graph_from_edges(n, s, d, directed=True, keep_component=False)
+        nn, arcs, _, _ = cc.cc_graph_info(g)
+        res = {}
+        for name, inb in (("outbound", False), ("inbound", True)):
+            t = _time_steps(lambda: cc.cc_reach_estimate(g, kr, SSEED, inb), args.steps,
+                            args.warmup, flush)
+            r = cc.cc_reach_estimate(g, kr, SSEED, inb)
+            lv = cc.cc_last_pass_stats(g)["levels"]
+            res[name] = dict(ms=t, levels_total=int(lv), full_samples=int((r["count"] == kr).sum()),
+                             empty=int((r["count"] == 0).sum()))
+        tot = res["outbound"]["ms"] + res["inbound"]["ms"]
+        line.update(metric="node samples/s", unit="nodes/s", value=2 * nn / (tot / 1e3),
+                    ms_per_step=tot, outbound=res["outbound"], inbound=res["inbound"],
+                    note="value = 2 n / (outbound + inbound time); host outputs",
+                    config={"workload": "reach", "graph": f"directed R-MAT scale {SCALE}, edge "
+                            f"factor {EF}, seed {GSEED}, all nodes", "n": nn, "arcs": arcs,
+                            "k": kr})
         cc.cc_graph_free(g)
     elif args.workload == "batch64":
         specs = batch64_graphs()

@@ -258,6 +258,33 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
                               const uint64_t *tau, const cc_opts *opts, cc_wout *out);
 
 /*
+ * cc_reach_estimate -- outbound / inbound estimates of general (not
+ * necessarily strongly connected) directed graphs (section 6.2, Algorithm
+ * 3).  With the nodes in a seeded random order (increasing splitmix64
+ * output number v of stream `seed`, ties by id -- the keys of
+ * cc_sample_choose), node v's sample is the k nodes of smallest rank among
+ * R(v), the nodes other than v that v reaches (inbound != 0: that reach v).
+ *   avg_dist  double[n]: average distance to the sample (0 when R(v) is
+ *             empty) -- the estimate of S(v)/|R(v)|, whose inverse is the
+ *             outbound (inbound) centrality
+ *   reach     double[n]: |R(v)| when it is below k, else the bottom-k
+ *             estimate 1 + (k-1)(n-2)/(T(v)-1) (1 when k = 1)
+ *   count     int32[n]: samples taken, min(k, |R(v)|)
+ *   dist_sum  uint64[n]: sum of the sample's distances
+ *   T         int64[n]: rank position (1-based, not counting v) of the k-th
+ *             sample; 0 when count < k
+ * Outputs are host arrays, any may be NULL.  Runs one cooperative launch
+ * over the order in groups of up to 256 sources: bit-packed searches on G^T
+ * (outbound) or G (inbound) that skip nodes already holding k + 1 nodes of
+ * smaller rank (themselves included).  Unit lengths only.  Errors:
+ * CC_ERR_ARG (k < 1, a graph with arc lengths), CC_ERR_OOM, CC_ERR_CUDA,
+ * CC_ERR_TIMEOUT (a bounded device-side wait ran out).
+ */
+int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, void *stream,
+                      double *avg_dist, double *reach, int32_t *count, uint64_t *dist_sum,
+                      int64_t *T);
+
+/*
  * cc_exact -- exact S(v) and B^-1(v) = (n-1)/S(v) for every node (eq. (1))
  * by traversals from every node, packed 64 per word.  Meant for small
  * graphs (the cost is n traversals).  closeness double[n], S uint64[n] (host,

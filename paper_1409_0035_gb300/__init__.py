@@ -39,7 +39,7 @@ EXPORTS = (
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
     "cc_estimate_adaptive", "cc_graph_set_node_weights", "cc_sample_varopt",
-    "cc_estimate_node_weighted",
+    "cc_estimate_node_weighted", "cc_reach_estimate",
 )
 
 PHASES = ("init", "td_queue", "td_push", "td_final", "bu_rebuild", "bu_light",
@@ -99,6 +99,7 @@ def lib():
         L.cc_graph_set_node_weights.argtypes = [P, P]
         L.cc_sample_varopt.argtypes = [P, i32, u64, P, P]
         L.cc_estimate_node_weighted.argtypes = [P, P, i32, P, P, P]
+        L.cc_reach_estimate.argtypes = [P, i32, u64, i32, P, P, P, P, P, P]
         L.cc_sampling_sums_single.argtypes = [P, P, i32, P, P]
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_pass_phases.argtypes = [P, P]
@@ -314,6 +315,20 @@ def cc_estimate_node_weighted(g, sample, tau, opts=None, out=None):
     o.S_sampled = _p(res["S_sampled"])
     _chk(lib().cc_estimate_node_weighted(g, _p(sample), k, _p(t), ctypes.byref(opts),
                                          ctypes.byref(o)), "cc_estimate_node_weighted")
+    return res
+
+
+def cc_reach_estimate(g, k, seed, inbound=False, stream=None):
+    """Outbound (inbound) estimates of section 6.2: dict of host arrays avg
+    (average distance to each node's bottom-k reachability sample), R_hat
+    (size of the reachability set), count, distsum, T."""
+    n = cc_graph_info(g)[0]
+    res = dict(avg=np.empty(n), R_hat=np.empty(n), count=np.empty(n, np.int32),
+               distsum=np.empty(n, np.uint64), T=np.empty(n, np.int64))
+    _chk(lib().cc_reach_estimate(g, int(k), ctypes.c_uint64(seed & (2**64 - 1)),
+                                 int(bool(inbound)), stream, _p(res["avg"]), _p(res["R_hat"]),
+                                 _p(res["count"]), _p(res["distsum"]), _p(res["T"])),
+         "cc_reach_estimate")
     return res
 
 

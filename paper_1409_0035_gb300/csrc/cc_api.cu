@@ -11,6 +11,7 @@
 #include "estimate.h"
 #include "graph_gpu.h"
 #include "nodew.h"
+#include "reach.h"
 #include "sssp.h"
 
 using namespace ccg;
@@ -97,6 +98,9 @@ struct cc_graph {
         nw_bsrc, nw_msum, nw_wsum, nw_S, nw_hist, nw_TS, nw_lc, nw_out;
     uint64_t beta_total = 0;
     bool has_beta = false;
+    // outbound / inbound reachability samples: order, per-node state, queues
+    DevBuf rc_order, rc_rank, rc_cnt, rc_extra, rc_dsum, rc_T, rc_qstamp, rc_vis, rc_F, rc_nxt,
+        rc_lev, rc_Q0, rc_Q1, rc_TL, rc_out;
     bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t D1 = 0;        // levels (largest distance) of the last first pass
     int cw = 32;           // sources per chunk of the last chunked first pass
@@ -454,7 +458,9 @@ void free_graph(cc_graph *g)
                      &g->beta, &g->nw_keys, &g->nw_tk, &g->nw_vals, &g->nw_tv, &g->nw_pre,
                      &g->nw_flags, &g->nw_tau, &g->nw_pick, &g->nw_mu, &g->nw_bsrc,
                      &g->nw_msum, &g->nw_wsum, &g->nw_S, &g->nw_hist, &g->nw_TS, &g->nw_lc,
-                     &g->nw_out};
+                     &g->nw_out, &g->rc_order, &g->rc_rank, &g->rc_cnt, &g->rc_extra,
+                     &g->rc_dsum, &g->rc_T, &g->rc_qstamp, &g->rc_vis, &g->rc_F, &g->rc_nxt,
+                     &g->rc_lev, &g->rc_Q0, &g->rc_Q1, &g->rc_TL, &g->rc_out};
     for (DevBuf *b : all) b->release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -994,7 +1000,9 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                      &g->beta, &g->nw_keys, &g->nw_tk, &g->nw_vals, &g->nw_tv, &g->nw_pre,
                      &g->nw_flags, &g->nw_tau, &g->nw_pick, &g->nw_mu, &g->nw_bsrc,
                      &g->nw_msum, &g->nw_wsum, &g->nw_S, &g->nw_hist, &g->nw_TS, &g->nw_lc,
-                     &g->nw_out};
+                     &g->nw_out, &g->rc_order, &g->rc_rank, &g->rc_cnt, &g->rc_extra,
+                     &g->rc_dsum, &g->rc_T, &g->rc_qstamp, &g->rc_vis, &g->rc_F, &g->rc_nxt,
+                     &g->rc_lev, &g->rc_Q0, &g->rc_Q1, &g->rc_TL, &g->rc_out};
     size_t t = 0;
     for (const DevBuf *b : ws) t += b->cap;
     return t;
@@ -1587,6 +1595,100 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
                 CK(cudaMemcpyAsync(out->closeness[e], f.clo[e], (size_t)n * 8, kind, st));
         }
     }
+    CK(cudaStreamSynchronize(st));
+    return CC_OK;
+}
+
+int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, void *stream,
+                      double *avg_dist, double *reach, int32_t *count, uint64_t *dist_sum,
+                      int64_t *T)
+{
+    if (!g || k < 1 || g->weighted) return CC_ERR_ARG;
+    RC(device_ok());
+    reset_timing(g);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)g->n;
+    const int W = (int)std::min<int64_t>(kReachMaxW, (g->n + 63) / 64);
+    const DevCSR &sg = (g->directed && !inbound) ? g->rv : g->fw;
+    RC(g->nw_keys.ensure(n * 8));
+    RC(g->nw_tk.ensure(n * 8));
+    RC(g->nw_vals.ensure(n * 4));
+    RC(g->nw_tv.ensure(n * 4));
+    RC(g->rc_order.ensure(n * 4));
+    RC(g->rc_rank.ensure(n * 4));
+    RC(g->rc_cnt.ensure(n * 4));
+    RC(g->rc_extra.ensure(n));
+    RC(g->rc_dsum.ensure(n * 8));
+    RC(g->rc_T.ensure(n * 8));
+    RC(g->rc_qstamp.ensure(n * 4));
+    RC(g->rc_vis.ensure(n * W * 8));
+    RC(g->rc_F.ensure(n * W * 8));
+    RC(g->rc_nxt.ensure(n * W * 8));
+    RC(g->rc_lev.ensure(n * 64 * W * 4));
+    RC(g->rc_Q0.ensure(n * 4));
+    RC(g->rc_Q1.ensure(n * 4));
+    RC(g->rc_TL.ensure(n * 4));
+    RC(g->rc_out.ensure(n * 16));
+    RC(g->ctl.ensure(sizeof(Ctl)));
+    CK(cudaMemsetAsync(g->rc_cnt.p, 0, n * 4, st));
+    CK(cudaMemsetAsync(g->rc_extra.p, 0, n, st));
+    CK(cudaMemsetAsync(g->rc_dsum.p, 0, n * 8, st));
+    CK(cudaMemsetAsync(g->rc_T.p, 0, n * 8, st));
+    CK(cudaMemsetAsync(g->rc_qstamp.p, 0, n * 4, st));
+    CK(cudaMemsetAsync(g->rc_vis.p, 0, n * W * 8, st));
+    CK(cudaMemsetAsync(g->rc_F.p, 0, n * W * 8, st));
+    CK(cudaMemsetAsync(g->rc_nxt.p, 0, n * W * 8, st));
+    RC(reach_order(g->n, seed, g->nw_keys.as<uint64_t>(), g->nw_vals.as<uint32_t>(),
+                   g->nw_tk.as<uint64_t>(), g->nw_tv.as<uint32_t>(), g->rc_order.as<int32_t>(),
+                   g->rc_rank.as<int32_t>(), st));
+    ReachJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.n = g->n;
+    j.k = k;
+    j.W = W;
+    j.rp = sg.rp.as<int64_t>();
+    j.col = sg.col.as<int32_t>();
+    j.order = g->rc_order.as<int32_t>();
+    j.rank = g->rc_rank.as<int32_t>();
+    j.cnt = g->rc_cnt.as<int32_t>();
+    j.extra = g->rc_extra.as<uint8_t>();
+    j.dsum = g->rc_dsum.as<uint64_t>();
+    j.T = g->rc_T.as<int64_t>();
+    j.qstamp = g->rc_qstamp.as<uint32_t>();
+    j.vis = g->rc_vis.as<uint64_t>();
+    j.F = g->rc_F.as<uint64_t>();
+    j.nxt = g->rc_nxt.as<uint64_t>();
+    j.lev = g->rc_lev.as<uint32_t>();
+    j.Q[0] = g->rc_Q0.as<int32_t>();
+    j.Q[1] = g->rc_Q1.as<int32_t>();
+    j.TL = g->rc_TL.as<int32_t>();
+    j.ctl = g->ctl.as<Ctl>();
+    j.timeout_ns = kTimeoutNs;
+    if (!g->ev0) {
+        CK(cudaEventCreate(&g->ev0));
+        CK(cudaEventCreate(&g->ev1));
+    }
+    CK(cudaEventRecord(g->ev0, st));
+    ReachStats rs{};
+    RC(reach_run(j, st, &rs));
+    CK(cudaEventRecord(g->ev1, st));
+    CK(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    g->call_launches = 1;
+    g->call_kernels += 1;
+    g->call_ms = ms;
+    g->last.levels = (int)rs.levels;
+    double *stage = g->rc_out.as<double>();
+    reach_finalize(g->n, k, g->rc_cnt.as<int32_t>(), g->rc_dsum.as<uint64_t>(),
+                   g->rc_T.as<int64_t>(), stage, stage + n, st);
+    g->call_kernels += 1;
+    CK(cudaGetLastError());
+    if (avg_dist) CK(cudaMemcpyAsync(avg_dist, stage, n * 8, cudaMemcpyDeviceToHost, st));
+    if (reach) CK(cudaMemcpyAsync(reach, stage + n, n * 8, cudaMemcpyDeviceToHost, st));
+    if (count) CK(cudaMemcpyAsync(count, g->rc_cnt.p, n * 4, cudaMemcpyDeviceToHost, st));
+    if (dist_sum) CK(cudaMemcpyAsync(dist_sum, g->rc_dsum.p, n * 8, cudaMemcpyDeviceToHost, st));
+    if (T) CK(cudaMemcpyAsync(T, g->rc_T.p, n * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return CC_OK;
 }

@@ -369,14 +369,21 @@ int nw_threshold(const uint32_t *beta, int64_t n, int k, uint64_t *keys, uint32_
     return CC_OK;
 }
 
+int random_order(int64_t n, uint64_t seed, uint64_t *keys, uint32_t *vals, uint64_t *tk,
+                 uint32_t *tv, bool *in_tmp, cudaStream_t st)
+{
+    k_order_keys<<<grid_for(n), kT, 0, st>>>(n, seed, keys, vals);
+    NW_CK(cudaGetLastError());
+    return device_radix_sort(keys, vals, n, 64, tk, tv, st, in_tmp);
+}
+
 int nw_draw(const uint32_t *beta, int64_t n, int k, uint64_t seed, const uint64_t *tau,
             uint64_t *keys, uint32_t *vals, uint64_t *tk, uint32_t *tv, uint64_t *pre,
             uint64_t *flags, int32_t *out, int64_t *count, cudaStream_t st)
 {
     const int g = grid_for(n);
-    k_order_keys<<<g, kT, 0, st>>>(n, seed, keys, vals);
     bool in_tmp = false;
-    NW_RC(device_radix_sort(keys, vals, n, 64, tk, tv, st, &in_tmp));
+    NW_RC(random_order(n, seed, keys, vals, tk, tv, &in_tmp, st));
     const uint32_t *order = in_tmp ? tv : vals;
     uint64_t *pos = in_tmp ? keys : tk;  // the key buffer not holding the result
     k_lengths<<<g, kT, 0, st>>>(order, beta, tau, n, pre);

@@ -20,6 +20,12 @@ int nw_total(const uint32_t *beta, int64_t n, uint64_t *dsum, uint64_t *total,
 int nw_threshold(const uint32_t *beta, int64_t n, int k, uint64_t *keys, uint32_t *vals,
                  uint64_t *tk, uint32_t *tv, uint64_t *pre, uint64_t *tau4, cudaStream_t st);
 
+// The nodes in increasing (splitmix64 output v of stream `seed`, v): a
+// seeded random order, left in vals (in_tmp false) or tv (in_tmp true).
+// Scratch: keys, tk (n uint64).  Synchronises the stream.
+int random_order(int64_t n, uint64_t seed, uint64_t *keys, uint32_t *vals, uint64_t *tk,
+                 uint32_t *tv, bool *in_tmp, cudaStream_t st);
+
 // Systematic draw of the sample along the splitmix64 order of `seed` given tau
 // (device): out[k] (device) receives the sampled nodes in that order; *count
 // the number drawn (k by construction; entries past k are not written).  Scratch as nw_threshold, plus
