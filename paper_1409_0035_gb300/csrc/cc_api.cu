@@ -104,6 +104,7 @@ struct cc_graph {
     bool sq = false;       // the current cc_estimate call wants SqErrEst
     int64_t D1 = 0;        // levels (largest distance) of the last first pass
     int cw = 32;           // sources per chunk of the last chunked first pass
+    bool resident = false; // its distance rows are all kept (chunk c at c * n * cw)
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha(W))
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
@@ -629,7 +630,29 @@ int chunk_width(cc_graph *g, int64_t k)
     return cw;
 }
 
-int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_t st)
+// Whether `bytes` of rows per table (two tables for round trips) fit in a
+// third of the device memory that is free or already held by the rows.
+bool rows_fit(cc_graph *g, size_t bytes)
+{
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const double tables = g->directed ? 2.0 : 1.0;
+    const double avail = (double)free_b + (double)g->distF.cap + (double)g->distR.cap;
+    return (double)bytes * tables <= avail / 3.0;
+}
+
+// First element of the rows of the chunk starting at source `base`.
+size_t chunk_offset(const cc_graph *g, int base)
+{
+    return g->resident ? (size_t)(base / g->cw) * (size_t)g->n * g->cw : 0;
+}
+
+// off: first element of the chunk's rows in distF / distR.
+int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_t st,
+              size_t off)
 {
     const int64_t n = g->n;
     if (!g->weighted) {
@@ -642,7 +665,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
             j.k = kc;
             j.sources = d_sources;
             j.red = RED_LEVELS;
-            j.dist_out = (dir ? g->distR : g->distF).as<uint32_t>();
+            j.dist_out = (dir ? g->distR : g->distF).as<uint32_t>() + off;
             j.dist_ld = cw;
             RC(run_pass(g, W, j, st));
             if (g->last.ninc_final != 0) return CC_ERR_DISCONNECTED;
@@ -659,7 +682,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
         j.w = g->weighted ? c.w.as<uint32_t>() : nullptr;
         j.kc = kc;
         j.sources = d_sources;
-        j.dist = (dir ? g->distR : g->distF).as<uint32_t>();
+        j.dist = (dir ? g->distR : g->distF).as<uint32_t>() + off;
         j.mask = g->mask.as<unsigned>();
         j.Q0 = g->Q0.as<int32_t>();
         j.Q1 = g->Q1.as<int32_t>();
@@ -720,8 +743,14 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st, const NwJob *nw = nullptr
     const int W = pow2_words(k);
     const int cw = chunk_width(g, k);
     g->cw = cw;
-    RC(g->distF.ensure((size_t)n * cw * 4));
-    if (g->directed) RC(g->distR.ensure((size_t)n * cw * 4));
+    // Keep every chunk's rows when they fit in a third of the free memory:
+    // the hybrid's second sweep (and each eps of the adaptive hybrid) then
+    // reduces them again instead of repeating the traversals.
+    const int nch = (k + cw - 1) / cw;
+    g->resident = nch == 1 || rows_fit(g, (size_t)n * cw * nch * 4);
+    const size_t rows = (size_t)n * cw * (g->resident ? nch : 1) * 4;
+    RC(g->distF.ensure(rows));
+    if (g->directed) RC(g->distR.ensure(rows));
     RC(g->mask.ensure(n * 4));
     RC(g->Q0.ensure(n * 4));
     RC(g->Q1.ensure(n * 4));
@@ -739,7 +768,10 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st, const NwJob *nw = nullptr
     r.ld = cw;
     for (int base = 0; base < k; base += cw) {
         const int kc = std::min(cw, k - base);
-        RC(run_chunk(g, src + base, kc, cw, st));
+        const size_t off = chunk_offset(g, base);
+        RC(run_chunk(g, src + base, kc, cw, st, off));
+        r.distF = g->distF.as<uint32_t>() + off;
+        r.distR = g->directed ? g->distR.as<uint32_t>() + off : nullptr;
         for (int s = 0; s < kc; s += 32) {  // one reduction per 32 columns
             r.base = base + s;
             r.sub = s;
@@ -748,8 +780,8 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st, const NwJob *nw = nullptr
             g->call_kernels += 1;
             if (nw) {
                 NwJob j = *nw;
-                j.distF = g->distF.as<uint32_t>();
-                j.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+                j.distF = r.distF;
+                j.distR = r.distR;
                 j.base = r.base;
                 j.sub = s;
                 j.kc = r.kc;
@@ -825,7 +857,10 @@ int chunked_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
     r.ld = cw;
     for (int base = 0; base < k; base += cw) {
         const int kc = std::min(cw, k - base);
-        RC(run_chunk(g, src + base, kc, cw, st));
+        const size_t off = chunk_offset(g, base);
+        if (!g->resident) RC(run_chunk(g, src + base, kc, cw, st, off));
+        r.distF = g->distF.as<uint32_t>() + off;
+        r.distR = g->directed ? g->distR.as<uint32_t>() + off : nullptr;
         for (int s = 0; s < kc; s += 32) {
             r.base = base + s;
             r.sub = s;
@@ -1537,7 +1572,10 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
         const int32_t *src = g->sources.as<int32_t>();
         for (int base = 0; base < k; base += cw) {
             const int kc = std::min(cw, k - base);
-            RC(run_chunk(g, src + base, kc, cw, st));
+            const size_t off = chunk_offset(g, base);
+            if (!g->resident) RC(run_chunk(g, src + base, kc, cw, st, off));
+            j.distF = g->distF.as<uint32_t>() + off;
+            j.distR = g->directed ? g->distR.as<uint32_t>() + off : nullptr;
             for (int s = 0; s < kc; s += 32) {
                 j.base = base + s;
                 j.sub = s;
@@ -1732,7 +1770,7 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
         r.ld = cw;
         for (int64_t base = 0; base < n; base += cw) {
             const int kc = (int)std::min<int64_t>(cw, n - base);
-            RC(run_chunk(g, g->sources.as<int32_t>() + base, kc, cw, st));
+            RC(run_chunk(g, g->sources.as<int32_t>() + base, kc, cw, st, 0));
             for (int s = 0; s < kc; s += 32) {
                 r.base = (int)base + s;
                 r.sub = s;
