@@ -426,7 +426,8 @@ int cc_server_free(cc_server_t s);
 
 /* ---- tuning ---------------------------------------------------------------- */
 /* Direction switch of the breadth-first traversal of one graph (0 restores
- * the default: 6 when the sample fits one 64-bit word, else 14): a level
+ * the default: 6 when the sample fits one 64-bit word and the mean degree
+ * is at least 8, else 14): a level
  * runs top-down while (CSR entries of the frontier) * alpha < (CSR entries
  * of the nodes some source has not reached yet), bottom-up otherwise.
  * Results do not depend on it, only the time. */

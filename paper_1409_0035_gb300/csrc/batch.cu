@@ -426,7 +426,7 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         B_CK(cudaMemcpy(p[16], samples[i], (size_t)k * 4, cudaMemcpyHostToDevice));
         j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
         j.timeout_ns = 10ull * 1000 * 1000 * 1000;
-        j.alpha = v.alpha ? v.alpha : default_alpha(W);
+        j.alpha = v.alpha ? v.alpha : default_alpha(W, j.n, j.arcs);
         j.ctl = ctl_jobs + 2 * i;
         J.W = W;
         J.k = k;

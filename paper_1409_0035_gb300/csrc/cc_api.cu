@@ -106,7 +106,7 @@ struct cc_graph {
     int cw = 32;           // sources per chunk of the last chunked first pass
     bool resident = false; // its distance rows are all kept (chunk c at c * n * cw)
     int64_t dist_max = 0;  // largest distance seen by the last estimate
-    int alpha = 0;  // traversal tuning (0: default_alpha(W))
+    int alpha = 0;  // traversal tuning (0: default_alpha)
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
     bool borrowed = false;  // CSR buffers belong to another handle
     int hist_cap = 0;
@@ -295,7 +295,7 @@ BfsJob base_job(cc_graph *g, int W, const DevCSR &push, const DevCSR &pull)
     j.sum2 = g->sum2.as<uint64_t>();
     j.ctl = g->ctl.as<Ctl>();
     j.timeout_ns = kTimeoutNs;
-    j.alpha = g->alpha ? g->alpha : default_alpha(W);
+    j.alpha = g->alpha ? g->alpha : default_alpha(W, j.n, j.arcs);
     j.max_ctas = g->max_ctas;
     return j;
 }

@@ -227,7 +227,7 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
     j.hist_cap = hist_cap;
     j.ctl = ctl;
     j.timeout_ns = 10ull * 1000 * 1000 * 1000;
-    j.alpha = default_alpha(W);
+    j.alpha = default_alpha(W, j.n, j.arcs);
     const int rc = launch_msbfs(W, j, st, nullptr);
     if (rc != CC_OK) return rc;
     Ctl h;
