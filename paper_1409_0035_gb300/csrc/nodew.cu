@@ -188,30 +188,46 @@ __device__ __forceinline__ uint64_t dist_at(const NwJob &J, int64_t v, int j)
     return d;
 }
 
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// Both sweeps take kTile nodes per warp at a time with lane = sampled node
+// of the slice: the rows of all kTile nodes are loaded first (coalesced, one
+// memory round trip per tile), per-source sums stay in the lanes'
+// registers, per-node sums are warp-reduced and land on lane u for node u,
+// whose read-modify-writes the first kTile lanes then issue together.
+constexpr int kTile = 8;
+
 // First sweep: wsum[v] += sum over the slice of mu_i d(c_i, v) and S[i] +=
-// sum over v of beta(v) d(c_i, v) (warp sums, one atomic per warp and
-// column).  The loop runs per warp so that every lane takes part in the
-// shuffles.
+// sum over v of beta(v) d(c_i, v).
 __global__ void __launch_bounds__(kT) k_nw_reduce1(NwJob J)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; w0 < J.n;
-         w0 += stride) {
-        const int64_t v = w0 + lane;
-        const bool on = v < J.n;
-        const uint64_t bv = on ? J.beta[v] : 0;
-        uint64_t acc = 0;
-        for (int j = 0; j < J.kc; ++j) {
-            const uint64_t d = on ? dist_at(J, v, j) : 0;
-            acc += J.mu[J.base + j] * d;
-            uint64_t x = bv * d;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool valid = lane < J.kc;
+    const uint64_t mu = valid ? J.mu[J.base + lane] : 0;
+    uint64_t Sacc = 0;
+    for (int64_t v0 = gwarp * kTile; v0 < J.n; v0 += nwarps * kTile) {
+        uint64_t d[kTile];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
-            if (lane == 0 && x) atomicAdd(&J.S[J.base + j], (unsigned long long)x);
+        for (int u = 0; u < kTile; ++u) d[u] = valid && v0 + u < J.n ? dist_at(J, v0 + u, lane) : 0;
+        const uint64_t bl = lane < kTile && v0 + lane < J.n ? J.beta[v0 + lane] : 0;
+        uint64_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < kTile; ++u) {
+            if (v0 + u >= J.n) break;  // warp-uniform
+            Sacc += __shfl_sync(0xFFFFFFFFu, bl, u) * d[u];
+            const uint64_t x = warp_sum64(mu * d[u]);
+            if (lane == u) mine = x;
         }
-        if (on) J.wsum[v] += acc;
+        if (lane < kTile && v0 + lane < J.n) J.wsum[v0 + lane] += mine;
     }
+    if (valid && Sacc) atomicAdd(&J.S[J.base + lane], (unsigned long long)Sacc);
 }
 
 // Second sweep (non-sampled nodes): the HC / L split of the slice's sampled
@@ -219,7 +235,8 @@ __global__ void __launch_bounds__(kT) k_nw_reduce1(NwJob J)
 // distances (D < kSmemRows) the slice's histogram (D + 1 rows of 32
 // columns) is accumulated per CTA in shared memory and added to the global
 // one at the end: most nodes share a handful of (distance, source) cells,
-// which global atomics would serialise in L2.
+// which global atomics would serialise in L2.  A warp's lanes always hit
+// different columns.
 constexpr int kSmemRows = 192;
 
 __global__ void __launch_bounds__(kT) k_nw_reduce2(NwJob J, int64_t D)
@@ -229,29 +246,66 @@ __global__ void __launch_bounds__(kT) k_nw_reduce2(NwJob J, int64_t D)
     const int cells = local ? (int)(D + 1) * 32 : 0;
     for (int c = threadIdx.x; c < cells; c += blockDim.x) sh[c] = 0;
     __syncthreads();
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < J.n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        if (J.sidx[v] >= 0) continue;
-        const uint64_t bv = J.beta[v];
-        const uint64_t thr = (uint64_t)J.delta[v] * J.b;
-        const uint32_t *drow = J.dcc + (size_t)J.pivot[v] * J.k + J.base;
-        uint64_t lpart = 0, hc = 0;
-        for (int j = 0; j < J.kc; ++j) {
-            const uint64_t d = dist_at(J, v, j);
-            const int i = J.base + j;
-            if (bv) {
-                if (local)
-                    atomicAdd(&sh[d * 32 + j], (unsigned long long)bv);
-                else
-                    atomicAdd(&J.hist[d * J.k + i], (unsigned long long)bv);
-            }
-            if ((uint64_t)drow[j] * J.a > thr)
-                hc += (uint64_t)J.bsrc[i] * d;
-            else
-                lpart += J.mu[i] * d;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool valid = lane < J.kc;
+    const int i = J.base + lane;
+    const uint64_t mu = valid ? J.mu[i] : 0;
+    const uint64_t bs = valid ? J.bsrc[i] : 0;
+    for (int64_t v0 = gwarp * kTile; v0 < J.n; v0 += nwarps * kTile) {
+        // per-node data on lanes 0..kTile-1
+        int32_t sx = 0, pv = 0;
+        uint32_t dl = 0, bv = 0;
+        if (lane < kTile && v0 + lane < J.n) {
+            const int64_t v = v0 + lane;
+            sx = J.sidx[v];
+            pv = J.pivot[v];
+            dl = J.delta[v];
+            bv = J.beta[v];
         }
-        J.lc[2 * v] += lpart;
-        J.lc[2 * v + 1] += hc;
+        uint64_t d[kTile];
+        uint32_t dc[kTile];
+#pragma unroll
+        for (int u = 0; u < kTile; ++u) {
+            const int32_t p = __shfl_sync(0xFFFFFFFFu, pv, u);
+            const bool on = valid && v0 + u < J.n;
+            d[u] = on ? dist_at(J, v0 + u, lane) : 0;
+            dc[u] = on ? J.dcc[(size_t)p * J.k + i] : 0;
+        }
+        uint64_t my_l = 0, my_h = 0;
+#pragma unroll
+        for (int u = 0; u < kTile; ++u) {
+            if (v0 + u >= J.n) break;                         // warp-uniform
+            if (__shfl_sync(0xFFFFFFFFu, sx, u) >= 0) continue;  // sampled: exact
+            const uint64_t thr = (uint64_t)__shfl_sync(0xFFFFFFFFu, dl, u) * J.b;
+            const uint32_t b_u = __shfl_sync(0xFFFFFFFFu, bv, u);
+            uint64_t lp = 0, hc = 0;
+            if (valid) {
+                const uint64_t dd = d[u];
+                if (b_u) {
+                    if (local)
+                        atomicAdd(&sh[dd * 32 + lane], (unsigned long long)b_u);
+                    else
+                        atomicAdd(&J.hist[dd * J.k + i], (unsigned long long)b_u);
+                }
+                if ((uint64_t)dc[u] * J.a > thr)
+                    hc = bs * dd;
+                else
+                    lp = mu * dd;
+            }
+            lp = warp_sum64(lp);
+            hc = warp_sum64(hc);
+            if (lane == u) {
+                my_l = lp;
+                my_h = hc;
+            }
+        }
+        if (lane < kTile && v0 + lane < J.n && sx < 0) {
+            const int64_t v = v0 + lane;
+            J.lc[2 * v] += my_l;
+            J.lc[2 * v + 1] += my_h;
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < cells; c += blockDim.x) {
@@ -405,15 +459,21 @@ void run_nw_mu(int k, const int32_t *sources, const uint32_t *beta, const uint64
     k_mu<<<(k + kT - 1) / kT, kT, 0, st>>>(k, sources, beta, tau, bsrc, mu, msum);
 }
 
+static int grid_tiles(int64_t n)  // a warp per kTile nodes
+{
+    const int64_t warps = (n + kTile - 1) / kTile;
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (warps * 32 + kT - 1) / kT), 152 * 16);
+}
+
 void run_nw_reduce1(const NwJob &j, cudaStream_t st)
 {
-    k_nw_reduce1<<<grid_for(j.n), kT, 0, st>>>(j);
+    k_nw_reduce1<<<grid_tiles(j.n), kT, 0, st>>>(j);
 }
 
 void run_nw_reduce2(const NwJob &j, int64_t D, cudaStream_t st)
 {
     const size_t smem = D < kSmemRows ? (size_t)(D + 1) * 32 * 8 : 0;  // <= 48 KB
-    k_nw_reduce2<<<grid_for(j.n), kT, smem, st>>>(j, D);
+    k_nw_reduce2<<<grid_tiles(j.n), kT, smem, st>>>(j, D);
 }
 
 void run_nw_tail(const unsigned long long *hist, int64_t D, int k, uint64_t *TS,

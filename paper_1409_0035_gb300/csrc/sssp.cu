@@ -131,37 +131,59 @@ __device__ __forceinline__ uint64_t chunk_dist(const ReduceJob &R, int64_t v, in
 
 // Pass-1 reduction of one chunk: sums, running (distance, index) minimum
 // for the pivot, distances between sampled nodes, exact S of the chunk's
-// sources and the largest distance.
+// sources and the largest distance.  A warp takes kTile nodes at a time,
+// lane = source: the rows of all kTile nodes are loaded before any is
+// reduced (one memory round trip per tile, not per node), and lane u then
+// holds node u's sums and key for the read-modify-writes, which the first
+// kTile lanes issue together.
+constexpr int kTile = 8;
+
 __global__ void k_reduce1(ReduceJob R)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int gi = R.base + lane;
+    const bool valid = lane < R.kc;
     unsigned long long Sl = 0, dmax = 0;
     int bad = 0;
-    for (int64_t v = gwarp; v < R.n; v += nwarps) {
-        const uint64_t d = chunk_dist(R, v, lane);
-        const bool valid = lane < R.kc;
-        if (valid && d >= (uint64_t)kInf) bad = 1;
-        const uint64_t dd = valid && d < kInf ? d : 0;
-        Sl += dd;
-        dmax = dd > dmax ? dd : dmax;
-        const unsigned long long s = warp_sum(dd), s2 = warp_sum(dd * dd);
-        unsigned long long key = valid ? ((d << 32) | (uint64_t)gi) : ~0ull;
+    for (int64_t v0 = gwarp * kTile; v0 < R.n; v0 += nwarps * kTile) {
+        uint64_t d[kTile];
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(FULL, key, o);
-            key = y < key ? y : key;
+        for (int u = 0; u < kTile; ++u)
+            d[u] = v0 + u < R.n ? chunk_dist(R, v0 + u, lane) : (uint64_t)kInf;
+        const int32_t sx =
+            !R.sum_only && lane < kTile && v0 + lane < R.n ? R.sidx[v0 + lane] : -1;
+        unsigned long long my_s = 0, my_s2 = 0, my_key = ~0ull;
+#pragma unroll
+        for (int u = 0; u < kTile; ++u) {
+            if (v0 + u >= R.n) break;  // warp-uniform
+            const uint64_t du = d[u];
+            if (valid && du >= (uint64_t)kInf) bad = 1;
+            const uint64_t dd = valid && du < kInf ? du : 0;
+            Sl += dd;
+            dmax = dd > dmax ? dd : dmax;
+            const unsigned long long s = warp_sum(dd), s2 = warp_sum(dd * dd);
+            unsigned long long key = valid ? ((du << 32) | (uint64_t)gi) : ~0ull;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(FULL, key, o);
+                key = y < key ? y : key;
+            }
+            if (lane == u) {
+                my_s = s;
+                my_s2 = s2;
+                my_key = key;
+            }
+            const int j = __shfl_sync(FULL, sx, u);
+            if (j >= 0 && valid) R.dcc[(int64_t)gi * R.k + j] = (uint32_t)dd;
         }
-        if (lane == 0) {
-            R.sum2[2 * v] += s;
-            R.sum2[2 * v + 1] += s2;
-            if (!R.sum_only && key < R.best[v]) R.best[v] = key;
+        if (lane < kTile && v0 + lane < R.n) {
+            const int64_t v = v0 + lane;
+            R.sum2[2 * v] += my_s;
+            R.sum2[2 * v + 1] += my_s2;
+            if (!R.sum_only && my_key < R.best[v]) R.best[v] = my_key;
         }
-        if (R.sum_only) continue;
-        const int j = R.sidx[v];
-        if (j >= 0 && valid) R.dcc[(int64_t)gi * R.k + j] = (uint32_t)dd;
     }
     if (lane < R.kc && !R.sum_only) {
         atomicAdd(&R.S_samp[gi], Sl);
