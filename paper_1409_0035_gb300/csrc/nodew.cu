@@ -227,7 +227,17 @@ __global__ void __launch_bounds__(kT) k_nw_reduce1(NwJob J)
         }
         if (lane < kTile && v0 + lane < J.n) J.wsum[v0 + lane] += mine;
     }
-    if (valid && Sacc) atomicAdd(&J.S[J.base + lane], (unsigned long long)Sacc);
+    // one global atomic per (CTA, source): the warps' sums meet in shared
+    // memory first
+    __shared__ uint64_t s_S[kT / 32][32];
+    s_S[threadIdx.x >> 5][lane] = Sacc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint64_t t = 0;
+        for (int w = 0; w < kT / 32; ++w) t += s_S[w][threadIdx.x];
+        if (threadIdx.x < J.kc && t)
+            atomicAdd(&J.S[J.base + threadIdx.x], (unsigned long long)t);
+    }
 }
 
 // Second sweep (non-sampled nodes): the HC / L split of the slice's sampled

@@ -185,9 +185,28 @@ __global__ void k_reduce1(ReduceJob R)
             if (!R.sum_only && my_key < R.best[v]) R.best[v] = my_key;
         }
     }
-    if (lane < R.kc && !R.sum_only) {
-        atomicAdd(&R.S_samp[gi], Sl);
-        atomicMax(R.dmax, dmax);
+    // Per-source sums and the largest distance are combined over the CTA in
+    // shared memory first: one global atomic per (CTA, source), not per
+    // (warp, source), and one atomicMax per CTA (same-address atomics from
+    // every lane serialise in L2).
+    __shared__ unsigned long long s_S[kBlock / 32][32], s_max[kBlock / 32];
+    const int wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(FULL, dmax, o);
+        dmax = y > dmax ? y : dmax;
+    }
+    s_S[wid][lane] = Sl;
+    if (lane == 0) s_max[wid] = dmax;
+    __syncthreads();
+    if (threadIdx.x < 32 && !R.sum_only) {
+        unsigned long long t = 0, m = 0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            t += s_S[w][threadIdx.x];
+            m = s_max[w] > m ? s_max[w] : m;
+        }
+        if (threadIdx.x < R.kc && t) atomicAdd(&R.S_samp[R.base + threadIdx.x], t);
+        if (threadIdx.x == 0 && m) atomicMax(R.dmax, m);
     }
     if (bad) atomicExch(R.err, CC_ERR_DISCONNECTED);
 }
@@ -330,7 +349,7 @@ int mssp_blocks_per_sm()
 
 void run_reduce1(const ReduceJob &r, cudaStream_t st)
 {
-    k_reduce1<<<grid_of(r.n * 32), 256, 0, st>>>(r);
+    k_reduce1<<<grid_of(r.n * 32), kBlock, 0, st>>>(r);
 }
 
 void run_reduce2(const ReduceJob &r, cudaStream_t st)
