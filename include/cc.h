@@ -276,8 +276,9 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
  * Outputs are host arrays, any may be NULL.  Runs one cooperative launch
  * over the order in groups of up to 256 sources: bit-packed searches on G^T
  * (outbound) or G (inbound) that skip nodes already holding k + 1 nodes of
- * smaller rank (themselves included).  Unit lengths only.  Errors:
- * CC_ERR_ARG (k < 1, a graph with arc lengths), CC_ERR_OOM, CC_ERR_CUDA,
+ * smaller rank (themselves included); breadth-first on unit lengths,
+ * label-correcting shortest paths with arc lengths (distances must stay
+ * below 2^32 - 1).  Errors: CC_ERR_ARG (k < 1), CC_ERR_OOM, CC_ERR_CUDA,
  * CC_ERR_TIMEOUT (a bounded device-side wait ran out).
  */
 int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, void *stream,

@@ -1641,7 +1641,7 @@ int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, v
                       double *avg_dist, double *reach, int32_t *count, uint64_t *dist_sum,
                       int64_t *T)
 {
-    if (!g || k < 1 || g->weighted) return CC_ERR_ARG;
+    if (!g || k < 1) return CC_ERR_ARG;
     RC(device_ok());
     reset_timing(g);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1676,6 +1676,7 @@ int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, v
     CK(cudaMemsetAsync(g->rc_vis.p, 0, n * W * 8, st));
     CK(cudaMemsetAsync(g->rc_F.p, 0, n * W * 8, st));
     CK(cudaMemsetAsync(g->rc_nxt.p, 0, n * W * 8, st));
+    if (g->weighted) CK(cudaMemsetAsync(g->rc_lev.p, 0xFF, n * 64 * W * 4, st));
     RC(reach_order(g->n, seed, g->nw_keys.as<uint64_t>(), g->nw_vals.as<uint32_t>(),
                    g->nw_tk.as<uint64_t>(), g->nw_tv.as<uint32_t>(), g->rc_order.as<int32_t>(),
                    g->rc_rank.as<int32_t>(), st));
@@ -1686,6 +1687,7 @@ int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, v
     j.W = W;
     j.rp = sg.rp.as<int64_t>();
     j.col = sg.col.as<int32_t>();
+    j.w = g->weighted ? sg.w.as<uint32_t>() : nullptr;
     j.order = g->rc_order.as<int32_t>();
     j.rank = g->rc_rank.as<int32_t>();
     j.cnt = g->rc_cnt.as<int32_t>();

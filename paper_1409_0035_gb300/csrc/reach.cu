@@ -26,6 +26,14 @@
 // the rule above keeps the stated aim, a uniform sample of size k of every
 // reachability set.
 //
+// With arc lengths (section 6.2 runs Dijkstra) each (node, source) slot
+// holds a tentative distance instead of a level: a round relaxes every
+// source whose distance at a frontier node dropped into its neighbours
+// (atomicMin), the nodes that improved form the next frontier, and the
+// rounds end when nothing improves -- label-correcting search, exact on the
+// unsaturated nodes by the same argument.  The slots of a node return to
+// infinity when it takes its samples.
+//
 // Every wait is the bounded grid barrier (CC_ERR_TIMEOUT on expiry).
 #include <algorithm>
 #include <cstdint>
@@ -53,7 +61,7 @@ __device__ __forceinline__ bool saturated(const ReachJob &J, int32_t x, int64_t 
     return c >= J.k && (J.extra[x] || (int64_t)J.rank[x] < base);
 }
 
-__global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
+__global__ void __launch_bounds__(kRT, 4) k_reach(ReachJob J, RState *rs)
 {
     const unsigned nb = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -97,14 +105,38 @@ __global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
                     const int32_t w = J.col[e];
                     if (saturated(J, w, base)) continue;
                     bool any = false;
+                    if (J.w) {
+                        // arc lengths: relax every changed source of u into w
+                        const uint64_t len = J.w[e];
 #pragma unroll
-                    for (int q = 0; q < kReachMaxW; ++q) {
-                        if (q >= W) break;
-                        const uint64_t nbits = Fu[q] & ~J.vis[(int64_t)w * W + q];
-                        if (nbits) {
-                            atomicOr((unsigned long long *)&J.nxt[(int64_t)w * W + q],
-                                     (unsigned long long)nbits);
-                            any = true;
+                        for (int q = 0; q < kReachMaxW; ++q) {
+                            if (q >= W) break;
+                            uint64_t imp = 0;
+                            for (uint64_t x = Fu[q]; x; x &= x - 1) {
+                                const int i = q * 64 + (__ffsll((long long)x) - 1);
+                                const uint64_t cand =
+                                    (uint64_t)__ldcg(&J.lev[(int64_t)u * G + i]) + len;
+                                if (cand >= (uint64_t)kInf) continue;
+                                const uint32_t old =
+                                    atomicMin(&J.lev[(int64_t)w * G + i], (uint32_t)cand);
+                                if (cand < old) imp |= 1ull << (i & 63);
+                            }
+                            if (imp) {
+                                atomicOr((unsigned long long *)&J.nxt[(int64_t)w * W + q],
+                                         (unsigned long long)imp);
+                                any = true;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < kReachMaxW; ++q) {
+                            if (q >= W) break;
+                            const uint64_t nbits = Fu[q] & ~J.vis[(int64_t)w * W + q];
+                            if (nbits) {
+                                atomicOr((unsigned long long *)&J.nxt[(int64_t)w * W + q],
+                                         (unsigned long long)nbits);
+                                any = true;
+                            }
                         }
                     }
                     if (any && atomicExch(&J.qstamp[w], epoch) != epoch)
@@ -112,7 +144,8 @@ __global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
                 }
             }
             if (!grid_sync(J.ctl, blockIdx.x, nb, J.timeout_ns)) return;
-            // the next frontier: new bits, their levels, first touches
+            // the next frontier: new bits (with arc lengths: the sources whose
+            // distance dropped), their levels, first touches
             const unsigned qn2 = qlen[nxq];
             for (int64_t idx = tid; idx < qn2; idx += nthr) {
                 const int32_t w = J.Q[nxq][idx];
@@ -120,13 +153,14 @@ __global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
                 for (int q = 0; q < W; ++q) {
                     const int64_t at = (int64_t)w * W + q;
                     const uint64_t old = J.vis[at];
-                    const uint64_t nbits = J.nxt[at] & ~old;
+                    const uint64_t nbits = J.w ? J.nxt[at] : J.nxt[at] & ~old;
                     if (old) fresh = false;
                     J.nxt[at] = 0;
                     J.vis[at] = old | nbits;
                     J.F[at] = nbits;
-                    for (uint64_t x = nbits; x; x &= x - 1)
-                        J.lev[(int64_t)w * G + q * 64 + (__ffsll((long long)x) - 1)] = level;
+                    if (!J.w)
+                        for (uint64_t x = nbits; x; x &= x - 1)
+                            J.lev[(int64_t)w * G + q * 64 + (__ffsll((long long)x) - 1)] = level;
                 }
                 if (fresh) J.TL[atomicAdd((unsigned *)&tlen[par], 1u)] = w;
             }
@@ -147,7 +181,8 @@ __global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
             bool done = false;
             for (int q = 0; q < W; ++q) {
                 const int64_t at = (int64_t)v * W + q;
-                uint64_t bits = J.vis[at];
+                const uint64_t reached = J.vis[at];
+                uint64_t bits = reached;
                 J.vis[at] = 0;
                 J.F[at] = 0;
                 if (rv >= base && rv < base + gs && (rv - base) >> 6 == q)
@@ -165,6 +200,9 @@ __global__ void __launch_bounds__(kRT) k_reach(ReachJob J, RState *rs)
                         done = true;
                     }
                 }
+                if (J.w)  // tentative distances start at infinity in every group
+                    for (uint64_t x = reached; x; x &= x - 1)
+                        J.lev[(int64_t)v * G + q * 64 + (__ffsll((long long)x) - 1)] = kInf;
             }
             J.cnt[v] = c;
             J.dsum[v] = ds;

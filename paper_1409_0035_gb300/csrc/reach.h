@@ -15,6 +15,7 @@ struct ReachJob {
     int k, W;                     // sample size; words per node (1..kReachMaxW)
     const int64_t *rp;            // search graph (G^T: outbound, G: inbound)
     const int32_t *col;
+    const uint32_t *w;            // its arc lengths (null: unit lengths)
     const int32_t *order, *rank;  // the random order and its inverse
     // per node
     int32_t *cnt;                 // samples taken (<= k)
@@ -24,6 +25,8 @@ struct ReachJob {
     uint32_t *qstamp;             // level stamp of the last push to the queue
     uint64_t *vis, *F, *nxt;      // n x W
     uint32_t *lev;                // n x 64 W: first-arrival level of each bit
+                                  // (arc lengths: tentative distance, kInf
+                                  // outside a group's search)
     int32_t *Q[2], *TL;           // frontier queues, touched list (n each)
     Ctl *ctl;                     // barrier counter and error code
     uint64_t timeout_ns;

@@ -4,7 +4,8 @@ the sum of the sample's distances and the rank position T bit-exact, the
 average distance and the size estimate within 1e-12 relative.  Covers graphs
 with many small and a few large reachability sets (directed R-MAT without
 taking a component), a DAG, a cycle, k below, at and above the 64 W-source
-group, an undirected graph, and several groups per run."""
+group, an undirected graph, several groups per run, and arc lengths
+(label-correcting rounds against the oracle's Dijkstra)."""
 import numpy as np
 import pytest
 
@@ -46,9 +47,9 @@ GRAPHS = {
 }
 
 
-def check(cc, n, s, d, k, seed, inbound, directed=True):
-    g, _ = cc.cc_graph_from_edges(n, s, d, directed=directed, keep_component=False)
-    og = orc.csr_from_edges(n, s, d, directed=directed, keep_component=False)
+def check(cc, n, s, d, k, seed, inbound, directed=True, w=None):
+    g, _ = cc.cc_graph_from_edges(n, s, d, w, directed=directed, keep_component=False)
+    og = orc.csr_from_edges(n, s, d, w=w, directed=directed, keep_component=False)
     try:
         assert cc.cc_graph_info(g)[0] == og.n
         r = cc.cc_reach_estimate(g, k, seed, inbound)
@@ -88,12 +89,22 @@ def test_undirected_in_and_out_agree(cc):
     assert np.array_equal(a["distsum"], b["distsum"])
 
 
-def test_arc_lengths_refused(cc):
-    n, s, d = synth.rmat_edges(8, 4, seed=1)
-    w = synth.random_weights(s.size, 1, 5, seed=2)
-    g, _ = cc.cc_graph_from_edges(n, s, d, w, directed=True, keep_component=False)
-    try:
-        with pytest.raises(cc.CCError):
-            cc.cc_reach_estimate(g, 4, 1)
-    finally:
-        cc.cc_graph_free(g)
+WCASES = [
+    # graph, k, inbound, arc-length range
+    ("rmat10-directed", 16, False, (1, 9)), ("rmat10-directed", 16, True, (1, 9)),
+    ("rmat11-directed", 300, False, (1, 1000)), ("dag1500", 8, True, (1, 50)),
+    ("cycle300", 299, False, (1, 5)),
+]
+
+
+@pytest.mark.parametrize("case", WCASES, ids=[f"{c[0]}-k{c[1]}-{'in' if c[2] else 'out'}-w"
+                                              for c in WCASES])
+def test_reach_arc_lengths_match_oracle(cc, case):
+    # Section 6.2 runs Dijkstra: with arc lengths the device's
+    # label-correcting rounds must give the same samples (reachability does
+    # not depend on lengths) and the shortest-path distance sums.
+    name, k, inbound, (lo, hi) = case
+    n, s, d = GRAPHS[name]()
+    w = synth.random_weights(s.size, lo, hi, seed=k)
+    r = check(cc, n, s, d, k, seed=5, inbound=inbound, w=w)
+    assert (r["count"] > 0).any()

@@ -161,3 +161,40 @@ def test_definition_matches_the_pruned_search(k):
     assert r["count"].tolist() == count
     assert [int(x) for x in r["distsum"]] == dsum
     assert r["T"].tolist() == T
+
+
+def test_weighted_directed_path_closed_form():
+    # Arc lengths: path i -> i+1 of length len[i]; every node reaches the
+    # higher ids at the prefix-sum distances.  k at least the reach: the
+    # sums are exact.
+    n = 10
+    lens = [3, 1, 4, 1, 5, 9, 2, 6, 5]
+    s = np.arange(n - 1, dtype=np.uint32)
+    g = O.csr_from_edges(n, s, s + 1, w=np.array(lens, np.uint32), directed=True,
+                         keep_component=False)
+    r = O.reach_from_table(O.all_pairs(g), O.sample_order(n, 5), n)
+    pre = np.concatenate([[0], np.cumsum(lens)])
+    for v in range(n):
+        want = sum(int(pre[u] - pre[v]) for u in range(v + 1, n))
+        assert r["count"][v] == n - 1 - v
+        assert int(r["distsum"][v]) == want
+
+
+def test_weighted_sample_distances_are_shortest_paths():
+    # With arc lengths the sample is still the k smallest ranks of R(v)
+    # (lengths do not change reachability) and each sampled distance is the
+    # shortest-path length; checked against scipy's Dijkstra.
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+    n, s, d = synth.rmat_edges(7, 4, seed=11)
+    w = synth.random_weights(s.size, 1, 9, seed=12)
+    g = O.csr_from_edges(n, s, d, w=w, directed=True, keep_component=False)
+    A = sp.csr_matrix((g.w.astype(float), g.col, g.row_ptr), shape=(g.n, g.n))
+    D = shortest_path(A, directed=True)
+    order = [int(x) for x in O.sample_order(g.n, 4)]
+    k = 5
+    r = O.reach_from_table(O.all_pairs(g), order, k)
+    for v in range(g.n):
+        reach = [u for u in order if u != v and np.isfinite(D[v, u])][:k]
+        assert r["count"][v] == len(reach)
+        assert int(r["distsum"][v]) == int(sum(D[v, u] for u in reach))
