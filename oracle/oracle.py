@@ -593,3 +593,48 @@ def all_pairs(g: Graph) -> np.ndarray:
     """n x n table of d(u, v) (row u), INF where v is unreachable: one BFS
     (Dijkstra with arc lengths) per node."""
     return np.stack([sssp(g, u) for u in range(g.n)])
+
+
+# --------------------------------------------------------------------------
+# One node at a time (undirected graphs of any size)
+# --------------------------------------------------------------------------
+
+def estimate_node(g: Graph, sources, v: int, eps=(1, 8)):
+    """Every statistic and estimate of section 2 for the single node v of an
+    undirected graph, from two searches: one from v (d(c_i, v) = d(v, c_i)
+    for every sampled node, and S(v)) and one from its pivot p (the H tail
+    d(p, w) over V \\ C, delta(p, c_i) and S(p)).  Same definitions as
+    estimate_from_table: pivot = the nearest sampled node, smallest index on
+    ties; x beyond when x a > Delta b; eq. (4) with the numerator
+    (Hsum + HCsum) |L n C| + LCsum |L| formed exactly and divided once.
+    Returns dict(pivot, delta, sum, s_hat (4 floats))."""
+    assert not g.directed
+    C = [int(c) for c in sources]
+    k, n = len(C), g.n
+    a, b = int(eps[0]), int(eps[1])
+    dv = sssp(g, v).astype(np.int64)
+    dC = np.array([dv[c] for c in C], dtype=np.int64)      # d(c_i, v)
+    sidx = {c: i for i, c in enumerate(C)}
+    total = int(dC.sum())
+    if v in sidx:
+        Sv = int(dv.sum())
+        return dict(pivot=sidx[v], delta=0, sum=total, s_hat=[float(Sv)] * 4)
+    i_p = int(np.argmin(dC))                                # first minimum
+    delta = int(dC[i_p])
+    dp = sssp(g, C[i_p]).astype(np.int64)
+    Sp = int(dp.sum())
+    from fractions import Fraction
+    s_samp = float(Fraction((n - 1) * total, k))
+    s_piv = float(Sp)
+    s_up = float(Sp + (n - 1) * delta)
+    notC = np.ones(n, dtype=bool)
+    notC[C] = False
+    H = notC & (dp * a > delta * b)
+    Hsum, Hnum = int(dp[H].sum()), int(H.sum())
+    HC = np.array([dp[c] * a > delta * b for c in C])
+    HCsum = int(dC[HC].sum())
+    LCnum = int((~HC).sum())
+    LCsum = int(dC[~HC].sum())
+    Lnum = (n - 1) - Hnum - int(HC.sum())
+    s_hyb = float(Fraction((Hsum + HCsum) * LCnum + LCsum * Lnum, LCnum))
+    return dict(pivot=i_p, delta=delta, sum=total, s_hat=[s_samp, s_piv, s_up, s_hyb])

@@ -425,3 +425,25 @@ def test_exhaustive_tiny_hybrid_against_definition_sets():
                         + sum(D[j, C[i]] for i in HC)
                         + Fraction(L, len(LC)) * sum(D[j, C[i]] for i in LC))
                 assert abs(r["s_hat"][3][j] - float(want)) <= 1e-12 * float(want)
+
+
+@pytest.mark.parametrize("gen,w,k,eps", [
+    (lambda: synth.rmat_edges(9, 8, seed=3), None, 40, (1, 6)),
+    (lambda: synth.grid_edges(20, 15), None, 12, (1, 2)),
+    (lambda: synth.rmat_edges(8, 8, seed=5), "w", 20, (1, 4)),
+])
+def test_single_node_estimate_equals_table(gen, w, k, eps):
+    """The one-node oracle (two searches per node, for graphs too large for
+    a k x n table) gives the table oracle's pivot, Delta, sum and all four
+    estimates for every node."""
+    n, s, d = gen()
+    wt = synth.random_weights(s.size, 1, 9, seed=2) if w else None
+    g = orc.csr_from_edges(n, s, d, w=wt)
+    C = orc.choose_sample(g.n, k, 7)
+    ref = orc.estimate_from_table(orc.dist_table(g, C), C, eps)
+    for v in range(g.n):
+        r = orc.estimate_node(g, C, v, eps)
+        assert r["pivot"] == ref["pivot"][v] and r["delta"] == ref["delta"][v]
+        assert r["sum"] == int(ref["sum"][v])
+        for e in range(4):
+            assert r["s_hat"][e] == ref["s_hat"][e][v], (v, e)
