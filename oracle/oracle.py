@@ -114,7 +114,10 @@ def _dedup_arcs(n, s, d, w):
     """Sort arcs by (s, d) and keep one per pair (the smallest weight)."""
     key = s.astype(np.int64) * n + d.astype(np.int64)
     if w is None:
-        key = np.unique(key)
+        key = np.sort(key)
+        first = np.ones(key.size, dtype=bool)
+        first[1:] = key[1:] != key[:-1]
+        key = key[first]
         return (key // n).astype(np.int64), (key % n).astype(np.int64), None
     order = np.lexsort((w, key))
     key, w = key[order], w[order]

@@ -12,6 +12,8 @@ self-loops are left in -- removing them is part of building the graph.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -53,20 +55,39 @@ def rmat_edges(scale: int, edge_factor: int, a=0.57, b=0.19, c=0.19, seed=1,
     m = edge_factor * n
     src = np.zeros(m, dtype=np.uint32)
     dst = np.zeros(m, dtype=np.uint32)
+    # u = x * 2^-53 with x = (splitmix64 output) >> 11, so u >= t exactly
+    # when x >= ceil(t * 2^53): the quadrant tests run on integers.
     t_ab, t_abc = a + b, a + b + c
-    for lo in range(0, m, _CHUNK):
-        hi = min(m, lo + _CHUNK)
-        e = np.arange(lo, hi, dtype=np.uint64)
-        s = np.zeros(hi - lo, dtype=np.uint32)
-        d = np.zeros(hi - lo, dtype=np.uint32)
-        for lev in range(scale):
-            u = uniform_at(seed, e * np.uint64(scale) + np.uint64(lev))
-            bit = np.uint32(1 << (scale - 1 - lev))
-            s |= np.where(u >= t_ab, bit, np.uint32(0)).astype(np.uint32)
-            d |= np.where(((u >= a) & (u < t_ab)) | (u >= t_abc), bit,
-                          np.uint32(0)).astype(np.uint32)
-        src[lo:hi] = s
-        dst[lo:hi] = d
+    X_a, X_ab, X_abc = (np.uint64(math.ceil(t * 2.0 ** 53)) for t in (a, t_ab, t_abc))
+    sd = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        for lo in range(0, m, _CHUNK):
+            hi = min(m, lo + _CHUNK)
+            e = np.arange(lo, hi, dtype=np.uint64)
+            s = np.zeros(hi - lo, dtype=np.uint32)
+            d = np.zeros(hi - lo, dtype=np.uint32)
+            # splitmix64 state seed + (counter + 1) * gamma for counter
+            # e * scale + lev, advanced by gamma per level
+            zc = sd + (e * np.uint64(scale) + np.uint64(1)) * _GAMMA
+            z = np.empty_like(zc)
+            t = np.empty_like(zc)
+            for lev in range(scale):
+                np.right_shift(zc, np.uint64(30), out=t)
+                np.bitwise_xor(zc, t, out=z)
+                z *= _M1
+                np.right_shift(z, np.uint64(27), out=t)
+                z ^= t
+                z *= _M2
+                np.right_shift(z, np.uint64(31), out=t)
+                z ^= t
+                z >>= np.uint64(11)
+                shift = np.uint32(scale - 1 - lev)
+                hi_s = z >= X_ab
+                s |= hi_s.astype(np.uint32) << shift
+                d |= (((z >= X_a) & ~hi_s) | (z >= X_abc)).astype(np.uint32) << shift
+                zc += _GAMMA
+            src[lo:hi] = s
+            dst[lo:hi] = d
     if relabel:
         keys = splitmix64_at(seed + 1, np.arange(n, dtype=np.uint64))
         order = np.lexsort((np.arange(n), keys))
