@@ -602,20 +602,31 @@ def all_pairs(g: Graph) -> np.ndarray:
 # One node at a time (undirected graphs of any size)
 # --------------------------------------------------------------------------
 
-def estimate_node(g: Graph, sources, v: int, eps=(1, 8)):
-    """Every statistic and estimate of section 2 for the single node v of an
-    undirected graph, from two searches: one from v (d(c_i, v) = d(v, c_i)
-    for every sampled node, and S(v)) and one from its pivot p (the H tail
-    d(p, w) over V \\ C, delta(p, c_i) and S(p)).  Same definitions as
+def _metric_from(g: Graph, x: int, roundtrip: bool) -> np.ndarray:
+    """d(x, .) (undirected), or the round-trip d(x, .) + d(., x) (section
+    6.1: a search on G plus one on G^T)."""
+    d = sssp(g, x).astype(np.int64)
+    if roundtrip:
+        back = sssp(g, x, reverse=True).astype(np.int64)
+        d = np.where((d == INF) | (back == INF), INF, d + back)
+    return d
+
+
+def estimate_node(g: Graph, sources, v: int, eps=(1, 8), roundtrip=False):
+    """Every statistic and estimate of section 2 for the single node v, from
+    searches out of v (its distance to every sampled node, and S(v)) and out
+    of its pivot p (the H tail d(p, w) over V \\ C, delta(p, c_i) and S(p)):
+    one search each on an undirected graph, a forward and a reversed one
+    each for round trips (section 6.1).  Same definitions as
     estimate_from_table: pivot = the nearest sampled node, smallest index on
     ties; x beyond when x a > Delta b; eq. (4) with the numerator
     (Hsum + HCsum) |L n C| + LCsum |L| formed exactly and divided once.
     Returns dict(pivot, delta, sum, s_hat (4 floats))."""
-    assert not g.directed
+    assert roundtrip == g.directed
     C = [int(c) for c in sources]
     k, n = len(C), g.n
     a, b = int(eps[0]), int(eps[1])
-    dv = sssp(g, v).astype(np.int64)
+    dv = _metric_from(g, v, roundtrip)
     dC = np.array([dv[c] for c in C], dtype=np.int64)      # d(c_i, v)
     sidx = {c: i for i, c in enumerate(C)}
     total = int(dC.sum())
@@ -624,7 +635,7 @@ def estimate_node(g: Graph, sources, v: int, eps=(1, 8)):
         return dict(pivot=sidx[v], delta=0, sum=total, s_hat=[float(Sv)] * 4)
     i_p = int(np.argmin(dC))                                # first minimum
     delta = int(dC[i_p])
-    dp = sssp(g, C[i_p]).astype(np.int64)
+    dp = _metric_from(g, C[i_p], roundtrip)
     Sp = int(dp.sum())
     from fractions import Fraction
     s_samp = float(Fraction((n - 1) * total, k))

@@ -447,3 +447,20 @@ def test_single_node_estimate_equals_table(gen, w, k, eps):
         assert r["sum"] == int(ref["sum"][v])
         for e in range(4):
             assert r["s_hat"][e] == ref["s_hat"][e][v], (v, e)
+
+
+@pytest.mark.parametrize("w", [None, "w"])
+def test_single_node_round_trip_equals_table(w):
+    """Round trips (section 6.1): the one-node oracle's forward and reversed
+    searches give the round-trip table oracle's statistics and estimates."""
+    n, s, d = synth.rmat_edges(9, 6, seed=13)
+    wt = synth.random_weights(s.size, 1, 7, seed=4) if w else None
+    g = orc.csr_from_edges(n, s, d, w=wt, directed=True)
+    C = orc.choose_sample(g.n, 24, 3)
+    ref = orc.estimate_from_table(orc.dist_table(g, C, roundtrip=True), C, (1, 3))
+    for v in range(g.n):
+        r = orc.estimate_node(g, C, v, (1, 3), roundtrip=True)
+        assert r["pivot"] == ref["pivot"][v] and r["delta"] == ref["delta"][v]
+        assert r["sum"] == int(ref["sum"][v])
+        for e in range(4):
+            assert r["s_hat"][e] == ref["s_hat"][e][v], (v, e)
