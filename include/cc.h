@@ -14,7 +14,11 @@
  * distances on the fly into per-node statistics, never storing the k x n
  * distance matrix.  From them the library forms, for every node, the sampling
  * estimate (eq. (3)), the pivoting estimate B(c(v)), the pivoting upper bound
- * B(c(v)) + Delta(v) and the hybrid estimate (eq. (4)).
+ * B(c(v)) + Delta(v) and the hybrid estimate (eq. (4)).  Further entry
+ * points give the hybrid's error estimate and the adaptive hybrid
+ * (sections 4, 6), node-weighted closeness (section 5), outbound / inbound
+ * estimates of general directed graphs (section 6.2), batches of graphs in
+ * one launch and a serving loop.
  *
  * Conventions for every entry point:
  *   - returns CC_OK (0) or a negative CC_ERR_* code; no exception crosses the
@@ -201,6 +205,7 @@ int cc_estimate_adaptive(cc_graph_t g, const int32_t *sample, int32_t k,
                          const uint32_t *eps_den, double *s_hat, double *closeness,
                          double *sq_err, int32_t *choice);
 
+/* ---- node weights -------------------------------------------------------- */
 /*
  * Node-weighted closeness (section 5, "Weighted Centrality"; its
  * modification of Algorithm 1).  With node weights beta(v) >= 0,
@@ -257,6 +262,7 @@ typedef struct {
 int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
                               const uint64_t *tau, const cc_opts *opts, cc_wout *out);
 
+/* ---- general directed graphs ---------------------------------------------- */
 /*
  * cc_reach_estimate -- outbound / inbound estimates of general (not
  * necessarily strongly connected) directed graphs (section 6.2, Algorithm
@@ -285,6 +291,7 @@ int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, v
                       double *avg_dist, double *reach, int32_t *count, uint64_t *dist_sum,
                       int64_t *T);
 
+/* ---- exact values and single-source reference ---------------------------- */
 /*
  * cc_exact -- exact S(v) and B^-1(v) = (n-1)/S(v) for every node (eq. (1))
  * by traversals from every node, packed 64 per word.  Meant for small
