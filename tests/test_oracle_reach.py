@@ -198,3 +198,83 @@ def test_weighted_sample_distances_are_shortest_paths():
         reach = [u for u in order if u != v and np.isfinite(D[v, u])][:k]
         assert r["count"][v] == len(reach)
         assert int(r["distsum"][v]) == int(sum(D[v, u] for u in reach))
+
+
+def _group_schedule(g, order, k, G, inbound=False):
+    """The device's schedule, modelled on the CPU: sources in rank order in
+    groups of G searched together (unit lengths: breadth-first by levels;
+    arc lengths: label-correcting rounds), nodes saturated at the start of
+    a group -- k + 1 sources other than the node reached it, or k and its
+    own search has run -- neither entered nor expanded, the first arrival
+    (shortest distance) of each source recorded, then every touched node
+    takes its lowest-rank sources other than itself until it holds k."""
+    n = g.n
+    if inbound:
+        rp, col, w = g.row_ptr, g.col, g.w
+    else:
+        rp, col, w = g.rrow_ptr, g.rcol, g.rw
+    rank = {int(u): p for p, u in enumerate(order)}
+    cnt, extra, dsum, T = [0] * n, [False] * n, [0] * n, [0] * n
+
+    def saturated(x, base):
+        return cnt[x] >= k and (extra[x] or rank[x] < base)
+
+    for base in range(0, n, G):
+        srcs = [int(u) for u in order[base:base + G]]
+        dist = {}                      # (node, i) -> distance
+        front = {}
+        for i, s in enumerate(srcs):
+            if not saturated(s, base):
+                dist[(s, i)] = 0
+                front.setdefault(s, set()).add(i)
+        while front:
+            nxt = {}
+            for u, bits in front.items():
+                for e in range(rp[u], rp[u + 1]):
+                    x = int(col[e])
+                    if saturated(x, base):
+                        continue
+                    ln = 1 if w is None else int(w[e])
+                    for i in bits:
+                        cand = dist[(u, i)] + ln
+                        if cand < dist.get((x, i), 1 << 62):
+                            dist[(x, i)] = cand
+                            nxt.setdefault(x, set()).add(i)
+            front = nxt
+        touched = {}
+        for (x, i), d in dist.items():
+            touched.setdefault(x, {})[i] = d
+        for x, got in touched.items():
+            for i in sorted(got):
+                if srcs[i] == x:
+                    continue
+                if cnt[x] < k:
+                    dsum[x] += got[i]
+                    cnt[x] += 1
+                    if cnt[x] == k:
+                        t = base + i + 1
+                        T[x] = t - 1 if rank[x] < base + i else t
+                else:
+                    extra[x] = True
+                    break
+    return cnt, dsum, T
+
+
+@pytest.mark.parametrize("G", [1, 3, 16, 64])
+@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("lengths", [False, True])
+def test_group_schedule_equals_definition(G, k, lengths):
+    # Searching G rank-ordered sources at once, with the pruning rule
+    # applied only at group boundaries and every touched node keeping its
+    # lowest ranks, gives the definition's samples, distances and T.
+    n, s, d = synth.rmat_edges(7, 3, seed=21)
+    w = synth.random_weights(s.size, 1, 6, seed=22) if lengths else None
+    g = O.csr_from_edges(n, s, d, w=w, directed=True, keep_component=False)
+    order = [int(x) for x in O.sample_order(g.n, 6)]
+    D = O.all_pairs(g)
+    for inbound in (False, True):
+        r = O.reach_from_table(D, order, k, inbound=inbound)
+        cnt, dsum, T = _group_schedule(g, order, k, G, inbound=inbound)
+        assert r["count"].tolist() == cnt
+        assert [int(x) for x in r["distsum"]] == dsum
+        assert r["T"].tolist() == T
