@@ -652,3 +652,65 @@ def estimate_node(g: Graph, sources, v: int, eps=(1, 8), roundtrip=False):
     Lnum = (n - 1) - Hnum - int(HC.sum())
     s_hyb = float(Fraction((Hsum + HCsum) * LCnum + LCsum * Lnum, LCnum))
     return dict(pivot=i_p, delta=delta, sum=total, s_hat=[s_samp, s_piv, s_up, s_hyb])
+
+
+def reach_node(g: Graph, order, v: int, k: int, inbound=False):
+    """reach_from_table for the single node v, from one search out of v
+    (on G for outbound, on G^T for inbound).  Returns dict(count, distsum,
+    T, avg, R_hat) for v."""
+    n = g.n
+    dist = sssp(g, v, reverse=inbound).astype(np.int64)
+    order = np.asarray(order, dtype=np.int64)
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n)
+    reach = order[(dist[order] != INF) & (order != v)]   # in rank order
+    sample = reach[:k]
+    count = int(sample.size)
+    distsum = int(dist[sample].sum())
+    T, R_hat = 0, float(count)
+    if count == k:
+        t = int(pos[sample[-1]]) + 1
+        T = t - 1 if pos[v] < pos[sample[-1]] else t
+        R_hat = 1.0 if k == 1 else 1.0 + float((k - 1) * (n - 2)) / float(T - 1)
+    return dict(count=count, distsum=distsum, T=T,
+                avg=(distsum / count if count else 0.0), R_hat=R_hat)
+
+
+def node_weighted_node(g: Graph, sources, beta, tau, v: int, eps=(1, 8), roundtrip=False):
+    """node_weighted_from_table for the single node v, from searches out of
+    v and out of its pivot (as estimate_node).  Returns dict(num (2 Python
+    ints over td), s_hat (2 floats), closeness (2 floats))."""
+    from fractions import Fraction
+    C = [int(c) for c in sources]
+    beta = [int(x) for x in beta]
+    tn, td = int(tau[0]), int(tau[1])
+    a, b = int(eps[0]), int(eps[1])
+    n = g.n
+    bvec = np.asarray(beta, dtype=np.int64)
+    total = int(bvec.sum())
+    dv = _metric_from(g, v, roundtrip)
+    sidx = {c: i for i, c in enumerate(C)}
+    if v in sidx:
+        S = int((bvec * dv).sum())
+        num = [S * td, S * td]
+    else:
+        col = np.array([dv[c] for c in C], dtype=np.int64)
+        bC = np.array([beta[c] for c in C], dtype=np.int64)
+        certain = np.array([is_certain(x, (tn, td)) for x in bC.tolist()], dtype=bool)
+        num0 = tn * int(col[~certain].sum()) + td * int((bC[certain] * col[certain]).sum())
+        i_p = int(np.argmin(col))
+        delta = int(col[i_p])
+        row = _metric_from(g, C[i_p], roundtrip)
+        notC = np.ones(n, dtype=bool)
+        notC[C] = False
+        H = notC & (row * a > delta * b)
+        Hsum = int((bvec[H] * row[H]).sum())
+        HC = np.array([row[c] * a > delta * b for c in C])
+        HCsum = int((bC[HC] * col[HC]).sum())
+        LC = ~HC
+        Lpart = (tn * int(col[LC & ~certain].sum()) +
+                 td * int((bC[LC & certain] * col[LC & certain]).sum()))
+        num = [num0, td * (Hsum + HCsum) + Lpart]
+    s_hat = [float(Fraction(x, td)) for x in num]
+    wv = float(total - beta[v])
+    return dict(num=num, s_hat=s_hat, closeness=[wv / x if x else float("nan") for x in s_hat])

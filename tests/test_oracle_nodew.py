@@ -207,3 +207,24 @@ def test_sample_is_exact_size_and_skips_zero_weights(seed):
     order = O.sample_order(60, seed).tolist()
     pos = [order.index(c) for c in C]
     assert pos == sorted(pos)  # listed in the order of the draw
+
+
+@pytest.mark.parametrize("graph", ["rmat", "weighted", "roundtrip"])
+def test_single_node_weighted_equals_table(graph):
+    # Two searches per node (from it and from its pivot) give the table
+    # function's numerators, estimates and closeness for every node.
+    if graph == "roundtrip":
+        n, s, d = synth.rmat_edges(8, 6, seed=41)
+        g = O.csr_from_edges(n, s, d, directed=True)
+    else:
+        n, s, d = synth.rmat_edges(8, 6, seed=42)
+        w = synth.random_weights(s.size, 1, 9, seed=43) if graph == "weighted" else None
+        g = O.csr_from_edges(n, s, d, w=w)
+    rt = graph == "roundtrip"
+    beta = _weights(g.n, "heavy", seed=44)
+    C, tau = O.sample_varopt(beta, 15, seed=45)
+    ref = O.node_weighted_from_table(O.dist_table(g, C, roundtrip=rt), C, beta, tau, (1, 3))
+    for v in range(g.n):
+        r = O.node_weighted_node(g, C, beta, tau, v, (1, 3), roundtrip=rt)
+        assert r["num"] == [ref["num"][0][v], ref["num"][1][v]]
+        assert r["s_hat"] == [ref["s_hat"][0][v], ref["s_hat"][1][v]]

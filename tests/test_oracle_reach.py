@@ -278,3 +278,22 @@ def test_group_schedule_equals_definition(G, k, lengths):
         assert r["count"].tolist() == cnt
         assert [int(x) for x in r["distsum"]] == dsum
         assert r["T"].tolist() == T
+
+
+@pytest.mark.parametrize("lengths", [False, True])
+def test_single_node_reach_equals_table(lengths):
+    # One search per node (for graphs too large for an n x n table) gives
+    # the table function's count, sum, T and estimates.
+    n, s, d = synth.rmat_edges(8, 4, seed=31)
+    w = synth.random_weights(s.size, 1, 9, seed=32) if lengths else None
+    g = O.csr_from_edges(n, s, d, w=w, directed=True, keep_component=False)
+    order = O.sample_order(g.n, 9)
+    D = O.all_pairs(g)
+    for inbound in (False, True):
+        for k in (1, 3, 20):
+            ref = O.reach_from_table(D, order, k, inbound=inbound)
+            for v in range(0, g.n, 3):
+                r = O.reach_node(g, order, v, k, inbound=inbound)
+                assert (r["count"], r["distsum"], r["T"]) == (
+                    ref["count"][v], int(ref["distsum"][v]), ref["T"][v])
+                assert r["avg"] == ref["avg"][v] and r["R_hat"] == ref["R_hat"][v]
