@@ -199,15 +199,6 @@ int build_classes(const std::vector<int64_t> &rp, int64_t n, Classes &c, const i
     return CC_OK;
 }
 
-int upload_csr(DevCSR &d, int64_t n, const std::vector<int64_t> &rp,
-               const std::vector<int32_t> &col, const std::vector<uint32_t> &w)
-{
-    RC(upload(d.rp, rp.data(), rp.size() * 8));
-    RC(upload(d.col, col.data(), col.size() * 4));
-    if (!w.empty()) RC(upload(d.w, w.data(), w.size() * 4));
-    return build_classes(rp, n, d.cls, d.rp.as<int64_t>(), d.col.as<int32_t>());
-}
-
 int pow2_words(int k)
 {
     const int need = (k + 63) / 64;
@@ -384,16 +375,6 @@ int validate_sample(const cc_graph *g, const int32_t *sample, int32_t k)
         if (c < 0 || c >= g->n || seen[c]) return CC_ERR_ARG;
         seen[c] = 1;
     }
-    return CC_OK;
-}
-
-int finish_graph(cc_graph *g, HostCSR &h)
-{
-    g->n = h.n;
-    g->arcs = (int64_t)h.col.size();
-    g->weighted = !h.w.empty();
-    RC(upload_csr(g->fw, h.n, h.rp, h.col, h.w));
-    if (h.has_rev) RC(upload_csr(g->rv, h.n, h.rrp, h.rcol, h.rw));
     return CC_OK;
 }
 
@@ -1134,13 +1115,10 @@ int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_
         old_id.swap(d.old_id);
     } else {
         // Directed: sort, merge, G and G^T and the largest strongly connected
-        // component (forward-backward search) on the device; a graph whose
-        // largest component holds no more than half of the nodes is decided
-        // by the host's full decomposition (Tarjan).
+        // component, all on the device.
         DeviceCSR F, R;
-        bool decided = false;
-        rc = build_csr_device_directed(n, m, src, dst, w, keep_component != 0, F, R, &decided);
-        if (rc == CC_OK && decided) {
+        rc = build_csr_device_directed(n, m, src, dst, w, keep_component != 0, F, R);
+        if (rc == CC_OK) {
             rc = adopt_device_csr(g, F);
             if (rc == CC_OK) rc = adopt_device_reverse(g, R);
             old_id.swap(F.old_id);
@@ -1149,12 +1127,6 @@ int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_
             if (d->rp) cudaFree(d->rp);
             if (d->col) cudaFree(d->col);
             if (d->w) cudaFree(d->w);
-        }
-        if (rc == CC_OK && !decided) {
-            HostCSR h;
-            rc = build_host_csr(n, m, src, dst, w, true, keep_component != 0, h);
-            if (rc == CC_OK) rc = finish_graph(g, h);
-            old_id.swap(h.old_id);
         }
     }
     if (rc != CC_OK) {

@@ -197,21 +197,5 @@ int choose_sample_ws(int64_t n, int k, uint64_t seed, int32_t *host_out, void *c
                      unsigned *count, int32_t *dout, cudaStream_t st);
 size_t sample_candidate_bytes();
 
-// Host-built CSR (the "graph to CSR" step).
-struct HostCSR {
-    int64_t n = 0;
-    std::vector<int64_t> rp;
-    std::vector<int32_t> col;
-    std::vector<uint32_t> w;
-    std::vector<int32_t> old_id;
-    bool has_rev = false;
-    std::vector<int64_t> rrp;
-    std::vector<int32_t> rcol;
-    std::vector<uint32_t> rw;
-};
-
-int build_host_csr(int64_t n, int64_t m, const uint32_t *src,
-                   const uint32_t *dst, const uint32_t *w, bool directed,
-                   bool keep_component, HostCSR &out);
 
 }  // namespace ccg

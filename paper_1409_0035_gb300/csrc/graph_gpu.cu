@@ -359,54 +359,249 @@ __global__ void k_swap_keys(const uint64_t *keys, const uint32_t *vals, int64_t 
     }
 }
 
-// Pivot of the forward-backward search: the largest out-degree x in-degree
-// (a node on many paths), ties to the smallest id.  Two passes: the score,
-// then the smallest node holding it.
-__global__ void k_pivot_score(const int64_t *rp, const int64_t *rrp, int64_t n,
-                              unsigned long long *best)
+// ------------------------------------------------- strongly connected parts
+//
+// Largest strongly connected component (round trips need strong
+// connectivity, section 6.1), found on the device.  Every live node
+// carries the label of the part of the graph it lies in; a part holds every
+// strongly connected component it meets.  The parts start as the weakly
+// connected components.  Each round:
+//   trim    a node without an arc from, or without one to, a live node of
+//           its own part is a component by itself;
+//   stats   per part: size, smallest id and a pivot (largest out x in
+//           degree, ties to the smallest id);
+//   prune   a part that cannot hold a component beating the best one found
+//           so far (fewer nodes, or as many with a larger smallest id) dies;
+//   search  forward and backward searches from every pivot, confined to its
+//           part; the nodes reached both ways are the pivot's component, the
+//           rest of the part splits into three new parts (reached forward
+//           only, backward only, neither), each holding whole components.
+// Labels: 2n + root for the weak components, p and n + p for the forward-
+// and backward-only remainders of pivot p (p never pivots again), the
+// remainder reached by neither keeps its label.
+constexpr uint64_t kDeadLab = ~0ull;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned long long best_key(unsigned size, uint32_t min_id)
 {
-    unsigned long long m = 0;
+    return ((unsigned long long)size << 32) | (0xFFFFFFFFull - min_id);
+}
+
+__global__ void k_scc_init(const int32_t *parent, int64_t n, uint64_t *lab, int32_t *comp)
+{
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        m = max(m, (unsigned long long)(rp[v + 1] - rp[v]) *
-                       (unsigned long long)(rrp[v + 1] - rrp[v]));
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t r = (int32_t)v;
+        while (parent[r] != r) r = parent[r];
+        lab[v] = (uint64_t)(2 * n + r);
+        comp[v] = -1;
+    }
+}
+
+// True when some arc of row v (a warp scans it 32 arcs at a time) leads to
+// a node labelled L.
+__device__ __forceinline__ bool row_meets(const int64_t *rp, const int32_t *col,
+                                          const uint64_t *lab, int64_t v, uint64_t L, int lane)
+{
+    const int64_t end = rp[v + 1];
+    for (int64_t e0 = rp[v]; e0 < end; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool hit = e < end && lab[col[e]] == L;
+        if (__any_sync(kFull, hit)) return true;
+    }
+    return false;
+}
+
+// Trim, a warp per node.  Labels change in place while other warps read
+// them: a node seen live or dead either way keeps the decision valid, since
+// a trimmed node is a component of its own.
+__global__ void k_scc_trim(const int64_t *rp, const int32_t *col, const int64_t *rrp,
+                           const int32_t *rcol, int64_t n, uint64_t *lab, int32_t *comp,
+                           unsigned long long *removed, unsigned long long *best)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long cnt = 0, bk = 0;
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n;
+         v += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint64_t L = lab[v];
+        if (L == kDeadLab) continue;
+        if (row_meets(rp, col, lab, v, L, lane) && row_meets(rrp, rcol, lab, v, L, lane))
+            continue;
+        if (lane == 0) {
+            lab[v] = kDeadLab;
+            comp[v] = (int32_t)v;
+            ++cnt;
+            bk = max(bk, best_key(1u, (uint32_t)v));
+        }
+    }
+    if (lane == 0 && cnt) {
+        atomicAdd(removed, cnt);
+        atomicMax(best, bk);
+    }
+}
+
+// Per part: size, smallest id, pivot key (out x in degree << 32 | ~id).
+// Warps whose live lanes share one part reduce first (the common case: one
+// large part).
+__global__ void k_scc_stats(const int64_t *rp, const int64_t *rrp, int64_t n,
+                            const uint64_t *lab, unsigned long long *pk, unsigned *sz,
+                            unsigned *mn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t v = base + lane;
+        const uint64_t L = v < n ? lab[v] : kDeadLab;
+        const bool live = L != kDeadLab;
+        const unsigned bal = __ballot_sync(kFull, live);
+        if (!bal) continue;
+        unsigned long long key = 0;
+        if (live) {
+            const unsigned long long s = (unsigned long long)(rp[v + 1] - rp[v]) *
+                                         (unsigned long long)(rrp[v + 1] - rrp[v]);
+            key = (min(s, 0xFFFFFFFFull) << 32) | (0xFFFFFFFFull - (uint64_t)v);
+        }
+        const uint64_t L0 = __shfl_sync(kFull, L, __ffs(bal) - 1);
+        if (__all_sync(kFull, !live || L == L0)) {
+            unsigned long long k = key;
+            unsigned m = live ? (unsigned)v : kFull;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(best, m);  // one atomic per warp
+            for (int o = 16; o >= 1; o >>= 1) {
+                k = max(k, __shfl_xor_sync(kFull, k, o));
+                m = min(m, __shfl_xor_sync(kFull, m, o));
+            }
+            if (lane == 0) {
+                atomicMax(&pk[L0], k);
+                atomicAdd(&sz[L0], (unsigned)__popc(bal));
+                atomicMin(&mn[L0], m);
+            }
+        } else if (live) {
+            atomicMax(&pk[L], key);
+            atomicAdd(&sz[L], 1u);
+            atomicMin(&mn[L], (unsigned)v);
+        }
+    }
 }
 
-__global__ void k_pivot_pick(const int64_t *rp, const int64_t *rrp, int64_t n,
-                             const unsigned long long *best, unsigned *pick)
+// Prune parts that cannot beat the best component so far; queue the pivots
+// of the others (both searches start from them).
+__global__ void k_scc_seed(int64_t n, uint64_t *lab, const unsigned long long *pk,
+                           const unsigned *sz, const unsigned *mn,
+                           const unsigned long long *best, unsigned *fw, unsigned *bw,
+                           int32_t *q, unsigned long long *qn)
 {
+    const unsigned long long b = *best;
+    const unsigned bs = (unsigned)(b >> 32);
+    const unsigned bm = (unsigned)(0xFFFFFFFFull - (b & 0xFFFFFFFFull));
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        if ((unsigned long long)(rp[v + 1] - rp[v]) * (unsigned long long)(rrp[v + 1] - rrp[v]) ==
-            *best)
-            atomicMin(pick, (unsigned)v);
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t L = lab[v];
+        if (L == kDeadLab) continue;
+        if (sz[L] < bs || (sz[L] == bs && mn[L] > bm)) {
+            lab[v] = kDeadLab;
+            continue;
+        }
+        if ((uint32_t)pk[L] == (uint32_t)(0xFFFFFFFFull - (uint64_t)v)) {
+            fw[v] = 1u;
+            bw[v] = 1u;
+            q[atomicAdd(qn, 1ull)] = (int32_t)v;
+        }
+    }
 }
 
-// One level of a breadth-first search: a warp per frontier node, a lane per
-// arc; the first to reach a node queues it.
-__global__ void k_bfs_step(const int64_t *rp, const int32_t *col, const int32_t *qin,
-                           int64_t nin, int32_t *qout, unsigned long long *nout, unsigned *vis)
+// One level of the confined searches: a warp per queued node, a lane per
+// arc; the first to reach a node of the same part queues it (one queue
+// reservation per warp step).
+__global__ void k_scc_bfs(const int64_t *rp, const int32_t *col, const uint64_t *lab,
+                          const int32_t *qin, int64_t nin, int32_t *qout,
+                          unsigned long long *nout, unsigned *vis)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < nin;
          t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int32_t u = qin[t];
-        for (int64_t e = rp[u] + lane; e < rp[u + 1]; e += 32) {
-            const int32_t v = col[e];
-            if (vis[v] == 0u && atomicExch(&vis[v], 1u) == 0u)
-                qout[atomicAdd(nout, 1ull)] = v;
+        const uint64_t L = lab[u];
+        const int64_t end = rp[u + 1];
+        for (int64_t e0 = rp[u]; e0 < end; e0 += 32) {
+            const int64_t e = e0 + lane;
+            int32_t x = -1;
+            bool push = false;
+            if (e < end) {
+                x = col[e];
+                push = lab[x] == L && vis[x] == 0u && atomicExch(&vis[x], 1u) == 0u;
+            }
+            const unsigned bal = __ballot_sync(kFull, push);
+            if (!bal) continue;
+            unsigned long long at = 0;
+            if (lane == __ffs(bal) - 1) at = atomicAdd(nout, (unsigned long long)__popc(bal));
+            at = __shfl_sync(kFull, at, __ffs(bal) - 1);
+            if (push) qout[at + __popc(bal & ((1u << lane) - 1u))] = x;
         }
     }
 }
 
-__global__ void k_both_flags(const unsigned *fv, const unsigned *bv, int64_t n, uint64_t *flags)
+// Split every searched part: both ways -> the pivot's component (dead),
+// forward only -> label p, backward only -> n + p, neither -> unchanged.
+__global__ void k_scc_split(int64_t n, uint64_t *lab, const unsigned long long *pk,
+                            unsigned *fw, unsigned *bw, int32_t *comp, unsigned *csz,
+                            unsigned *cmn)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t v = base + lane;
+        const uint64_t L = v < n ? lab[v] : kDeadLab;
+        bool in_s = false;
+        uint32_t p = 0;
+        if (L != kDeadLab) {
+            p = (uint32_t)(0xFFFFFFFFull - (pk[L] & 0xFFFFFFFFull));
+            const bool f = fw[v] != 0u, b = bw[v] != 0u;
+            if (f && b) {
+                in_s = true;
+                comp[v] = (int32_t)p;
+                lab[v] = kDeadLab;
+            } else if (f) {
+                lab[v] = p;
+            } else if (b) {
+                lab[v] = (uint64_t)n + p;
+            }
+            if (f) fw[v] = 0u;
+            if (b) bw[v] = 0u;
+        }
+        const unsigned bal = __ballot_sync(kFull, in_s);
+        if (!bal) continue;
+        const uint32_t p0 = __shfl_sync(kFull, p, __ffs(bal) - 1);
+        if (__all_sync(kFull, !in_s || p == p0)) {
+            if (lane == __ffs(bal) - 1) {
+                atomicAdd(&csz[p0], (unsigned)__popc(bal));
+                atomicMin(&cmn[p0], (unsigned)v);  // lowest member lane: smallest id
+            }
+        } else if (in_s) {
+            atomicAdd(&csz[p], 1u);
+            atomicMin(&cmn[p], (unsigned)v);
+        }
+    }
+}
+
+__global__ void k_scc_best(int64_t n, const unsigned *csz, const unsigned *cmn,
+                           unsigned long long *best)
+{
+    unsigned long long k = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (csz[v]) k = max(k, best_key(csz[v], cmn[v]));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) k = max(k, __shfl_xor_sync(kFull, k, o));
+    if ((threadIdx.x & 31) == 0 && k) atomicMax(best, k);
+}
+
+__global__ void k_comp_flags(const int32_t *comp, int64_t n, int32_t c, uint64_t *flags)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        flags[v] = (fv[v] && bv[v]) ? 1 : 0;
+        flags[v] = comp[v] == c ? 1 : 0;
 }
 
 // Kept nodes: new ids, and per kept row the arcs whose head is kept too (a
@@ -760,34 +955,111 @@ static int filter_csr(const int64_t *rp, const int32_t *col, const uint32_t *w, 
     return CC_OK;
 }
 
-// Breadth-first reachability from `root` over (rp, col) into vis (0/1).
-static int reach(const int64_t *rp, const int32_t *col, int64_t n, int32_t root, unsigned *vis,
-                 Buf &q0, Buf &q1, Buf &cnt, cudaStream_t st)
+// Largest strongly connected component (see the kernels above): flags[v] =
+// 1 for its nodes, *kept = its size.  Ties go to the component holding the
+// smallest id.
+static int largest_scc(const int64_t *rp, const int32_t *col, const int64_t *rrp,
+                       const int32_t *rcol, int64_t n, uint64_t *flags, int64_t *kept,
+                       cudaStream_t st)
 {
-    G_CK(cudaMemsetAsync(vis, 0, n * 4, st));
-    const unsigned one = 1u;
-    G_CK(cudaMemcpyAsync(vis + root, &one, 4, cudaMemcpyHostToDevice, st));
-    G_CK(cudaMemcpyAsync(q0.p, &root, 4, cudaMemcpyHostToDevice, st));
-    int32_t *qin = q0.as<int32_t>(), *qout = q1.as<int32_t>();
-    int64_t nin = 1;
-    while (nin > 0) {
-        G_CK(cudaMemsetAsync(cnt.p, 0, 8, st));
-        k_bfs_step<<<gsz(nin * 32), 256, 0, st>>>(rp, col, qin, nin, qout,
-                                                  cnt.as<unsigned long long>(), vis);
-        unsigned long long h = 0;
-        G_CK(cudaMemcpyAsync(&h, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+    Buf parent, lab, comp, fw, bw, qp, q0, q1, pk, sz, mn, csz, cmn, ctr;
+    const int64_t nl = 3 * n;  // label space
+    G_RC(parent.alloc(n * 4));
+    G_RC(lab.alloc(n * 8));
+    G_RC(comp.alloc(n * 4));
+    G_RC(fw.alloc(n * 4));
+    G_RC(bw.alloc(n * 4));
+    G_RC(qp.alloc(n * 4));
+    G_RC(q0.alloc(n * 4));
+    G_RC(q1.alloc(n * 4));
+    G_RC(pk.alloc(nl * 8));
+    G_RC(sz.alloc(nl * 4));
+    G_RC(mn.alloc(nl * 4));
+    G_RC(csz.alloc(n * 4));
+    G_RC(cmn.alloc(n * 4));
+    G_RC(ctr.alloc(3 * 8));  // best, removed, queue count
+    unsigned long long *best = ctr.as<unsigned long long>(), *removed = best + 1,
+                       *qn = best + 2;
+    // weak components by union-find over the arcs of G and of G^T
+    k_iota32<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n);
+    k_hook<<<gsz(n * 32), 256, 0, st>>>(rp, col, n, parent.as<int32_t>());
+    k_hook<<<gsz(n * 32), 256, 0, st>>>(rrp, rcol, n, parent.as<int32_t>());
+    k_scc_init<<<gsz(n), 256, 0, st>>>(parent.as<int32_t>(), n, lab.as<uint64_t>(),
+                                       comp.as<int32_t>());
+    G_CK(cudaMemsetAsync(fw.p, 0, n * 4, st));
+    G_CK(cudaMemsetAsync(bw.p, 0, n * 4, st));
+    G_CK(cudaMemsetAsync(csz.p, 0, n * 4, st));
+    G_CK(cudaMemsetAsync(cmn.p, 0xFF, n * 4, st));
+    G_CK(cudaMemsetAsync(best, 0, 8, st));
+    uint64_t *L = lab.as<uint64_t>();
+    for (;;) {
+        // trim while it removes nodes (at most 16 sweeps a round; the
+        // searches settle whatever is left)
+        for (int it = 0; it < 16; ++it) {
+            G_CK(cudaMemsetAsync(removed, 0, 8, st));
+            k_scc_trim<<<gsz(n * 32), 256, 0, st>>>(rp, col, rrp, rcol, n, L,
+                                                    comp.as<int32_t>(), removed, best);
+            unsigned long long h = 0;
+            G_CK(cudaMemcpyAsync(&h, removed, 8, cudaMemcpyDeviceToHost, st));
+            G_CK(cudaStreamSynchronize(st));
+            if (h == 0) break;
+        }
+        G_CK(cudaMemsetAsync(pk.p, 0, nl * 8, st));
+        G_CK(cudaMemsetAsync(sz.p, 0, nl * 4, st));
+        G_CK(cudaMemsetAsync(mn.p, 0xFF, nl * 4, st));
+        G_CK(cudaMemsetAsync(qn, 0, 8, st));
+        k_scc_stats<<<gsz(n), 256, 0, st>>>(rp, rrp, n, L, pk.as<unsigned long long>(),
+                                            sz.as<unsigned>(), mn.as<unsigned>());
+        k_scc_seed<<<gsz(n), 256, 0, st>>>(n, L, pk.as<unsigned long long>(), sz.as<unsigned>(),
+                                           mn.as<unsigned>(), best, fw.as<unsigned>(),
+                                           bw.as<unsigned>(), qp.as<int32_t>(), qn);
+        unsigned long long npiv = 0;
+        G_CK(cudaMemcpyAsync(&npiv, qn, 8, cudaMemcpyDeviceToHost, st));
         G_CK(cudaStreamSynchronize(st));
-        nin = (int64_t)h;
-        std::swap(qin, qout);
+        if (npiv == 0) break;  // every part settled or pruned
+        for (int dir = 0; dir < 2; ++dir) {
+            const int64_t *r = dir ? rrp : rp;
+            const int32_t *c = dir ? rcol : col;
+            unsigned *vis = dir ? bw.as<unsigned>() : fw.as<unsigned>();
+            int32_t *qin = q0.as<int32_t>(), *qout = q1.as<int32_t>();
+            G_CK(cudaMemcpyAsync(qin, qp.p, npiv * 4, cudaMemcpyDeviceToDevice, st));
+            int64_t nin = (int64_t)npiv;
+            while (nin > 0) {
+                G_CK(cudaMemsetAsync(qn, 0, 8, st));
+                k_scc_bfs<<<gsz(nin * 32), 256, 0, st>>>(r, c, L, qin, nin, qout, qn, vis);
+                unsigned long long h = 0;
+                G_CK(cudaMemcpyAsync(&h, qn, 8, cudaMemcpyDeviceToHost, st));
+                G_CK(cudaStreamSynchronize(st));
+                nin = (int64_t)h;
+                std::swap(qin, qout);
+            }
+        }
+        k_scc_split<<<gsz(n), 256, 0, st>>>(n, L, pk.as<unsigned long long>(), fw.as<unsigned>(),
+                                            bw.as<unsigned>(), comp.as<int32_t>(),
+                                            csz.as<unsigned>(), cmn.as<unsigned>());
+        k_scc_best<<<gsz(n), 256, 0, st>>>(n, csz.as<unsigned>(), cmn.as<unsigned>(), best);
     }
+    unsigned long long hb = 0;
+    G_CK(cudaMemcpyAsync(&hb, best, 8, cudaMemcpyDeviceToHost, st));
+    G_CK(cudaStreamSynchronize(st));
+    const int64_t size = (int64_t)(hb >> 32);
+    const int64_t min_id = (int64_t)(0xFFFFFFFFull - (hb & 0xFFFFFFFFull));
+    if (size < 2 || min_id >= n) {
+        *kept = size;
+        return CC_OK;
+    }
+    int32_t c = -1;
+    G_CK(cudaMemcpyAsync(&c, comp.as<int32_t>() + min_id, 4, cudaMemcpyDeviceToHost, st));
+    G_CK(cudaStreamSynchronize(st));
+    k_comp_flags<<<gsz(n), 256, 0, st>>>(comp.as<int32_t>(), n, c, flags);
+    *kept = size;
     return CC_OK;
 }
 
 int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *h_src, const uint32_t *h_dst,
                               const uint32_t *h_w, bool keep_component, DeviceCSR &F,
-                              DeviceCSR &R, bool *decided)
+                              DeviceCSR &R)
 {
-    *decided = false;
     if (n < 2 || m < 0 || (m > 0 && (!h_src || !h_dst))) return CC_ERR_ARG;
     if (n > 0x7FFFFFFFLL || m > 0x7FFFFFFFLL) return CC_ERR_TOO_LARGE;
     cudaStream_t st = 0;
@@ -854,10 +1126,8 @@ int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *h_src, const
     const uint64_t *rks = (A2 > 0 && in_tmp) ? ko : ks;
     const uint32_t *rvs = (A2 > 0 && in_tmp) ? vo : vs;
     G_RC(csr_from_sorted(rks, rvs, (int64_t)A2, n, b, h_w != nullptr, rrp, rcol, rw, st));
-    // 3. largest strongly connected component: the forward-backward search
-    //    from a pivot gives the pivot's component; holding more than half of
-    //    the nodes, it is the largest.  Otherwise the caller decides on the
-    //    host.
+    // 3. the largest strongly connected component (largest_scc), unless
+    //    every node is kept
     if (!keep_component) {
         std::vector<int32_t> ids(n);
         for (int64_t v = 0; v < n; ++v) ids[v] = (int32_t)v;
@@ -871,36 +1141,15 @@ int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *h_src, const
         std::swap(R.rp, rrp.p); std::swap(R.col, rcol.p); if (h_w) std::swap(R.w, rw.p);
         G_CK(cudaMemcpy(F.rp_host.data(), F.rp, (n + 1) * 8, cudaMemcpyDeviceToHost));
         G_CK(cudaMemcpy(R.rp_host.data(), R.rp, (n + 1) * 8, cudaMemcpyDeviceToHost));
-        *decided = true;
         return CC_OK;
     }
-    Buf best, pick, fvis, bvis, q0, q1, cnt;
-    G_RC(best.alloc(8));
-    G_RC(pick.alloc(4));
-    G_CK(cudaMemset(best.p, 0, 8));
-    G_CK(cudaMemset(pick.p, 0xFF, 4));
-    k_pivot_score<<<gsz(n), 256, 0, st>>>(frp.as<int64_t>(), rrp.as<int64_t>(), n,
-                                          best.as<unsigned long long>());
-    k_pivot_pick<<<gsz(n), 256, 0, st>>>(frp.as<int64_t>(), rrp.as<int64_t>(), n,
-                                         best.as<unsigned long long>(), pick.as<unsigned>());
-    unsigned piv = 0;
-    G_CK(cudaMemcpy(&piv, pick.p, 4, cudaMemcpyDeviceToHost));
-    G_RC(fvis.alloc(n * 4));
-    G_RC(bvis.alloc(n * 4));
-    G_RC(q0.alloc(n * 4));
-    G_RC(q1.alloc(n * 4));
-    G_RC(cnt.alloc(8));
-    G_RC(reach(frp.as<int64_t>(), fcol.as<int32_t>(), n, (int32_t)piv, fvis.as<unsigned>(), q0,
-               q1, cnt, st));
-    G_RC(reach(rrp.as<int64_t>(), rcol.as<int32_t>(), n, (int32_t)piv, bvis.as<unsigned>(), q0,
-               q1, cnt, st));
-    k_both_flags<<<gsz(n), 256, 0, st>>>(fvis.as<unsigned>(), bvis.as<unsigned>(), n,
-                                         fl.as<uint64_t>());
+    int64_t nk = 0;
+    G_RC(largest_scc(frp.as<int64_t>(), fcol.as<int32_t>(), rrp.as<int64_t>(),
+                     rcol.as<int32_t>(), n, fl.as<uint64_t>(), &nk, st));
+    if (nk < 2) return CC_ERR_GRAPH;
     uint64_t kept = 0;
     G_RC(scan_u64(fl.as<uint64_t>(), pos.as<uint64_t>(), n, &kept, st));
-    const int64_t nk = (int64_t)kept;
-    if (nk <= n - nk) return CC_OK;  // no majority component: not decided here
-    if (nk < 2) return CC_ERR_GRAPH;
+    if ((int64_t)kept != nk) return CC_ERR_CUDA;  // flags disagree with the component size
     // 4. renumber the kept nodes (increasing original id) and keep the arcs
     //    between them, in G and in G^T
     Buf newid, oldid, newid2, oldid2;
@@ -916,7 +1165,6 @@ int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *h_src, const
     G_CK(cudaMemcpy(F.old_id.data(), oldid.p, nk * 4, cudaMemcpyDeviceToHost));
     R.old_id = F.old_id;
     G_CK(cudaDeviceSynchronize());
-    *decided = true;
     return CC_OK;
 }
 

@@ -18,13 +18,13 @@ int build_csr_device(int64_t n, int64_t m, const uint32_t *src, const uint32_t *
                      const uint32_t *w, bool keep_component, DeviceCSR &out);
 
 // Directed graph to CSR on the device: arcs one way, merged, G in F and G^T
-// in R (same numbering).  With keep_component, the largest strongly
-// connected component is taken when the forward-backward search from the
-// pivot finds one holding more than half of the nodes (then it is the
-// largest); *decided = false otherwise (the caller takes the host path).
+// in R (same numbering).  With keep_component, only the largest strongly
+// connected component (ties to the one holding the smallest id) is kept,
+// found by trimming and forward-backward searches confined to ever smaller
+// parts of the graph.
 int build_csr_device_directed(int64_t n, int64_t m, const uint32_t *src, const uint32_t *dst,
                               const uint32_t *w, bool keep_component, DeviceCSR &F,
-                              DeviceCSR &R, bool *decided);
+                              DeviceCSR &R);
 
 // Exclusive scan of n uint64 values (in -> out, may alias); *total = the sum.
 // Synchronises the stream.

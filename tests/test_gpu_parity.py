@@ -140,13 +140,76 @@ def test_directed_build_device_scc(cc, scale, ef, weighted):
 def test_directed_build_without_majority_component(cc):
     """Two directed 40-cycles joined by a 30-node path: the largest
     components tie (the one holding node 0 wins) and none holds half the
-    nodes, so the full decomposition decides."""
+    nodes."""
     c1 = synth.cycle_edges(40)
     a = np.concatenate([c1[1], c1[1] + 70, np.arange(40, 69, dtype=np.uint32), [39]])
     b = np.concatenate([c1[2], c1[2] + 70, np.arange(41, 70, dtype=np.uint32), [40]])
     a = np.append(a, np.uint32(69))
     b = np.append(b, np.uint32(70))
     _check_directed_build(cc, 110, a.astype(np.uint32), b.astype(np.uint32))
+
+
+@pytest.mark.parametrize("scale,ef,weighted", [(18, 16, False), (18, 8, True), (12, 4, False)])
+def test_directed_build_minority_scc(cc, scale, ef, weighted):
+    """Directed R-MAT with many isolated and one-way nodes: the largest
+    strongly connected component holds well under half of the ids (37-47 %),
+    so the decomposition has to settle every other part first."""
+    n, s, d = synth.rmat_edges(scale, ef, seed=scale + 5)
+    w = synth.random_weights(s.size, 1, 50, seed=6) if weighted else None
+    _check_directed_build(cc, n, s, d, w)
+
+
+def _cat(*pairs):
+    a = np.concatenate([np.asarray(p[0], np.int64) for p in pairs])
+    b = np.concatenate([np.asarray(p[1], np.int64) for p in pairs])
+    return a.astype(np.uint32), b.astype(np.uint32)
+
+
+def _cycle(ids):
+    ids = np.asarray(ids, np.int64)
+    return ids, np.roll(ids, -1)
+
+
+def test_directed_build_pivot_in_small_component(cc):
+    """The node of largest out x in degree sits in a 2-cycle with 200 arcs
+    out to sinks and 200 in from sources, and one arc into a 50-cycle: the
+    first search settles the 2-cycle, the 50-cycle is found in a later
+    round."""
+    hub = ([0, 1], [1, 0])
+    outs = (np.zeros(200), np.arange(300, 500))
+    ins = (np.arange(500, 700), np.zeros(200))
+    link = ([0], [100])
+    a, b = _cat(hub, outs, ins, link, _cycle(np.arange(100, 150)))
+    _check_directed_build(cc, 700, a, b)
+
+
+def test_directed_build_chain_and_ties(cc):
+    """Cycles of sizes 3..12 chained one way (one weak component, ten
+    strong ones) next to separate 12-cycles: the largest size ties between
+    parts and the one holding the smallest id wins; ids interleave so that
+    the winner is not the first part found."""
+    rng = np.random.default_rng(5)
+    ids = rng.permutation(400)
+    parts, at, heads = [], 0, []
+    for size in range(3, 13):
+        cyc = ids[at:at + size]
+        at += size
+        parts.append(_cycle(cyc))
+        heads.append(cyc[0])
+    parts += [(heads[:-1], heads[1:])]                 # chain A -> B -> ...
+    for _ in range(4):                                  # separate 12-cycles
+        parts.append(_cycle(ids[at:at + 12]))
+        at += 12
+    a, b = _cat(*parts)
+    _check_directed_build(cc, 400, a, b)
+
+
+def test_directed_build_acyclic_rejected(cc):
+    """A directed acyclic graph has only one-node components: no graph to
+    keep."""
+    a, b = _cat((np.arange(0, 99), np.arange(1, 100)), (np.zeros(50), np.arange(50, 100)))
+    with pytest.raises(cc.CCError):
+        cc.cc_graph_from_edges(100, a, b, directed=True)
 
 
 def test_directed_build_all_nodes(cc):
