@@ -30,8 +30,8 @@
  *
  * Readings of the paper fixed by this interface:
  *   - eps is the rational eps_num / eps_den with 0 < eps_num <= eps_den;
- *     "distance greater than Delta/eps" is evaluated exactly as
- *     d * eps_num > Delta * eps_den (strictly greater goes to H / HC);
+ *     membership of H and HC (section 2, eq. (4): beyond Delta/eps from the
+ *     pivot) is tested exactly, in integers, as d * eps_num > Delta * eps_den;
  *   - the pivot c(v) is the sampled node at minimum distance, ties to the
  *     smallest sample index; a sampled node is its own pivot;
  *   - every estimator returns the exact S(v) for v in C;
@@ -116,12 +116,13 @@ int cc_graph_copy_csr(cc_graph_t g, int reverse, int64_t *row_ptr,
 
 /* ---- sample ---------------------------------------------------------- */
 /*
- * cc_sample_choose -- uniform sample of k distinct nodes (section 2: "sample
- * k points uniformly at random"; Algorithm 1, first step).  Node v gets the
- * key splitmix64(seed, v) = mix(seed + (v+1) * 0x9E3779B97F4A7C15) with the
- * splitmix64 output function mix (Steele, Lea, Flood 2014); the sample is the
- * k nodes with the smallest (key, v), in that order (bottom-k sampling,
- * uniform without replacement).  sample_out int32[k] (host).  Computed on the
+ * cc_sample_choose -- uniform sample of k distinct nodes (section 2: k
+ * nodes drawn uniformly without replacement; Algorithm 1, first step).
+ * Node v gets the key splitmix64(seed, v) =
+ * mix(seed + (v+1) * 0x9E3779B97F4A7C15) with the splitmix64 output
+ * function mix (Steele, Lea, Flood 2014); the sample is the k nodes with the
+ * smallest (key, v), in that order (bottom-k sampling, uniform without
+ * replacement).  sample_out int32[k] (host).  Computed on the
  * device.  Errors: CC_ERR_ARG (k < 1, k > n or k > CC_MAX_K).
  */
 int cc_sample_choose(cc_graph_t g, int32_t k, uint64_t seed,
@@ -266,7 +267,7 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
 /*
  * cc_reach_estimate -- outbound / inbound estimates of general (not
  * necessarily strongly connected) directed graphs (section 6.2, Algorithm
- * 3).  With the nodes in a seeded random order (increasing splitmix64
+ * 4).  With the nodes in a seeded random order (increasing splitmix64
  * output number v of stream `seed`, ties by id -- the keys of
  * cc_sample_choose), node v's sample is the k nodes of smallest rank among
  * R(v), the nodes other than v that v reaches (inbound != 0: that reach v).
@@ -321,17 +322,24 @@ int cc_sampling_sums_single(cc_graph_t g, const int32_t *sample, int32_t k,
  * of the same computation.
  *   n            nodes; d_row_ptr int64[n+1] and d_col int32[row_ptr[n]] are
  *                a connected undirected graph in device memory (each edge
- *                listed both ways, e.g. as returned by cc_graph_copy_csr);
- *                checked on the device (CC_ERR_GRAPH when malformed)
+ *                listed both ways, e.g. as returned by cc_graph_copy_csr).
+ *                The device checks that the row offsets ascend within the
+ *                arcs, that every column is a node id and that every node
+ *                has as many arcs in as out (CC_ERR_GRAPH otherwise).  The
+ *                last is only a necessary condition of symmetry: a CSR that
+ *                passes it without being symmetric gives undefined results
  *   sample, k    host int32[k], distinct node ids (CC_ERR_ARG otherwise)
  *   outputs      device memory owned by the caller: d_sample_sum uint64[n],
  *                d_pivot int32[n], d_delta uint32[n], d_S_sampled uint64[k]
  *   stream       cudaStream_t or NULL
  * Allocates nothing: all working memory lives in one fixed 32 MiB device
  * array inside the library, present on every GPU that loads the library until
- * the process exits.  Calls that need more -- about 4*n*W*8 + 52*n + 4*k*k +
- * 8192*k bytes with W = ceil(k/64) rounded up to a power of two, or more than
- * 2047 BFS levels -- return CC_ERR_TOO_LARGE before touching the device.
+ * the process exits.  A call that needs more -- about 4*n*W*8 + 52*n +
+ * 4*k*k + 8192*k bytes with W = ceil(k/64) rounded up to a power of two --
+ * returns CC_ERR_TOO_LARGE before touching the device.  A traversal deeper
+ * than 2047 levels (the array's distance histogram) is found only after the
+ * pass: the call then returns CC_ERR_TOO_LARGE with the outputs partly
+ * written and undefined.
  * The first call on a device looks up that array's device address (once per
  * device, with the device current); make that first call before any stream
  * capture.  Every call reuses the array and clears what it needs; calls that

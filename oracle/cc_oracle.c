@@ -249,7 +249,8 @@ static int sample_index(int64_t n, int32_t k, const int32_t *sources,
  * Inputs: table[i*n+v] = d(c_i, v) for a metric (undirected graph distances
  * or round-trip distances); sources[i] = c_i (distinct); eps = a/b, 0<a<=b.
  *
- * Outputs (each may be NULL):
+ * Outputs (each may be NULL; with hyb, s_hat and closeness all NULL the
+ * estimates are skipped):
  *   pivot[v]    c(v) as a sample index (section 2); own index for v in C
  *   delta[v]    Delta(v) = d(v, c(v)); 0 for v in C
  *   sum[v]      sum_i d(c_i, v) (the sampling accumulator, section 3)
@@ -304,10 +305,13 @@ int orc_estimate(int64_t n, int32_t k, const int32_t *sources,
     }
 
     const uint64_t nm1 = (uint64_t)(n - 1);
+    /* Only the first-pass statistics asked for: no estimates. */
+    const int want_est = hyb || s_hat || closeness;
     for (int64_t j = 0; j < n; ++j) {
         uint64_t sj = 0;
         for (int32_t i = 0; i < k; ++i) sj += D(i, j);
         if (sum) sum[j] = sj;
+        if (!want_est) continue;
 
         double est[4];
         uint64_t h6[6] = {0, 0, 0, 0, 0, 0};
@@ -325,7 +329,7 @@ int orc_estimate(int64_t n, int32_t k, const int32_t *sources,
             /* pivoting upper bound: B(c(j)) + Delta(j) -> S(c(j)) + (n-1)Delta. */
             est[2] = (double)((u128)S[p] + (u128)nm1 * Dj);
 
-            /* eq. (4): x is "greater than Delta/eps" iff x*a > Delta*b. */
+            /* eq. (4): x lies beyond Delta/eps iff x*a > Delta*b. */
             const u128 thr = (u128)Dj * eps_b;
             uint64_t Hsum = 0, Hnum = 0;
             for (int64_t w = 0; w < n; ++w) {

@@ -325,6 +325,23 @@ def estimate_from_table(table: np.ndarray, sources, eps=(1, 8)):
     return out
 
 
+def pass1_from_table(table: np.ndarray, sources):
+    """The first-pass statistics of estimate_from_table alone -- pivot,
+    delta, sum, S_samp, delta_cc -- without its estimates (whose H tail
+    costs O(n) per node)."""
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    k, n = table.shape
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    out = dict(pivot=np.empty(n, np.int32), delta=np.empty(n, np.uint32),
+               sum=np.empty(n, np.uint64), S_samp=np.empty(k, np.uint64),
+               delta_cc=np.empty((k, k), np.uint32))
+    rc = _L().orc_estimate(n, k, _p(src), _p(table), 1, 1, _p(out["pivot"]),
+                           _p(out["delta"]), _p(out["sum"]), _p(out["S_samp"]),
+                           _p(out["delta_cc"]), None, None, None)
+    _check(rc, "pass1")
+    return out
+
+
 def estimate(g: Graph, sources, eps=(1, 8), roundtrip=False):
     """dist_table + estimate_from_table."""
     return estimate_from_table(dist_table(g, sources, roundtrip), sources, eps)
@@ -548,7 +565,7 @@ def exact_weighted_S(table_all: np.ndarray, beta):
 
 # --------------------------------------------------------------------------
 # Outbound / inbound estimates for general directed graphs (section 6.2,
-# Algorithm 3)
+# Algorithm 4)
 # --------------------------------------------------------------------------
 #
 # For node v, R(v) = the nodes u != v that v reaches (outbound; inbound: that
@@ -621,7 +638,8 @@ def estimate_node(g: Graph, sources, v: int, eps=(1, 8), roundtrip=False):
     estimate_from_table: pivot = the nearest sampled node, smallest index on
     ties; x beyond when x a > Delta b; eq. (4) with the numerator
     (Hsum + HCsum) |L n C| + LCsum |L| formed exactly and divided once.
-    Returns dict(pivot, delta, sum, s_hat (4 floats))."""
+    Returns dict(pivot, delta, sum, s_hat (4 floats), hyb (the six
+    integers Hsum, Hnum, HCsum, LCsum, LCnum, LCsumSq; zeros for v in C))."""
     assert roundtrip == g.directed
     C = [int(c) for c in sources]
     k, n = len(C), g.n
@@ -632,7 +650,8 @@ def estimate_node(g: Graph, sources, v: int, eps=(1, 8), roundtrip=False):
     total = int(dC.sum())
     if v in sidx:
         Sv = int(dv.sum())
-        return dict(pivot=sidx[v], delta=0, sum=total, s_hat=[float(Sv)] * 4)
+        return dict(pivot=sidx[v], delta=0, sum=total, s_hat=[float(Sv)] * 4,
+                    hyb=[0] * 6)
     i_p = int(np.argmin(dC))                                # first minimum
     delta = int(dC[i_p])
     dp = _metric_from(g, C[i_p], roundtrip)
@@ -649,9 +668,11 @@ def estimate_node(g: Graph, sources, v: int, eps=(1, 8), roundtrip=False):
     HCsum = int(dC[HC].sum())
     LCnum = int((~HC).sum())
     LCsum = int(dC[~HC].sum())
+    LCsumSq = sum(int(x) * int(x) for x in dC[~HC])
     Lnum = (n - 1) - Hnum - int(HC.sum())
     s_hyb = float(Fraction((Hsum + HCsum) * LCnum + LCsum * Lnum, LCnum))
-    return dict(pivot=i_p, delta=delta, sum=total, s_hat=[s_samp, s_piv, s_up, s_hyb])
+    return dict(pivot=i_p, delta=delta, sum=total, s_hat=[s_samp, s_piv, s_up, s_hyb],
+                hyb=[Hsum, Hnum, HCsum, LCsum, LCnum, LCsumSq])
 
 
 def reach_node(g: Graph, order, v: int, k: int, inbound=False):

@@ -70,6 +70,26 @@ __global__ void k_check_csr(int64_t n, const int64_t *rp, const int32_t *col, in
         if (col[e] < 0 || col[e] >= n) atomicExch(err, CC_ERR_GRAPH);
 }
 
+// In-degrees (indeg zeroed by the caller); out-of-range columns are left to
+// k_check_csr's report.
+__global__ void k_in_degree(int64_t n, const int32_t *col, int64_t arcs, int32_t *indeg)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < arcs;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[e];
+        if (c >= 0 && c < n) atomicAdd(&indeg[c], 1);
+    }
+}
+
+// A symmetric CSR has every node's in-degree equal to its out-degree (a
+// necessary condition only: it catches a directed CSR, not every error).
+__global__ void k_degree_match(int64_t n, const int64_t *rp, const int32_t *indeg, int *err)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        if (rp[v + 1] - rp[v] != (int64_t)indeg[v]) atomicExch(err, CC_ERR_GRAPH);
+}
+
 __global__ void k_iota(int32_t *p, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -185,6 +205,10 @@ extern "C" int cc_sampling_pivots_noalloc(int64_t n, const int64_t *d_row_ptr,
 
     NA_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     k_check_csr<<<grid_of(arcs), 256, 0, st>>>(n, d_row_ptr, d_col, arcs, err);
+    // T (the traversal's queue, overwritten by it) holds the in-degrees.
+    NA_CK(cudaMemsetAsync(T, 0, (size_t)n * 4, st));
+    k_in_degree<<<grid_of(arcs), 256, 0, st>>>(n, d_col, arcs, T);
+    k_degree_match<<<grid_of(n), 256, 0, st>>>(n, d_row_ptr, T, err);
     NA_CK(cudaMemcpyAsync(src, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
     run_fill_i32(sidx, n, -1, st);
     k_sidx_checked<<<(k + 255) / 256, 256, 0, st>>>(sidx, src, k, err);

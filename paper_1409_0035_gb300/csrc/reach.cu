@@ -1,5 +1,5 @@
 // Outbound / inbound estimates of general directed graphs (section 6.2,
-// Algorithm 3): for every node v, the k nodes of smallest rank (a seeded
+// Algorithm 4): for every node v, the k nodes of smallest rank (a seeded
 // random order) among those v reaches (outbound) or that reach v (inbound),
 // their distances, and the rank position of the k-th.
 //
@@ -21,7 +21,7 @@
 // its lowest ranks, so the samples equal those of the sequential procedure
 // with this pruning, and the first-arrival levels are exact distances
 // (every node on a shortest path from v to an accepted source is
-// unsaturated).  Algorithm 3 prunes at k nodes other than x, which can stop
+// unsaturated).  Algorithm 4 prunes at k nodes other than x, which can stop
 // a search at a node whose k samples include v and leave v a sample short;
 // the rule above keeps the stated aim, a uniform sample of size k of every
 // reachability set.

@@ -1,5 +1,5 @@
 """GPU parity of the outbound / inbound estimates of general directed graphs
-(section 6.2, Algorithm 3) against the oracle: per node the sample count,
+(section 6.2, Algorithm 4) against the oracle: per node the sample count,
 the sum of the sample's distances and the rank position T bit-exact, the
 average distance and the size estimate within 1e-12 relative.  Covers graphs
 with many small and a few large reachability sets (directed R-MAT without

@@ -445,8 +445,12 @@ def test_single_node_estimate_equals_table(gen, w, k, eps):
         r = orc.estimate_node(g, C, v, eps)
         assert r["pivot"] == ref["pivot"][v] and r["delta"] == ref["delta"][v]
         assert r["sum"] == int(ref["sum"][v])
+        assert r["hyb"] == [int(x) for x in ref["hyb"][v]], v
         for e in range(4):
             assert r["s_hat"][e] == ref["s_hat"][e][v], (v, e)
+    p1 = orc.pass1_from_table(orc.dist_table(g, C), C)
+    for key in ("pivot", "delta", "sum", "S_samp", "delta_cc"):
+        assert (p1[key] == ref[key]).all(), key
 
 
 @pytest.mark.parametrize("w", [None, "w"])
@@ -462,5 +466,6 @@ def test_single_node_round_trip_equals_table(w):
         r = orc.estimate_node(g, C, v, (1, 3), roundtrip=True)
         assert r["pivot"] == ref["pivot"][v] and r["delta"] == ref["delta"][v]
         assert r["sum"] == int(ref["sum"][v])
+        assert r["hyb"] == [int(x) for x in ref["hyb"][v]], v
         for e in range(4):
             assert r["s_hat"][e] == ref["s_hat"][e][v], (v, e)

@@ -1,5 +1,5 @@
 """Pins of the oracle's outbound / inbound estimates for general directed
-graphs (section 6.2, Algorithm 3): the average distance to a bottom-k sample
+graphs (section 6.2, Algorithm 4): the average distance to a bottom-k sample
 of each node's reachability set and the bottom-k estimate of its size.
 
 The pins: closed forms on a directed path and a cycle; over every order of
@@ -103,7 +103,7 @@ def test_inbound_is_outbound_of_the_reversed_graph():
 
 
 def _pruned_searches(g, order, k):
-    """Algorithm 3's procedure: BFS from each node in rank order on the
+    """Algorithm 4's procedure: BFS from each node in rank order on the
     reversed graph, pruned at saturated nodes, with the mark rule for T.
     The pruning counts the searches that reached a node including its own
     and prunes at k + 1: then a node x it stops at holds k + 1 nodes of

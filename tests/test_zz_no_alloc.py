@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import oracle as orc
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,48 @@ def test_no_alloc_matches_estimate_twice(cc, scale, k, seed):
             assert (got["S"].view(np.uint64) == want["S_samp"]).all()
     finally:
         cc.cc_graph_free(g)
+    # and against the oracle's running-state pass on its own CSR of the graph
+    og = orc.csr_from_edges(n0, s, d)
+    assert (og.row_ptr == rp).all() and (og.col == col).all()
+    ref = orc.streaming_pass(og, C)
+    assert (got["sum"].view(np.uint64) == ref["sum"]).all()
+    assert (got["pivot"] == ref["pivot"]).all()
+    assert (got["delta"].view(np.uint32) == ref["delta"]).all()
+    assert (got["S"].view(np.uint64) == ref["S_samp"]).all()
+
+
+def test_no_alloc_level_limit_then_normal_call(cc):
+    """A path of 2100 nodes sampled at one end needs 2099 levels, more than
+    the fixed distance histogram holds: the call reports CC_ERR_TOO_LARGE
+    (after the pass), and the array it left behind does not disturb the
+    next, normal call."""
+    import torch
+    n, s, d = synth.path_edges(2100)
+    og = orc.csr_from_edges(n, s, d)
+    rc, _ = _run(cc, torch, og.n, og.row_ptr, og.col, np.array([0, 1], np.int32))
+    assert rc == cc.CC_ERR_TOO_LARGE
+    n0, s, d = synth.rmat_edges(11, 8, seed=4)
+    og = orc.csr_from_edges(n0, s, d)
+    C = orc.choose_sample(og.n, 100, 9)
+    rc, got = _run(cc, torch, og.n, og.row_ptr, og.col, C)
+    assert rc == cc.CC_OK, cc.cc_strerror(rc)
+    ref = orc.streaming_pass(og, C)
+    assert (got["sum"].view(np.uint64) == ref["sum"]).all()
+    assert (got["pivot"] == ref["pivot"]).all()
+    assert (got["delta"].view(np.uint32) == ref["delta"]).all()
+    assert (got["S"].view(np.uint64) == ref["S_samp"]).all()
+
+
+def test_no_alloc_rejects_one_way_csr(cc):
+    """A directed cycle (every arc one way) has in-degree 1 and out-degree 1
+    everywhere -- passes the degree check -- so a one-way path is used: its
+    first node has an arc out and none in."""
+    import torch
+    n = 50
+    rp = np.concatenate([np.arange(n, dtype=np.int64), [n - 1]])
+    col = np.arange(1, n, dtype=np.int32)
+    rc, _ = _run(cc, torch, n, rp, col, np.array([0, 7], np.int32))
+    assert rc == cc.CC_ERR_GRAPH
 
 
 def test_no_alloc_refuses_sizes_beyond_its_array(cc):
