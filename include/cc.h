@@ -449,6 +449,26 @@ int cc_server_free(cc_server_t s);
  * Results do not depend on it, only the time. */
 int cc_set_tuning(cc_graph_t g, int32_t alpha);
 
+/* Parameters of a graph's estimates (cc_set_param); results never depend
+ * on them, only the time.
+ *   CC_PARAM_ALPHA            the direction switch of cc_set_tuning (0:
+ *                             default)
+ *   CC_PARAM_HYBRID_ONE_PASS  1 (default): the bit-packed path classifies
+ *                             each arriving bit for the hybrid during the
+ *                             first pass -- by the triangle inequality,
+ *                             d(c(v), c_i) lies within d(c_i, v) -+ Delta(v)
+ *                             (section 3) -- keeping only the undecided
+ *                             ones (a byte per node and source) to resolve
+ *                             once the distances between sampled nodes are
+ *                             known, so no second traversal runs unless a
+ *                             band offset exceeds a byte, the error estimate
+ *                             is asked for, or the rows do not fit a third
+ *                             of the free memory; 0: always the two-pass
+ *                             form */
+#define CC_PARAM_ALPHA 0
+#define CC_PARAM_HYBRID_ONE_PASS 1
+int cc_set_param(cc_graph_t g, int32_t param, int32_t value);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Counters of the last traversal pass run on g: levels, top-down and
  * bottom-up levels, CSR entries examined and frontier words gathered.

@@ -34,7 +34,7 @@ EXPORTS = (
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
-    "cc_set_tuning", "cc_batch_create", "cc_batch_run", "cc_batch_result",
+    "cc_set_tuning", "cc_set_param", "cc_batch_create", "cc_batch_run", "cc_batch_result",
     "cc_batch_info", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
@@ -106,6 +106,7 @@ def lib():
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
         L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
         L.cc_set_tuning.argtypes = [P, i32]
+        L.cc_set_param.argtypes = [P, i32, i32]
         L.cc_batch_create.argtypes = [i32, P, P, P, P, P, i32, P]
         L.cc_batch_run.argtypes = [P, P]
         L.cc_batch_result.argtypes = [P, i32, P, i32]
@@ -368,6 +369,13 @@ def cc_last_pass_phases(g):
 
 def cc_set_tuning(g, alpha=0):
     _chk(lib().cc_set_tuning(g, int(alpha)), "cc_set_tuning")
+
+
+CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS = 0, 1
+
+
+def cc_set_param(g, param, value):
+    _chk(lib().cc_set_param(g, int(param), int(value)), "cc_set_param")
 
 
 def cc_last_pass_trace(g, max_levels=64):

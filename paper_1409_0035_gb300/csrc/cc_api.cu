@@ -85,7 +85,7 @@ struct cc_graph {
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
         distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp, AT0, AT1, ATa0,
-        ATa1;
+        ATa1, band, bflag, gate2;
     // error estimate of the hybrid (SqErrEst): squared errors, fallback
     // distances, per-node flags, farthest-sample table, staged output
     DevBuf hcse, fdist, sqflag, istar, sqe;
@@ -107,6 +107,7 @@ struct cc_graph {
     bool resident = false; // its distance rows are all kept (chunk c at c * n * cw)
     int64_t dist_max = 0;  // largest distance seen by the last estimate
     int alpha = 0;  // traversal tuning (0: default_alpha)
+    bool band_off = false;  // CC_PARAM_HYBRID_ONE_PASS = 0: always two passes
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
     bool borrowed = false;  // CSR buffers belong to another handle
     int hist_cap = 0;
@@ -433,7 +434,7 @@ void free_graph(cc_graph *g)
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
                      &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
-                     &g->ATa0, &g->ATa1,
+                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
@@ -472,7 +473,9 @@ int prepare_sq(cc_graph *g, int k, cudaStream_t st)
 
 // First pass of the bit-packed path: sums, pivots, Delta, delta_cc, the
 // per-source level histogram and the exact S of the sampled nodes.
-int bfs_pass1(cc_graph *g, int k, cudaStream_t st)
+// With eps_a > 0 the pass also classifies each arriving bit for the hybrid
+// of eps = eps_a / eps_b (RED_BAND), so that no second pass is needed.
+int bfs_pass1(cc_graph *g, int k, cudaStream_t st, uint32_t eps_a = 0, uint32_t eps_b = 0)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
@@ -482,6 +485,17 @@ int bfs_pass1(cc_graph *g, int k, cudaStream_t st)
     j.k = k;
     j.sources = g->sources.as<int32_t>();
     j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
+    if (eps_a > 0) {
+        RC(g->band.ensure((size_t)n * 64 * W));
+        RC(g->bflag.ensure((size_t)n));
+        RC(g->lc2.ensure(n * 16));
+        j.red |= RED_BAND;
+        j.band = g->band.as<uint8_t>();
+        j.bflag = g->bflag.as<uint8_t>();
+        j.lc2 = g->lc2.as<uint64_t>();
+        j.eps_a = eps_a;
+        j.eps_b = eps_b;
+    }
     j.pivot = g->pivot.as<int32_t>();
     j.delta = g->delta.as<uint32_t>();
     j.dcc = g->dcc.as<uint32_t>();
@@ -525,7 +539,7 @@ int check_pass1(cc_graph *g, bool hybrid, int k)
 // The hybrid part of the bit-packed path for eps = a/b, after bfs_pass1:
 // H statistics from the histogram tails, thresholds, L-masks and, where
 // needed, the second pass.
-int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
+int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st, bool band = false)
 {
     const int64_t n = g->n;
     const int W = pow2_words(k);
@@ -557,13 +571,27 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
     // node and, for the error estimate, the squared errors over HC(v) or
     // the distance to the farthest sample where HC(v) is empty.  It is
     // queued regardless and exits at once (like the L-mask kernel) when the
-    // preparation counted no such node.
+    // preparation counted no such node.  After a first pass that
+    // classified on arrival, LCsum is complete once the deferred bits are
+    // resolved, and the second pass runs only if a band offset overflowed.
+    const unsigned *gate = g->npartial.as<unsigned>();
+    if (band) {
+        RC(g->gate2.ensure(8));
+        run_band_resolve(n, k, 64 * W, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(),
+                         g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(), g->hp.as<HybPrep>(),
+                         g->bflag.as<uint8_t>(), g->band.as<uint8_t>(),
+                         g->sum2.as<uint64_t>(), g->lc2.as<uint64_t>(),
+                         &g->ctl.as<Ctl>()->band_ovf, g->gate2.as<unsigned>(),
+                         g->npartial.as<unsigned>(), st);
+        g->call_kernels += 2;
+        gate = g->gate2.as<unsigned>();
+    }
     RC(g->Lmask.ensure((size_t)n * W * 8));
     run_lmask(n, W, k, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(), g->dcc.as<uint32_t>(),
-              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), g->npartial.as<unsigned>(), st);
+              g->hp.as<HybPrep>(), g->Lmask.as<uint64_t>(), gate, st);
     g->call_kernels += 1;
     BfsJob j2 = base_job(g, W, g->fw, g->fw);
-    j2.gate = g->npartial.as<unsigned>();
+    j2.gate = gate;
     j2.k = k;
     j2.sources = g->sources.as<int32_t>();
     j2.red = RED_LC;
@@ -582,11 +610,28 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st)
     return queue_pass(g, 1, W, j2, st);
 }
 
+// Whether the first pass can classify the hybrid's bits on arrival: the
+// plain hybrid (not its error estimate, which needs every sampled node's
+// distance) while the band rows (64W bytes per node) fit in a third of the
+// free device memory.
+bool use_band(cc_graph *g, int k, const cc_opts *opts)
+{
+    if (!opts->want_hybrid || g->sq || g->band_off) return false;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const double need = (double)g->n * 64.0 * pow2_words(k);
+    return need <= ((double)free_b + (double)g->band.cap) / 3.0;
+}
+
 int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 {
-    RC(bfs_pass1(g, k, st));
+    const bool band = use_band(g, k, opts);
+    RC(bfs_pass1(g, k, st, band ? opts->eps_num : 0, band ? opts->eps_den : 0));
     if (!opts->want_hybrid) return CC_OK;
-    return bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st);
+    return bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st, band);
 }
 
 // One 32-source chunk of shortest paths (forward, and reversed for round
@@ -995,6 +1040,7 @@ int ccg::graph_borrow(cc_graph_t dst, cc_graph_t src)
         c.nL = s.nL; c.nM = s.nM; c.nH = s.nH; c.nHch = s.nHch; c.nT = s.nT;
     }
     dst->alpha = src->alpha;
+    dst->band_off = src->band_off;
     dst->borrowed = true;
     return CC_OK;
 }
@@ -1009,7 +1055,7 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
                           &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
-                     &g->ATa0, &g->ATa1,
+                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
@@ -1212,6 +1258,23 @@ int cc_set_tuning(cc_graph_t g, int32_t alpha)
     if (!g || alpha < 0) return CC_ERR_ARG;
     g->alpha = alpha;
     return CC_OK;
+}
+
+int cc_set_param(cc_graph_t g, int32_t param, int32_t value)
+{
+    if (!g) return CC_ERR_ARG;
+    switch (param) {
+    case CC_PARAM_ALPHA:
+        if (value < 0) return CC_ERR_ARG;
+        g->alpha = value;
+        return CC_OK;
+    case CC_PARAM_HYBRID_ONE_PASS:
+        if (value != 0 && value != 1) return CC_ERR_ARG;
+        g->band_off = value == 0;
+        return CC_OK;
+    default:
+        return CC_ERR_ARG;
+    }
 }
 
 int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,

@@ -40,6 +40,14 @@ enum : uint32_t {
     // (flag 1: not in Lmask; 128-bit {lo, hi}), and fdist[v] = d(c_i, v) for
     // c_i = istar[c(v)] (flag 2: no sampled node beyond the threshold)
     RED_SQ = 64u,
+    // hybrid within the first pass (eps = eps_a / eps_b): a bit arriving at
+    // node v on level l belongs to L(v) when (l + Delta(v)) eps_a <=
+    // Delta(v) eps_b, to HC(v) when (l - Delta(v)) eps_a > Delta(v) eps_b --
+    // lc2[v] += l, l^2 (the complement of L, turned into L's sums after the
+    // pass; valid once bflag[v] & 2) --, and is deferred otherwise: its
+    // level's offset in that band, l + Delta(v) - floor(Delta(v) eps_b /
+    // eps_a), goes to band[v * 64W + i] (valid once bflag[v] & 1)
+    RED_BAND = 128u,
 };
 
 // Per-level statistics, indexed by level mod 4 (written during level l,
@@ -64,6 +72,7 @@ constexpr int kTraceLevels = 64;
 struct Ctl {
     unsigned long long bar_arrive;  // grid barrier arrivals (see barrier.cuh)
     int err;                // 0 or a CC_ERR_* code
+    int band_ovf;           // RED_BAND: some band offset did not fit a byte
     int levels;             // last level that produced new bits
     long long ninc_final;   // nodes never completed (non-zero: disconnected)
     unsigned long long td_levels, bu_levels;
@@ -136,6 +145,9 @@ struct BfsJob {
     const int32_t *istar;   // RED_SQ: per sample index, the farthest other sample
     uint64_t *hcse;         // RED_SQ: n x 2
     uint32_t *fdist;        // RED_SQ: n
+    uint8_t *band;          // RED_BAND: n x 64W band offsets of deferred bits
+    uint8_t *bflag;         // RED_BAND: n, zeroed by the pass
+    uint32_t eps_a, eps_b;  // RED_BAND: eps
     Ctl *ctl;
     uint64_t timeout_ns;
     int alpha;              // top-down while ef * alpha < eu
@@ -166,15 +178,18 @@ struct GraphView {
 };
 int graph_view(cc_graph_t g, GraphView *v);
 // Default direction switch of the bit-packed traversal (alpha of
-// cc_set_tuning) for W words per node: with one word a top-down push costs
-// about as much as a gathered word, with more the atomic pushes cost more.
-// Direction threshold: top-down while frontier arcs x alpha < arcs of
-// incomplete nodes.  6 for a one-word sample on graphs of mean degree >= 8
-// (R-MAT), 14 otherwise (wider samples; low-degree grids and meshes, whose
-// one-word traversals measured 20 % faster with 14).
+// cc_set_tuning) for W words per node.  Direction threshold: top-down while
+// frontier arcs x alpha < arcs of incomplete nodes.  Measured (device time
+// of one pass): a one-word sample prefers 6 on graphs of mean degree >= 8
+// (R-MAT) and 14 on low-degree grids and meshes (512^2 grid, k = 64: 23 ms
+// against 27 ms at 4); wider samples prefer 14 on R-MAT and 4 on low-degree
+// graphs, whose frontier nodes push in lane groups (1024^2 grid, k = 256:
+// 108 ms against 132 ms at 14; 886^2, k = 512: 160 ms against 183 ms).
 inline int default_alpha(int W, int64_t n, int64_t arcs)
 {
-    return W == 1 && arcs >= 8 * n ? 6 : 14;
+    const bool dense = arcs >= 8 * n;
+    if (W == 1) return dense ? 6 : 14;
+    return dense ? 14 : 4;
 }
 
 // Output number c of the splitmix64 stream `seed` (Steele, Lea and Flood

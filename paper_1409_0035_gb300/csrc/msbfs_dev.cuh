@@ -96,7 +96,7 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         J.vis[vw] = vis | nw;
     }
     int sx = -1;
-    if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC))) sx = J.sidx[v];
+    if (valid && (J.red & (RED_DCC | RED_HIST | RED_LC | RED_BAND))) sx = J.sidx[v];
     int c = __popcll(nw);
     int cL = 0;
     unsigned long long xs = 0;
@@ -139,6 +139,58 @@ __device__ __forceinline__ void tile_reduce(const BfsJob &J, int l, bool valid,
         pv = min(pv, __shfl_xor_sync(FULL, pv, o));
     }
     const bool leader = valid && w == 0;
+    // (l + 1) eps_a <= eps_b puts every bit of level l in L(v) whatever
+    // Delta(v) >= 1: nothing to record (all levels of a small-diameter
+    // graph).
+    if ((J.red & RED_BAND) && valid && sx < 0 && c > 0 &&
+        ((uint64_t)l + 1u) * J.eps_a > J.eps_b) {
+        // The hybrid's classification on arrival (section 3's use of the
+        // triangle inequality): d(c(v), c_i) lies within l -+ Delta(v).  The
+        // class is the same for the W lanes of v (same l and Delta).
+        // lc2 collects the complement of L(v) (the sums over HC(v)), so a
+        // node whose bits all land in L(v) -- every node of a graph of
+        // small diameter -- writes nothing here.
+        const uint64_t Dv = had ? (uint64_t)J.delta[v] : (uint64_t)l;
+        const uint64_t ul = (uint64_t)l;
+        if ((ul - Dv) * J.eps_a > Dv * J.eps_b) {
+            if (leader) {  // in HC(v); bflag bit 2: lc2[v] holds sums
+                const uint8_t f = J.bflag[v];
+                const uint64_t s1 = ul * (uint64_t)c, s2 = ul * ul * (uint64_t)c;
+                if (f & 2) {
+                    J.lc2[2 * (int64_t)v] += s1;
+                    J.lc2[2 * (int64_t)v + 1] += s2;
+                } else {
+                    J.lc2[2 * (int64_t)v] = s1;
+                    J.lc2[2 * (int64_t)v + 1] = s2;
+                    J.bflag[v] = f | 2;
+                }
+            }
+        } else if ((ul + Dv) * J.eps_a > Dv * J.eps_b) {
+            // Deferred: a byte per source, the first such level clearing
+            // the row (each lane its own word's 64 bytes).
+            const uint64_t o = ul + Dv - Dv * J.eps_b / J.eps_a;  // 1 .. 2 Delta
+            uint8_t *row = J.band + (int64_t)v * (64 * W) + 64 * w;
+            const unsigned gmask =
+                W == 32 ? FULL : (((1u << (W & 31)) - 1u) << ((lane / W) * W));
+            const uint8_t f = J.bflag[v];  // bit 1: v's band row is cleared
+            __syncwarp(gmask);               // every lane of v has read it
+            if (!(f & 1)) {
+                uint4 *r4 = reinterpret_cast<uint4 *>(row);
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                r4[0] = z; r4[1] = z; r4[2] = z; r4[3] = z;
+                if (leader) J.bflag[v] = f | 1;
+            }
+            if (o > 255u) {
+                if (leader) J.ctl->band_ovf = 1;
+            } else {
+                uint64_t bb = nw;
+                while (bb) {
+                    row[__ffsll((long long)bb) - 1] = (uint8_t)o;
+                    bb &= bb - 1;
+                }
+            }
+        }
+    }
     if (leader && c > 0) {
         const uint64_t ul = (uint64_t)l;
         if (J.red & RED_SUM) {
@@ -500,6 +552,39 @@ __device__ __forceinline__ void td_push(const BfsJob &J, const int32_t *__restri
     A.words += wl;
 }
 
+// Top-down push of one low-degree frontier node by its lane group: lane w
+// pushes word f (its word w) to the `len` entries of `row`, kUnroll entries
+// per step (the column indices are the same for the group's lanes and load
+// as one broadcast).  Same effect as td_push.
+template <int W>
+__device__ __forceinline__ void td_push_lane(const BfsJob &J, const int32_t *__restrict__ row,
+                                             int len, uint64_t f, int w, LevelCtl *C,
+                                             int32_t *Tout, LaneAcc<W> &A, const Stage &stage)
+{
+    unsigned wl = 0;
+    for (int x = 0; x < len; x += kUnroll) {
+        int vv[kUnroll];
+        load_row<kUnroll>(row, x, len, 1, vv);
+        uint64_t vs[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q)
+            vs[q] = vv[q] >= 0 ? J.vis[(int64_t)vv[q] * W + w] : ~0ull;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            if (vv[q] < 0) continue;
+            const int v = vv[q];
+            wl += 1;
+            const uint64_t nbits = f & ~vs[q];
+            if (!nbits) continue;
+            const uint64_t old =
+                atomicOr((unsigned long long *)&J.nxt[(int64_t)v * W + w], nbits);
+            if (old == 0ull && atomicCAS(&J.tflag[v], 0u, 1u) == 0u)
+                stage_push(stage, v, Tout, &C->tlen);
+        }
+    }
+    A.words += wl;
+}
+
 // One traversal pass of job J on the team (team_rank, team_size); barriers
 // on *bar.  On error (a barrier timed out) the pass returns early with the
 // code in bar->err.
@@ -569,6 +654,8 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     for (int i = tid; i < W * 64; i += kBlock) s_hist[i] = 0;
     if (J.red & RED_LC)
         for (int64_t i = gtid; i < 2 * n; i += gthreads) J.lc2[i] = 0;
+    if (J.red & RED_BAND)
+        for (int64_t v = gtid; v < n; v += gthreads) J.bflag[v] = 0;
     if (J.red & RED_LEVELS)
         for (int64_t i = gtid; i < n * J.dist_ld; i += gthreads) J.dist_out[i] = kInf;
     if (!sync_after(CC_PH_INIT)) return;
@@ -663,14 +750,46 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 qn = ((volatile LevelCtl *)C)->qcnt;
             }
             int32_t *Tout = (Qin == J.T) ? J.Q1 : J.T;
-            // P1: push the frontier words of the queued nodes; when the
-            // graph has chunk tasks, a heavy node's list is pushed by them.
-            for (int64_t t = gwarp; t < qn; t += nwarps) {
-                const int u = Qin[t];
-                const int64_t b = rp[u], e = rp[u + 1];
-                if (J.ntH > 0 && e - b > kMediumMaxDeg) continue;
-                const uint64_t f = Fin[(int64_t)u * W + w];
-                td_push<W>(J, col, f, b, e, C, Tout, A, stage);
+            // P1: push the frontier words of the queued nodes.  Nodes of at
+            // most kLightMaxDeg entries: a lane group each, NPW per warp
+            // (a grid's frontier node has 4 entries: a warp each would leave
+            // most lanes idle and chain one node after another).
+            for (int64_t t0 = gwarp * NPW; t0 < qn; t0 += nwarps * NPW) {
+                const int64_t t = t0 + grp;
+                if (t < qn) {
+                    const int u = Qin[t];
+                    const int64_t b = rp[u], e = rp[u + 1];
+                    if (e - b <= kLightMaxDeg) {
+                        const uint64_t f = Fin[(int64_t)u * W + w];
+                        if (f) td_push_lane<W>(J, col + b, (int)(e - b), f, w, C, Tout, A, stage);
+                    }
+                }
+            }
+            // Larger nodes: a warp tests its queue entries (every nwarps-th,
+            // so that consecutive ones go to different warps) 32 at a time
+            // by ballot and pushes each larger one whole; when the graph has
+            // chunk tasks, a heavy node's list is pushed by them.
+            for (int64_t j0 = 0; gwarp + j0 * nwarps < qn; j0 += 32) {
+                const int64_t t = gwarp + (j0 + lane) * nwarps;
+                int u = 0;
+                int64_t b = 0, e = 0;
+                bool big = false;
+                if (t < qn) {
+                    u = Qin[t];
+                    b = rp[u];
+                    e = rp[u + 1];
+                    big = e - b > kLightMaxDeg && !(J.ntH > 0 && e - b > kMediumMaxDeg);
+                }
+                unsigned m = __ballot_sync(FULL, big);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int uu = __shfl_sync(FULL, u, src);
+                    const int64_t bb = __shfl_sync(FULL, b, src);
+                    const int64_t ee = __shfl_sync(FULL, e, src);
+                    const uint64_t f = Fin[(int64_t)uu * W + w];
+                    td_push<W>(J, col, f, bb, ee, C, Tout, A, stage);
+                }
             }
             // Heavy frontier nodes: the warp's chunk tasks (every nwarps-th)
             // are tested 32 at a time, a lane each, and only those of nodes

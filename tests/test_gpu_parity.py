@@ -431,3 +431,53 @@ def test_exact_weighted_and_roundtrip(cc):
         assert (S == orc.exact_S(og, roundtrip=True)).all()
     finally:
         cc.cc_graph_free(g)
+
+
+ONE_PASS = {
+    "grid": lambda: synth.grid_edges(61, 47),
+    "ws": lambda: synth.watts_strogatz_edges(3000, 6, 0.02, seed=9),
+    "rmat": lambda: synth.rmat_edges(11, 8, seed=5),
+    "path": lambda: synth.path_edges(700),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ONE_PASS))
+@pytest.mark.parametrize("k", [3, 64, 100, 256])
+def test_hybrid_in_first_pass(cc, name, k):
+    """The hybrid classified on arrival (one traversal, deferred bits
+    resolved after it) equals the oracle and the two-pass form, for eps
+    down to 1/sqrt(k) and up to 1; long paths with few sources overflow the
+    byte band and fall back to the second pass, still exact."""
+    n, s, d = ONE_PASS[name]()
+    g, old, og = both(cc, n, s, d)
+    try:
+        k = min(k, og.n)
+        C = orc.choose_sample(og.n, k, 11 + k)
+        for eps in [(1, 1), (1, 2), (2, 7), orc.default_eps(k)]:
+            cc.cc_set_param(g, cc.CC_PARAM_HYBRID_ONE_PASS, 1)
+            r1, want = check_estimate(cc, g, og, C, eps)
+            cc.cc_set_param(g, cc.CC_PARAM_HYBRID_ONE_PASS, 0)
+            o = cc.cc_opts_default(k)
+            o.eps_num, o.eps_den = eps
+            r2 = cc.cc_estimate(g, C, o)
+            for key in ("hyb", "sum", "pivot", "delta"):
+                assert (r1[key] == r2[key]).all(), (eps, key)
+            assert (r1["s_hat"] == r2["s_hat"]).all(), eps
+    finally:
+        cc.cc_graph_free(g)
+
+
+def test_hybrid_in_first_pass_runs_one_traversal(cc):
+    """On a grid, where some L(v) misses sampled nodes, the hybrid needs
+    one traversal launch instead of two."""
+    n, s, d = synth.grid_edges(120, 90)
+    g, _ = cc.cc_graph_from_edges(n, s, d)
+    try:
+        C = cc.cc_sample_choose(g, 128, 4)
+        cc.cc_estimate(g, C)
+        assert cc.cc_last_call_timing(g)[0] == 1
+        cc.cc_set_param(g, cc.CC_PARAM_HYBRID_ONE_PASS, 0)
+        cc.cc_estimate(g, C)
+        assert cc.cc_last_call_timing(g)[0] == 2
+    finally:
+        cc.cc_graph_free(g)
