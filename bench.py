@@ -718,19 +718,40 @@ def run_extra(args):
         b = cc.cc_batch_create(handles, samples, autotune=True)
         ms = _time_steps(lambda: cc.cc_batch_run(b), args.steps, args.warmup, flush)
         info = cc.cc_batch_info(b)
+        plans = [cc.cc_batch_plan(b, i) for i in range(len(handles))]
+        classes = {}
+        for p in plans:
+            classes.setdefault(p["words"], {"graphs": 0, "teams": p["class_teams"],
+                                            "ctas": p["class_ctas"],
+                                            "ctas_per_sm": p["ctas_per_sm"], "alpha": {}})
+            c = classes[p["words"]]
+            c["graphs"] += 1
+            c["alpha"][str(p["alpha"])] = c["alpha"].get(str(p["alpha"]), 0) + 1
         seq = 0.0
         per = []
+        single_src = 0.0
         for g, C, desc in zip(handles, samples, kinds):
             t = _time_steps(lambda: cc.cc_estimate(g, C), 1, 1)
             seq += t
             per.append((t, desc, len(C), cc.cc_last_pass_stats(g)["levels"]))
+        # one source per launch (the traversal alone, no estimates): the
+        # same sources on every graph, timed on a bounded share of them
+        nsrc = 2
+        for g, C in zip(handles, samples):
+            t0 = time.perf_counter()
+            cc.cc_sampling_sums_single(g, C[:nsrc])
+            single_src += (time.perf_counter() - t0) * 1e3 * len(C) / min(nsrc, len(C))
         per.sort(reverse=True)
         by_kind = {}
         for t, desc, k, lv in per:
             by_kind[desc.split()[0]] = by_kind.get(desc.split()[0], 0.0) + t
         line.update(value=work / (ms / 1e3) / 1e9, ms_per_step=ms,
                     sequential={"value": work / (seq / 1e3) / 1e9, "ms": seq},
-                    speedup_vs_sequential=seq / ms, plan=info,
+                    speedup_vs_sequential=seq / ms, plan=info, plan_by_word_width=classes,
+                    single_source_per_launch={
+                        "ms": single_src, "value": work / (single_src / 1e3) / 1e9,
+                        "note": f"{nsrc} sources per graph timed, scaled to its k",
+                        "speedup": single_src / ms},
                     sequential_ms_by_kind=by_kind,
                     slowest=[{"graph": d, "k": k, "levels": lv, "ms": t}
                              for t, d, k, lv in per[:6]],

@@ -362,14 +362,21 @@ typedef struct cc_batch *cc_batch_t;
  *   samples[i]     host int32[ks[i]] distinct node ids of graph i
  *   ks[i]          1 <= k <= 512
  *   eps_num/den    per-graph hybrid eps (NULL: 1/round(sqrt(k)))
- *   autotune       1: time every graph alone once, then choose the team
- *                  count by a cost model and by timing the best plans;
- *                  0: plan from CSR sizes only
- * The run is one cooperative launch covering the GPU: its CTAs form equal
- * teams, each team estimating its graphs one after another with team-wide
- * bounded barriers.  The launch (and its memsets) is captured in a CUDA
- * graph on the first run when the runtime allows it.  Device memory for
- * every graph's state and results is owned by the batch.
+ *   autotune       1: time every graph alone under the direction switches
+ *                  alpha in {default, 2, 4, 8, 14} and keep the fastest per
+ *                  graph; per word-width class, model every team count and
+ *                  two block shapes (the kernel's full residency per SM and
+ *                  half of it) and time the six best plans;
+ *                  0: default alpha, plan from CSR sizes only
+ * The graphs fall into classes by their word width W (1, 2, 4 or 8 64-bit
+ * words per node).  A run is one cooperative launch per class, specialised
+ * for its W and covering the GPU, the classes one after another: the CTAs
+ * of a class form equal teams, each team estimating its graphs one after
+ * another with team-wide bounded barriers.  The hybrid is classified during
+ * the first traversal (as cc_estimate's one-pass form) when the graph's
+ * band rows could be allocated.  The launches (and their memsets) are
+ * captured in a CUDA graph on the first run when the runtime allows it.
+ * Device memory for every graph's state and results is owned by the batch.
  * Errors: CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA.
  */
 int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs,
@@ -387,11 +394,18 @@ int cc_batch_run(cc_batch_t b, void *stream);
 int cc_batch_result(cc_batch_t b, int32_t i, const cc_out *out,
                     int32_t device_outputs);
 
-/* Plan and timing of the last run: team count, CTAs in the launch, device
- * time of the last run in ms (CUDA events around the launch), whether the
- * run replayed a captured CUDA graph.  Any pointer may be NULL. */
+/* Plan and timing of the last run: teams over all classes, CTAs of the
+ * largest class launch, device time of the last run in ms (CUDA events
+ * around the launches), whether the run replayed a captured CUDA graph.
+ * Any pointer may be NULL. */
 int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
                   int32_t *graph_captured);
+
+/* Graph i's place in the plan: its word width, the direction switch it
+ * runs with, its team within its class, the class's team count, CTAs and
+ * resident CTAs per SM.  Any pointer may be NULL. */
+int cc_batch_plan(cc_batch_t b, int32_t i, int32_t *words, int32_t *alpha, int32_t *team,
+                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm);
 
 int cc_batch_free(cc_batch_t b);
 

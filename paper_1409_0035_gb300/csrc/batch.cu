@@ -1,21 +1,26 @@
-// Many graphs, one persistent launch.
+// Many graphs, one persistent launch per word width.
 //
 // A batch holds graphs of uneven size, each with its own sample (k <= 512)
-// and eps.  One cooperative kernel covers the whole GPU; its CTAs are split
-// into teams of equal size and every team works through a list of graphs,
-// running each graph's whole estimate on its own CTAs: sample index, the
-// bit-packed first pass (sums, pivots, Delta, sampled-pair distances, level
-// histogram), the tail tables, the hybrid thresholds, the second pass when
-// some L(v) misses a sampled node, and the FP64 finalisation -- the same
-// device code as the single-graph path, with team-wide bounded barriers
-// (sections 2-3 of the paper, applied to every graph of the batch).
+// and eps.  The graphs fall into classes by their word width W (k sources
+// packed in W 64-bit words per node); each class runs as one cooperative
+// kernel specialised for its W that covers the whole GPU, the classes one
+// after another in the same stream (and in one captured CUDA graph).  A
+// class kernel's CTAs are split into teams of equal size and every team
+// works through a list of graphs, running each graph's whole estimate on
+// its own CTAs: sample index, the bit-packed first pass (sums, pivots,
+// Delta, sampled-pair distances, level histogram, and the hybrid's
+// classification on arrival), the tail tables, the hybrid thresholds, the
+// resolution of the deferred bits (or the second pass when a band offset
+// overflowed), and the FP64 finalisation -- the same device code as the
+// single-graph path, with team-wide bounded barriers (sections 2-3 of the
+// paper, applied to every graph of the batch).
 //
-// The team count and the graph-to-team assignment come from a planner:
-// with autotuning it times every graph once alone (whole GPU), models a
-// graph's time on a team of s CTAs as levels * c + work * G / s, assigns
-// graphs to P teams longest-first for P in {1, 2, ..., 64}, then times every
-// plan for real and keeps the fastest.  The launch and its
-// memsets are captured once in a CUDA graph and replayed on every run.
+// The autotuner (cc_batch_create with autotune = 1) times every graph
+// alone under several direction switches alpha and keeps the fastest per
+// graph; per class it models the time of every team count P on a team of s
+// CTAs as levels * c + work * G / s (graphs longest first onto the least
+// loaded team), for two block shapes (the kernel's full residency and half
+// of it per SM), then times every plan for real and keeps the fastest.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,7 +39,8 @@ namespace {
 constexpr int kBatchMaxW = 8;  // k <= 512
 
 struct BatchJob {
-    BfsJob j;  // pass-1 configuration (pass 2 derived from it)
+    BfsJob j;   // pass 1
+    BfsJob j2;  // pass 2 (the two-pass hybrid): RED_LC over Lmask
     int W, k, want_hybrid;
     uint32_t a, b;
     uint32_t *hist;
@@ -70,18 +76,22 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
     d_scatter_sidx(sidx, B.j.sources, k, gtid, gthreads);
     if (!grid_sync(bar, rank, size, to)) return;
 
-    bfs_pass<W>(B.j, rank, size, bar, s_hist);
-    if (!grid_sync(bar, rank, size, to)) return;
-    volatile Ctl *c1 = B.ctl1;
-    if (c1->ninc_final != 0 || c1->err != 0) {
-        if (gtid == 0) *B.status = c1->err == 1 ? CC_ERR_TOO_LARGE
-                                  : c1->err < 0 ? c1->err
-                                                : CC_ERR_DISCONNECTED;
-        return;
-    }
-    const int D = c1->levels;
-    d_S_sampled(B.hist, D, k, B.j.dcc, B.Ssamp, gtid >> 5, gthreads >> 5);
-    if (B.want_hybrid) {
+    // Pass 1, then (only when the hybrid needs it and the first pass could
+    // not settle every bit) pass 2, from one call site.
+    for (int pass = 0; pass < 2; ++pass) {
+        bfs_pass<W>(pass ? B.j2 : B.j, rank, size, bar, s_hist);
+        if (!grid_sync(bar, rank, size, to)) return;
+        if (pass == 1) break;
+        volatile Ctl *c1 = B.ctl1;
+        if (c1->ninc_final != 0 || c1->err != 0) {
+            if (gtid == 0) *B.status = c1->err == 1 ? CC_ERR_TOO_LARGE
+                                      : c1->err < 0 ? c1->err
+                                                    : CC_ERR_DISCONNECTED;
+            return;
+        }
+        const int D = c1->levels;
+        d_S_sampled(B.hist, D, k, B.j.dcc, B.Ssamp, gtid >> 5, gthreads >> 5);
+        if (!B.want_hybrid) break;
         for (int i = (int)rank; i < k; i += (int)size)
             d_tail_source(B.hist, D, k, B.TN, B.TS, i, D + 1);
         d_maxdelta(B.j.dcc, k, B.maxd, gtid >> 5, gthreads >> 5);
@@ -89,17 +99,16 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
         d_hyb_prep(3, n, k, D, D + 1, B.a, B.b, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.maxd,
                    B.TN, B.TS, B.hp, B.npartial, SqPrep{nullptr}, gtid, gthreads);
         if (!grid_sync(bar, rank, size, to)) return;
-        if (*(volatile unsigned *)B.npartial > 0) {
-            d_lmask(n, W, k, B.j.sidx, B.j.pivot, B.j.dcc, B.hp, B.Lmask, gtid, gthreads);
+        if (*(volatile unsigned *)B.npartial == 0) break;
+        if (B.j.band && !c1->band_ovf) {
+            // classified on arrival: resolve the deferred bits
+            d_band_resolve(n, k, 64 * W, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.hp,
+                           B.j.bflag, B.j.band, B.j.sum2, B.lc2, gtid >> 5, gthreads >> 5);
             if (!grid_sync(bar, rank, size, to)) return;
-            BfsJob j2 = B.j;
-            j2.red = RED_LC;
-            j2.Lmask = B.Lmask;
-            j2.lc2 = B.lc2;
-            j2.ctl = B.ctl2;
-            bfs_pass<W>(j2, rank, size, bar, s_hist);
-            if (!grid_sync(bar, rank, size, to)) return;
+            break;
         }
+        d_lmask(n, W, k, B.j.sidx, B.j.pivot, B.j.dcc, B.hp, B.Lmask, gtid, gthreads);
+        if (!grid_sync(bar, rank, size, to)) return;
     }
     FinalizeArgs fa{};
     fa.n = n;
@@ -123,21 +132,37 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
     if (gtid == 0) *B.status = CC_OK;
 }
 
-__global__ void __launch_bounds__(kBlock, 2)
-batch_kernel(const BatchJob *jobs, const Team *teams, const int *cta_team, const int *order)
+// Resident CTAs per SM the register allocation must allow (as the
+// single-graph traversal kernel).
+#ifndef CC_BATCH_MIN_CTAS
+#define CC_BATCH_MIN_CTAS 4
+#endif
+
+// One word-width class: its teams (cta_team maps a CTA to its team) work
+// through their graphs (order[job_begin .. job_end) of the team).
+template <int W>
+__global__ void __launch_bounds__(kBlock, CC_BATCH_MIN_CTAS)
+    batch_kernel(const BatchJob *jobs, const Team *teams, const int *cta_team, const int *order)
 {
-    extern __shared__ unsigned s_hist[];  // kBatchMaxW * 64 counters
+    extern __shared__ unsigned s_hist[];  // W * 64 counters
     const Team T = teams[cta_team[blockIdx.x]];
     const unsigned rank = blockIdx.x - (unsigned)T.first;
     for (int q = T.job_begin; q < T.job_end; ++q) {
-        const BatchJob &B = jobs[order[q]];
-        switch (B.W) {
-        case 1: run_job<1>(B, rank, (unsigned)T.size, T.bar, s_hist); break;
-        case 2: run_job<2>(B, rank, (unsigned)T.size, T.bar, s_hist); break;
-        case 4: run_job<4>(B, rank, (unsigned)T.size, T.bar, s_hist); break;
-        default: run_job<8>(B, rank, (unsigned)T.size, T.bar, s_hist); break;
-        }
+        run_job<W>(jobs[order[q]], rank, (unsigned)T.size, T.bar, s_hist);
         if (*(volatile int *)&T.bar->err < 0) return;
+    }
+}
+
+constexpr int kClasses = 4;  // W = 1, 2, 4, 8
+constexpr int kClassW[kClasses] = {1, 2, 4, 8};
+
+const void *class_kernel(int c)
+{
+    switch (c) {
+    case 0: return (const void *)batch_kernel<1>;
+    case 1: return (const void *)batch_kernel<2>;
+    case 2: return (const void *)batch_kernel<4>;
+    default: return (const void *)batch_kernel<8>;
     }
 }
 
@@ -155,16 +180,28 @@ struct DBuf {
 
 using namespace ccg;
 
+// The graphs of one word-width class and their plan.
+struct BatchClass {
+    std::vector<int> graphs;  // batch indices
+    int grid = 0;             // CTAs of the class launch
+    int per_sm = 0;           // resident CTAs per SM it uses
+    int max_per_sm = 0;       // the kernel's residency limit
+    int teams = 0;
+    std::vector<int> team_of;  // per graph of the class
+    DBuf dteams, dcta, dorder;
+};
+
 struct cc_batch {
     int ngraphs = 0;
     std::vector<cc_graph_t> graphs;
-    std::vector<int> k, W;
+    std::vector<int> k, W, cls, alpha;
     std::vector<int64_t> n;
     std::vector<std::vector<DBuf>> bufs;  // per graph
     std::vector<BatchJob> hjobs;
-    DBuf djobs, dteams, dcta, dorder, dctl, dstatus;
+    BatchClass classes[kClasses];
+    DBuf djobs, dctl, dstatus;
     size_t ctl_bytes = 0;
-    int grid = 0, teams = 0;
+    int P_max = 64, sms = 0;
     std::vector<double> solo_ms;
     std::vector<int> levels;
     cudaGraph_t graph = nullptr;
@@ -200,82 +237,96 @@ int dalloc(DBuf &b, size_t bytes)
     return CC_OK;
 }
 
-int batch_grid(int *grid)
+// Streaming multiprocessors and each class kernel's resident CTAs per SM.
+int batch_residency(cc_batch *b)
 {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0;
     B_CK(cudaGetDevice(&dev));
-    B_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, kBlock,
-                                                       kBatchMaxW * 64 * sizeof(unsigned)));
-    if (per < 1) return CC_ERR_CUDA;
-    *grid = per * sms;
+    B_CK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int c = 0; c < kClasses; ++c) {
+        int per = 0;
+        B_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, class_kernel(c), kBlock, (size_t)kClassW[c] * 64 * sizeof(unsigned)));
+        if (per < 1) return CC_ERR_CUDA;
+        b->classes[c].max_per_sm = per;
+    }
     return CC_OK;
 }
 
-// Plan: P equal teams, graphs assigned longest-first to the least loaded
-// team under the model t_g(s) = levels_g * c + work_g * G / s.
-double plan(const cc_batch *b, int P, std::vector<int> &team_of)
+// Plan of class c: P equal teams over `grid` CTAs, its graphs assigned
+// longest-first to the least loaded team under the model t_g(s) =
+// levels_g * c + work_g * G / s.  Returns the modelled time.
+double plan(const cc_batch *b, int c, int grid, int P, std::vector<int> &team_of)
 {
+    const BatchClass &K = b->classes[c];
     const double c_level = 0.012;  // ms of fixed cost per level (barriers)
-    const int G = b->grid, s = G / P;
-    std::vector<double> t(b->ngraphs);
-    for (int i = 0; i < b->ngraphs; ++i) {
+    const int full = b->sms * K.max_per_sm;
+    const int s = grid / P;
+    const int ng = (int)K.graphs.size();
+    std::vector<double> t(ng);
+    for (int x = 0; x < ng; ++x) {
+        const int i = K.graphs[x];
         const double fixed = b->levels[i] * c_level;
         const double work = std::max(0.0, b->solo_ms[i] - fixed);
-        t[i] = fixed + work * (double)G / s;
+        t[x] = fixed + work * (double)full / s;
     }
-    std::vector<int> idx(b->ngraphs);
+    std::vector<int> idx(ng);
     std::iota(idx.begin(), idx.end(), 0);
     std::sort(idx.begin(), idx.end(), [&](int x, int y) { return t[x] > t[y]; });
     std::vector<double> load(P, 0.0);
-    team_of.assign(b->ngraphs, 0);
-    for (int i : idx) {
+    team_of.assign(ng, 0);
+    for (int x : idx) {
         const int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        team_of[i] = best;
-        load[best] += t[i];
+        team_of[x] = best;
+        load[best] += t[x];
     }
     return *std::max_element(load.begin(), load.end());
 }
 
-int upload_plan(cc_batch *b, int P, const std::vector<int> &team_of)
+int upload_plan(cc_batch *b, int c, int per_sm, int P, const std::vector<int> &team_of)
 {
-    const int G = b->grid, s = G / P;
+    BatchClass &K = b->classes[c];
+    const int G = b->sms * per_sm, s = G / P;
     std::vector<Team> teams(P);
     std::vector<int> order;
     std::vector<int> cta(G, P - 1);
+    Ctl *bars = reinterpret_cast<Ctl *>(b->dctl.p) + c * b->P_max;
     for (int t = 0; t < P; ++t) {
         teams[t].first = t * s;
         teams[t].size = (t == P - 1) ? G - t * s : s;
         teams[t].job_begin = (int)order.size();
-        for (int i = 0; i < b->ngraphs; ++i)
-            if (team_of[i] == t) order.push_back(i);
+        for (size_t x = 0; x < K.graphs.size(); ++x)
+            if (team_of[x] == t) order.push_back(K.graphs[x]);
         teams[t].job_end = (int)order.size();
-        teams[t].bar = reinterpret_cast<Ctl *>(b->dctl.p) + t;
-        for (int c = teams[t].first; c < teams[t].first + teams[t].size; ++c) cta[c] = t;
+        teams[t].bar = bars + t;
+        for (int q = teams[t].first; q < teams[t].first + teams[t].size; ++q) cta[q] = t;
     }
-    if (b->dteams.p) { cudaFree(b->dteams.p); b->dteams.p = nullptr; }
-    if (b->dcta.p) { cudaFree(b->dcta.p); b->dcta.p = nullptr; }
-    if (b->dorder.p) { cudaFree(b->dorder.p); b->dorder.p = nullptr; }
-    B_RC(dalloc(b->dteams, sizeof(Team) * P));
-    B_RC(dalloc(b->dcta, sizeof(int) * G));
-    B_RC(dalloc(b->dorder, sizeof(int) * std::max(1, (int)order.size())));
-    B_CK(cudaMemcpy(b->dteams.p, teams.data(), sizeof(Team) * P, cudaMemcpyHostToDevice));
-    B_CK(cudaMemcpy(b->dcta.p, cta.data(), sizeof(int) * G, cudaMemcpyHostToDevice));
-    B_CK(cudaMemcpy(b->dorder.p, order.data(), sizeof(int) * order.size(),
+    for (DBuf *d : {&K.dteams, &K.dcta, &K.dorder})
+        if (d->p) { cudaFree(d->p); d->p = nullptr; }
+    B_RC(dalloc(K.dteams, sizeof(Team) * P));
+    B_RC(dalloc(K.dcta, sizeof(int) * G));
+    B_RC(dalloc(K.dorder, sizeof(int) * std::max(1, (int)order.size())));
+    B_CK(cudaMemcpy(K.dteams.p, teams.data(), sizeof(Team) * P, cudaMemcpyHostToDevice));
+    B_CK(cudaMemcpy(K.dcta.p, cta.data(), sizeof(int) * G, cudaMemcpyHostToDevice));
+    B_CK(cudaMemcpy(K.dorder.p, order.data(), sizeof(int) * order.size(),
                     cudaMemcpyHostToDevice));
-    b->teams = P;
+    K.teams = P;
+    K.grid = G;
+    K.per_sm = per_sm;
+    K.team_of = team_of;
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->captured = false;
     return CC_OK;
 }
 
-// Memsets and the launch, in stream order.
-int enqueue(cc_batch *b, cudaStream_t st)
+// Memsets and the class launches (the classes in `mask`), in stream order.
+int enqueue(cc_batch *b, cudaStream_t st, unsigned mask = 0xFu)
 {
     B_CK(cudaMemsetAsync(b->dctl.p, 0, b->ctl_bytes, st));
     B_CK(cudaMemsetAsync(b->dstatus.p, 0xFF, sizeof(int) * b->ngraphs, st));
     for (int i = 0; i < b->ngraphs; ++i) {
+        if (!((mask >> b->cls[i]) & 1u)) continue;
         const BatchJob &J = b->hjobs[i];
         const int64_t n = b->n[i];
         const int k = b->k[i];
@@ -285,13 +336,17 @@ int enqueue(cc_batch *b, cudaStream_t st)
         B_CK(cudaMemsetAsync(J.lc2, 0, n * 16, st));
         B_CK(cudaMemsetAsync(J.npartial, 0, 4, st));
     }
-    void *args[] = {&b->djobs.p, &b->dteams.p, &b->dcta.p, &b->dorder.p};
-    B_CK(cudaLaunchCooperativeKernel((const void *)batch_kernel, dim3(b->grid), dim3(kBlock),
-                                     args, kBatchMaxW * 64 * sizeof(unsigned), st));
+    for (int c = 0; c < kClasses; ++c) {
+        BatchClass &K = b->classes[c];
+        if (K.graphs.empty() || !((mask >> c) & 1u)) continue;
+        void *args[] = {&b->djobs.p, &K.dteams.p, &K.dcta.p, &K.dorder.p};
+        B_CK(cudaLaunchCooperativeKernel(class_kernel(c), dim3(K.grid), dim3(kBlock), args,
+                                         (size_t)kClassW[c] * 64 * sizeof(unsigned), st));
+    }
     return CC_OK;
 }
 
-int run_once(cc_batch *b, cudaStream_t st, bool use_graph)
+int run_once(cc_batch *b, cudaStream_t st, bool use_graph, unsigned mask = 0xFu)
 {
     if (!b->e0) {
         B_CK(cudaEventCreate(&b->e0));
@@ -318,7 +373,7 @@ int run_once(cc_batch *b, cudaStream_t st, bool use_graph)
     if (use_graph && b->captured) {
         B_CK(cudaGraphLaunch(b->exec, st));
     } else {
-        B_RC(enqueue(b, st));
+        B_RC(enqueue(b, st, mask));
     }
     B_CK(cudaEventRecord(b->e1, st));
     B_CK(cudaStreamSynchronize(st));
@@ -326,8 +381,8 @@ int run_once(cc_batch *b, cudaStream_t st, bool use_graph)
     B_CK(cudaEventElapsedTime(&ms, b->e0, b->e1));
     b->last_ms = ms;
     // any barrier error (timeout) of a team
-    std::vector<Ctl> bars(b->teams);
-    B_CK(cudaMemcpy(bars.data(), b->dctl.p, sizeof(Ctl) * b->teams, cudaMemcpyDeviceToHost));
+    std::vector<Ctl> bars((size_t)kClasses * b->P_max);
+    B_CK(cudaMemcpy(bars.data(), b->dctl.p, sizeof(Ctl) * bars.size(), cudaMemcpyDeviceToHost));
     for (const Ctl &c : bars)
         if (c.err < 0) return c.err;
     return CC_OK;
@@ -350,12 +405,11 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
     b->graphs.assign(graphs, graphs + ngraphs);
     b->bufs.resize(ngraphs);
     b->hjobs.resize(ngraphs);
-    B_RC(batch_grid(&b->grid));
-    const int P_max = std::min(64, b->grid);
-    b->ctl_bytes = sizeof(Ctl) * (size_t)(P_max + 2 * ngraphs);
+    B_RC(batch_residency(b));
+    b->ctl_bytes = sizeof(Ctl) * (size_t)(kClasses * b->P_max + 2 * ngraphs);
     B_RC(dalloc(b->dctl, b->ctl_bytes));
     B_RC(dalloc(b->dstatus, sizeof(int) * ngraphs));
-    Ctl *ctl_jobs = reinterpret_cast<Ctl *>(b->dctl.p) + P_max;
+    Ctl *ctl_jobs = reinterpret_cast<Ctl *>(b->dctl.p) + kClasses * b->P_max;
     for (int i = 0; i < ngraphs; ++i) {
         GraphView v;
         B_RC(graph_view(graphs[i], &v));
@@ -379,6 +433,10 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         b->n.push_back(n);
         b->k.push_back(k);
         b->W.push_back(W);
+        const int c = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3;
+        b->cls.push_back(c);
+        b->alpha.push_back(v.alpha);
+        b->classes[c].graphs.push_back(i);
         auto &bf = b->bufs[i];
         bf.resize(40);
         int q = 0;
@@ -423,8 +481,15 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         j.ATa0 = (int4 *)take((size_t)std::max<int64_t>(1, v.nT) * 16);
         j.ATa1 = (int4 *)take((size_t)std::max<int64_t>(1, v.nT) * 16);
         if (!j.ACH0 || !j.ACH1 || !j.AT0 || !j.AT1 || !j.ATa0 || !j.ATa1) return CC_ERR_OOM;
+        // Rows of the hybrid's deferred bits (64W bytes per node) and their
+        // flags; without them the graph takes the two-pass hybrid.
+        j.band = (uint8_t *)take((size_t)n * 64 * W);
+        j.bflag = j.band ? (uint8_t *)take((size_t)n) : nullptr;
+        if (!j.bflag) j.band = nullptr;
         B_CK(cudaMemcpy(p[16], samples[i], (size_t)k * 4, cudaMemcpyHostToDevice));
-        j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
+        j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST | (j.band ? RED_BAND : 0u);
+        j.eps_a = a;
+        j.eps_b = bb;
         j.timeout_ns = 10ull * 1000 * 1000 * 1000;
         j.alpha = v.alpha ? v.alpha : default_alpha(W, j.n, j.arcs);
         j.ctl = ctl_jobs + 2 * i;
@@ -442,6 +507,7 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         J.hp = (HybPrep *)take((size_t)n * sizeof(HybPrep));
         J.Lmask = (uint64_t *)take((size_t)n * W * 8);
         J.lc2 = (uint64_t *)take((size_t)n * 16);
+        j.lc2 = J.lc2;
         J.npartial = (unsigned *)take(4);
         J.shat = (double *)take((size_t)n * 8 * CC_NUM_EST);
         J.clo = (double *)take((size_t)n * 8 * CC_NUM_EST);
@@ -454,17 +520,21 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
         J.ctl1 = ctl_jobs + 2 * i;
         J.ctl2 = ctl_jobs + 2 * i + 1;
         J.status = reinterpret_cast<int *>(b->dstatus.p) + i;
+        J.j2 = j;  // every field of pass 1 set by now
+        J.j2.red = RED_LC;
+        J.j2.Lmask = J.Lmask;
+        J.j2.lc2 = J.lc2;
+        J.j2.ctl = J.ctl2;
         b->hjobs[i] = J;
     }
-    B_RC(dalloc(b->djobs, sizeof(BatchJob) * ngraphs));
-    B_CK(cudaMemcpy(b->djobs.p, b->hjobs.data(), sizeof(BatchJob) * ngraphs,
-                    cudaMemcpyHostToDevice));
 
-    // Cost model inputs: each graph alone on the whole GPU (autotune), or
-    // arcs * W as a proxy.
+    // Cost model inputs: each graph alone on the whole GPU (autotune: under
+    // every direction switch of the candidate list, keeping the fastest),
+    // or arcs * W as a proxy.
     b->solo_ms.assign(ngraphs, 0.0);
     b->levels.assign(ngraphs, 0);
     if (autotune) {
+        const int alphas[] = {0, 2, 4, 8, 14};
         for (int i = 0; i < ngraphs; ++i) {
             cc_opts o;
             cc_opts_default(&o, b->k[i]);
@@ -472,51 +542,80 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
             o.eps_den = b->hjobs[i].b;
             cc_out none;
             std::memset(&none, 0, sizeof(none));
-            B_RC(cc_estimate(graphs[i], samples[i], b->k[i], &o, &none));
-            int32_t nl = 0;
-            double ms = 0, bytes = 0;
-            int32_t kern = 0;
-            cc_last_call_timing(graphs[i], &nl, &ms, &bytes, &kern);
-            int64_t lv = 0;
-            cc_last_pass_stats(graphs[i], &lv, nullptr, nullptr, nullptr, nullptr);
-            b->solo_ms[i] = ms;
-            b->levels[i] = (int)lv;
+            const int keep = b->alpha[i];
+            B_RC(cc_estimate(graphs[i], samples[i], b->k[i], &o, &none));  // warm
+            double best = 1e300;
+            int best_a = 0;
+            int64_t best_lv = 0;
+            for (int al : alphas) {
+                B_RC(cc_set_tuning(graphs[i], al));
+                B_RC(cc_estimate(graphs[i], samples[i], b->k[i], &o, &none));
+                int32_t nl = 0, kern = 0;
+                double ms = 0, bytes = 0;
+                cc_last_call_timing(graphs[i], &nl, &ms, &bytes, &kern);
+                int64_t lv = 0;
+                cc_last_pass_stats(graphs[i], &lv, nullptr, nullptr, nullptr, nullptr);
+                if (ms < best) { best = ms; best_a = al; best_lv = lv; }
+            }
+            B_RC(cc_set_tuning(graphs[i], keep));
+            BfsJob &j = b->hjobs[i].j;
+            b->alpha[i] = best_a ? best_a : default_alpha(b->W[i], j.n, j.arcs);
+            j.alpha = b->alpha[i];
+            b->hjobs[i].j2.alpha = b->alpha[i];
+            b->solo_ms[i] = best;
+            b->levels[i] = (int)best_lv;
         }
     } else {
         for (int i = 0; i < ngraphs; ++i) {
-            GraphView v;
-            graph_view(graphs[i], &v);
-            b->solo_ms[i] = 1e-9 * (double)v.arcs * b->W[i];
+            const BfsJob &j = b->hjobs[i].j;
+            b->alpha[i] = j.alpha;
+            b->solo_ms[i] = 1e-9 * (double)j.arcs * b->W[i];
             b->levels[i] = 8;
         }
     }
-    // Model every team count; with autotuning time every plan for real (the
-    // model cannot tell work-bound from latency-bound graphs, whose level
-    // time does not shrink with more CTAs).
-    std::vector<std::pair<double, int>> cand;
-    for (int P = 1; P <= P_max; P *= 2) {
-        std::vector<int> t;
-        cand.push_back({plan(b, P, t), P});
-    }
-    std::sort(cand.begin(), cand.end());
-    int bestP = cand[0].second;
-    if (autotune) {
-        double best = 1e300;
-        for (size_t c = 0; c < cand.size(); ++c) {
-            std::vector<int> t;
-            plan(b, cand[c].second, t);
-            B_RC(upload_plan(b, cand[c].second, t));
-            double tot = 0;
-            for (int rep = 0; rep < 2; ++rep) {
-                B_RC(run_once(b, 0, false));
-                tot += b->last_ms;
+    B_RC(dalloc(b->djobs, sizeof(BatchJob) * ngraphs));
+    B_CK(cudaMemcpy(b->djobs.p, b->hjobs.data(), sizeof(BatchJob) * ngraphs,
+                    cudaMemcpyHostToDevice));
+    // Per class: every team count P and two block shapes (the kernel's full
+    // residency per SM and half of it) by the model; with autotuning the six
+    // best by the model are timed for real (the model cannot tell
+    // work-bound from latency-bound graphs, whose level time does not
+    // shrink with more CTAs).
+    for (int c = 0; c < kClasses; ++c) {
+        BatchClass &K = b->classes[c];
+        if (K.graphs.empty()) continue;
+        struct Cand { double t; int per, P; };
+        std::vector<Cand> cand;
+        std::vector<int> shapes = {K.max_per_sm};
+        if (K.max_per_sm / 2 >= 1 && K.max_per_sm / 2 != K.max_per_sm)
+            shapes.push_back(K.max_per_sm / 2);
+        for (int per : shapes) {
+            const int G = b->sms * per;
+            for (int P = 1; P <= std::min(b->P_max, G); P *= 2) {
+                std::vector<int> t;
+                cand.push_back({plan(b, c, G, P, t), per, P});
             }
-            if (tot < best) { best = tot; bestP = cand[c].second; }
         }
+        std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.t < y.t; });
+        Cand best = cand[0];
+        if (autotune) {
+            double bt = 1e300;
+            for (size_t q = 0; q < cand.size() && q < 6; ++q) {
+                std::vector<int> t;
+                plan(b, c, b->sms * cand[q].per, cand[q].P, t);
+                B_RC(upload_plan(b, c, cand[q].per, cand[q].P, t));
+                double tot = 0;
+                for (int rep = 0; rep < 2; ++rep) {
+                    B_RC(run_once(b, 0, false, 1u << c));
+                    tot += b->last_ms;
+                }
+                if (tot < bt) { bt = tot; best = cand[q]; }
+            }
+        }
+        std::vector<int> team_of;
+        plan(b, c, b->sms * best.per, best.P, team_of);
+        B_RC(upload_plan(b, c, best.per, best.P, team_of));
     }
-    std::vector<int> team_of;
-    plan(b, bestP, team_of);
-    B_RC(upload_plan(b, bestP, team_of));
     *out = guard.release();
     return CC_OK;
 }
@@ -564,10 +663,31 @@ int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
                   int32_t *graph_captured)
 {
     if (!b) return CC_ERR_ARG;
-    if (teams) *teams = b->teams;
-    if (grid) *grid = b->grid;
+    int t = 0, g = 0;
+    for (const BatchClass &K : b->classes) {
+        t += K.teams;
+        g = std::max(g, K.grid);
+    }
+    if (teams) *teams = t;
+    if (grid) *grid = g;
     if (last_ms) *last_ms = b->last_ms;
     if (graph_captured) *graph_captured = b->captured;
+    return CC_OK;
+}
+
+int cc_batch_plan(cc_batch_t b, int32_t i, int32_t *words, int32_t *alpha, int32_t *team,
+                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm)
+{
+    if (!b || i < 0 || i >= b->ngraphs) return CC_ERR_ARG;
+    const BatchClass &K = b->classes[b->cls[i]];
+    int x = 0;
+    while (x < (int)K.graphs.size() && K.graphs[x] != i) ++x;
+    if (words) *words = b->W[i];
+    if (alpha) *alpha = b->alpha[i];
+    if (team) *team = x < (int)K.team_of.size() ? K.team_of[x] : 0;
+    if (class_teams) *class_teams = K.teams;
+    if (class_ctas) *class_ctas = K.grid;
+    if (ctas_per_sm) *ctas_per_sm = K.per_sm;
     return CC_OK;
 }
 

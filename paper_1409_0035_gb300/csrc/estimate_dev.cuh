@@ -203,6 +203,52 @@ __device__ __forceinline__ void d_lmask(int64_t n, int W, int k, const int32_t *
     }
 }
 
+// After a first pass with RED_BAND, for the nodes whose L(v) misses a
+// sampled node: lc2 holds the sums over the bits settled in HC(v) on
+// arrival (when bflag bit 2 is set); each deferred bit (a lane per source,
+// a warp per node: warp w0, w0 + wstride, ...) whose sampled node lies
+// beyond the threshold from the pivot joins them with its level l = thr -
+// Delta + offset; then LCsum = sum - those and LCsumSq = sumsq - their
+// squares.  Called by whole warps.
+__device__ __forceinline__ void d_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx,
+                                               const int32_t *pivot, const uint32_t *delta,
+                                               const uint32_t *dcc, const HybPrep *hp,
+                                               const uint8_t *bflag, const uint8_t *band,
+                                               const uint64_t *sum2, uint64_t *lc2, int64_t w0,
+                                               int64_t wstride)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = w0; v < n; v += wstride) {
+        if (sidx[v] >= 0 || !(hp[v].LCnum & kPartialBit)) continue;
+        const uint8_t f = bflag[v];
+        uint64_t s = 0, s2 = 0;
+        if (f & 1) {
+            const int p = pivot[v];
+            const uint64_t t = hp[v].thr;
+            const uint64_t base = t - delta[v];
+            const uint8_t *row = band + v * rowb;  // valid: bflag bit 1
+            for (int i = lane; i < k; i += 32) {
+                const uint32_t o = row[i];
+                if (o && dcc[(int64_t)p * k + i] > t) {
+                    const uint64_t l = base + o;
+                    s += l;
+                    s2 += l * l;
+                }
+            }
+#pragma unroll
+            for (int x = 16; x >= 1; x >>= 1) {
+                s += __shfl_xor_sync(0xFFFFFFFFu, s, x);
+                s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, x);
+            }
+        }
+        if (lane == 0) {
+            const uint64_t h1 = (f & 2) ? lc2[2 * v] : 0, h2 = (f & 2) ? lc2[2 * v + 1] : 0;
+            lc2[2 * v] = sum2[2 * v] - h1 - s;
+            lc2[2 * v + 1] = sum2[2 * v + 1] - h2 - s2;
+        }
+    }
+}
+
 __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
                                 int64_t stride)
 {
