@@ -478,9 +478,19 @@ int cc_set_tuning(cc_graph_t g, int32_t alpha);
  *                             band offset exceeds a byte, the error estimate
  *                             is asked for, or the rows do not fit a third
  *                             of the free memory; 0: always the two-pass
- *                             form */
+ *                             form
+ *   CC_PARAM_SSSP_DELTA       bucket width of the shortest-path rounds with
+ *                             arc lengths (delta-stepping with a near and a
+ *                             far queue: labels below the threshold relax
+ *                             in rounds, the others wait until the near
+ *                             queue empties and the threshold moves on);
+ *                             0 restores the default (96 mean arc
+ *                             lengths), a negative value relaxes every
+ *                             label at once (plain label-correcting
+ *                             rounds) */
 #define CC_PARAM_ALPHA 0
 #define CC_PARAM_HYBRID_ONE_PASS 1
+#define CC_PARAM_SSSP_DELTA 2
 int cc_set_param(cc_graph_t g, int32_t param, int32_t value);
 
 /* ---- diagnostics --------------------------------------------------------- */

@@ -372,7 +372,7 @@ def cc_set_tuning(g, alpha=0):
     _chk(lib().cc_set_tuning(g, int(alpha)), "cc_set_tuning")
 
 
-CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS = 0, 1
+CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS, CC_PARAM_SSSP_DELTA = 0, 1, 2
 
 
 def cc_set_param(g, param, value):

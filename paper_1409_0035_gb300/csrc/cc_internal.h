@@ -73,6 +73,8 @@ struct Ctl {
     unsigned long long bar_arrive;  // grid barrier arrivals (see barrier.cuh)
     int err;                // 0 or a CC_ERR_* code
     int band_ovf;           // RED_BAND: some band offset did not fit a byte
+    unsigned far_len[3];    // shortest paths: lengths of the three far queues
+    unsigned long long far_min[3];  // and the smallest label each waits with
     int levels;             // last level that produced new bits
     long long ninc_final;   // nodes never completed (non-zero: disconnected)
     unsigned long long td_levels, bu_levels;

@@ -1,7 +1,8 @@
 // Multi-source shortest paths with uint32 arc lengths, 32 sources at a time
 // (sections 3 and 7: one Dijkstra per sampled node, 32-bit integer arc
 // lengths), and the per-chunk reductions that feed the same estimators as the
-// breadth-first path.
+// breadth-first path.  The rounds relax by buckets of distance (delta-
+// stepping): see mssp_kernel.
 //
 // A chunk holds the tentative distances of up to 32 sources as one 128-byte
 // row per node (dist[v][lane], lane = source within the chunk), so a warp
@@ -38,13 +39,24 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
     Ctl *ctl = J.ctl;
     const unsigned nb = gridDim.x;
     unsigned long long relax = 0;
-    __shared__ int32_t s_buf[kStage];
-    __shared__ unsigned s_cnt, s_base;
+    __shared__ int32_t s_buf[kStage], s_fbuf[kStage];
+    __shared__ unsigned s_cnt, s_base, s_fcnt, s_fbase;
     const Stage stage{s_buf, &s_cnt, &s_base};
-    if (threadIdx.x == 0) s_cnt = 0;
+    const Stage fstage{s_fbuf, &s_fcnt, &s_fbase};
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_fcnt = 0;
+    }
 
+    if (gtid < 3) ctl->far_min[gtid] = ~0ull;
     for (int64_t i = gtid; i < n * kChunkSrc; i += gthreads) J.dist[i] = kInf;
-    for (int64_t v = gtid; v < n; v += gthreads) J.mask[v] = 0u;
+    for (int64_t v = gtid; v < n; v += gthreads) {
+        J.mask[v] = 0u;
+        if (J.delta) {
+            J.nstamp[v] = 0u;
+            J.fstamp[v] = 0u;
+        }
+    }
     if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     if (gtid < J.kc) {
         const int v = J.sources[gtid];
@@ -52,36 +64,83 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
         if (atomicOr(&J.mask[v], 1u << gtid) == 0u) {
             const unsigned p = atomicAdd(&ctl->lev[0].qlen, 1u);
             J.Q0[p] = v;
+            if (J.delta) J.nstamp[v] = 1u;  // queued for round 0
         }
     }
     if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
 
+    // Epoch e fills far queue e % 3; at the advance to e + 1 that queue is
+    // processed as the round's queue and queue (e + 2) % 3, consumed two
+    // advances ago, gets its length cleared for epoch e + 2.
+    const uint64_t delta = J.delta;
+    uint64_t T = delta ? delta : ~0ull;
+    unsigned epoch = 0;
     int r = 0;
     for (;; ++r) {
-        const unsigned qn = ((volatile LevelCtl *)&ctl->lev[r & 3])->qlen;
-        if (qn == 0) break;
-        if (gtid == 0) ((LevelCtl *)&ctl->lev[(r + 2) & 3])->qlen = 0;
+        unsigned qn = ((volatile LevelCtl *)&ctl->lev[r & 3])->qlen;
         const int32_t *Qin = (r & 1) ? J.Q1 : J.Q0;
+        if (qn == 0) {
+            if (!delta) break;
+            const unsigned fn = ((volatile Ctl *)ctl)->far_len[epoch % 3];
+            if (fn == 0) break;
+            Qin = J.far[epoch % 3];
+            qn = fn;
+            // next bucket: at least one step, and on to the one holding the
+            // smallest waiting label (empty buckets are skipped)
+            const unsigned long long fmin = ((volatile Ctl *)ctl)->far_min[epoch % 3];
+            T += delta;
+            if (fmin != ~0ull && fmin >= T) T = (fmin / delta + 1) * delta;
+            epoch += 1;
+            if (gtid == 0) {
+                ctl->far_len[(epoch + 1) % 3] = 0;
+                ctl->far_min[(epoch + 1) % 3] = ~0ull;
+                ctl->td_levels += 1;
+            }
+        }
+        if (gtid == 0) ((LevelCtl *)&ctl->lev[(r + 2) & 3])->qlen = 0;
         int32_t *Qout = (r & 1) ? J.Q0 : J.Q1;
         unsigned *qout_len = &ctl->lev[(r + 1) & 3].qlen;
+        int32_t *Fout = delta ? J.far[epoch % 3] : nullptr;
+        unsigned *fout_len = &ctl->far_len[epoch % 3];
+        const unsigned nst = (unsigned)r + 2u;  // stamp: queued for round r + 1
+        const unsigned fst = epoch + 1u;        // stamp: in this epoch's far queue
         for (int64_t t = gwarp; t < (int64_t)qn; t += nwarps) {
             const int u = Qin[t];
             unsigned m = 0;
             if (lane == 0) m = atomicExch(&J.mask[u], 0u);
             m = __shfl_sync(FULL, m, 0);
-            const bool active = (m >> lane) & 1u;
+            const bool pending = (m >> lane) & 1u;
             // The row may have been lowered by an atomicMin of another SM in
             // this round (that is what set the mask bit): read it from L2,
             // the point where those atomics are performed, not from a
             // possibly stale L1 line.
-            const uint64_t du = active ? __ldcg(J.dist + (int64_t)u * kChunkSrc + lane) : 0ull;
+            const uint64_t du = pending ? __ldcg(J.dist + (int64_t)u * kChunkSrc + lane) : 0ull;
+            // Labels at or beyond the threshold wait in the far queue.
+            const bool active = pending && du < T;
+            const unsigned later = __ballot_sync(FULL, pending && !active);
+            if (later) {
+                unsigned long long lo = pending && !active ? du : ~0ull;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(FULL, lo, o);
+                    lo = y < lo ? y : lo;
+                }
+                if (lane == 0) {
+                    atomicOr(&J.mask[u], later);
+                    atomicMin(&ctl->far_min[epoch % 3], lo);
+                    if (atomicExch(&J.fstamp[u], fst) != fst)
+                        stage_push(fstage, u, Fout, fout_len);
+                }
+            }
+            if (!__any_sync(FULL, active)) continue;
             const int64_t b = J.rp[u], e = J.rp[u + 1];
             for (int64_t x = b; x < e; ++x) {
                 const int v = __ldg(J.col + x);
                 const uint64_t wt = J.w ? (uint64_t)__ldg(J.w + x) : 1ull;
                 bool imp = false;
+                uint64_t nd = 0;
                 if (active) {
-                    const uint64_t nd = du + wt;
+                    nd = du + wt;
                     relax += 1;
                     if (nd >= (uint64_t)kInf) {
                         atomicCAS(&ctl->err, 0, CC_ERR_TOO_LARGE);
@@ -90,12 +149,37 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                         if ((unsigned)nd < *slot) imp = (unsigned)nd < atomicMin(slot, (unsigned)nd);
                     }
                 }
-                const unsigned bits = __ballot_sync(FULL, imp);
-                if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u)
-                    stage_push(stage, v, Qout, qout_len);
+                if (!delta) {
+                    const unsigned bits = __ballot_sync(FULL, imp);
+                    if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u)
+                        stage_push(stage, v, Qout, qout_len);
+                    continue;
+                }
+                const unsigned nbits = __ballot_sync(FULL, imp && nd < T);
+                const unsigned fbits = __ballot_sync(FULL, imp && nd >= T);
+                if (!(nbits | fbits)) continue;
+                unsigned long long lo = imp && nd >= T ? nd : ~0ull;
+                if (fbits) {
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) {
+                        const unsigned long long y = __shfl_xor_sync(FULL, lo, o);
+                        lo = y < lo ? y : lo;
+                    }
+                }
+                if (lane == 0) {
+                    atomicOr(&J.mask[v], nbits | fbits);
+                    if (nbits && atomicExch(&J.nstamp[v], nst) != nst)
+                        stage_push(stage, v, Qout, qout_len);
+                    if (fbits) {
+                        atomicMin(&ctl->far_min[epoch % 3], lo);
+                        if (atomicExch(&J.fstamp[v], fst) != fst)
+                            stage_push(fstage, v, Fout, fout_len);
+                    }
+                }
             }
         }
         stage_flush(stage, Qout, qout_len);
+        if (delta) stage_flush(fstage, Fout, fout_len);
         if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     }
     __shared__ unsigned long long s_rel[kBlock / 32];

@@ -20,6 +20,13 @@ struct SsspJob {
     uint32_t *dist;         // n x 32
     unsigned *mask;         // n
     int32_t *Q0, *Q1;       // n each
+    // Buckets (delta-stepping with a near and a far queue): labels below the
+    // threshold T relax in rounds; labels at or beyond it wait in far queues
+    // until the near queue empties and T grows by delta (0: no buckets, T
+    // infinite).
+    uint64_t delta;
+    int32_t *far[3];        // n each
+    uint32_t *nstamp, *fstamp;  // n each: round / epoch a node was last queued for
     Ctl *ctl;
     uint64_t timeout_ns;
     int max_ctas;           // 0: a whole-GPU launch
