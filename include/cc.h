@@ -422,7 +422,10 @@ typedef struct cc_server *cc_server_t;
  *   hbm_budget    bytes of device memory the running requests may use
  *                 (0: half of the free memory at creation)
  * A submitted request waits, first come first served, until a slot is free
- * and its footprint fits in the budget left by the running ones.
+ * and its footprint fits in the budget left by the running ones.  The first
+ * pass of every completed request stays resident (within the budget, least
+ * recently used evicted first): a later request for the same graph, k and
+ * seed, with any estimator or eps, skips it.
  */
 int cc_server_create(int32_t ngraphs, const cc_graph_t *graphs, int32_t slots,
                      uint64_t hbm_budget, cc_server_t *out);
@@ -450,6 +453,12 @@ int cc_server_result(cc_server_t s, int64_t request_id, double *s_hat,
  * completion) and the largest number of requests that ran at once. */
 int cc_server_stats(cc_server_t s, int64_t *completed, double *p50_ms,
                     double *p99_ms, double *mean_ms, int32_t *peak_running);
+
+/* Resident sampled state: requests that found their (graph, k, seed)
+ * first pass resident (hits) or ran it (misses), the states held and the
+ * device bytes the idle ones hold.  Any pointer may be NULL. */
+int cc_server_cache_stats(cc_server_t s, int64_t *hits, int64_t *misses, int32_t *states,
+                          uint64_t *resident_bytes);
 
 /* Drain the queue, stop the workers and release the server. */
 int cc_server_free(cc_server_t s);

@@ -36,7 +36,8 @@ EXPORTS = (
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
     "cc_set_tuning", "cc_set_param", "cc_batch_create", "cc_batch_run", "cc_batch_result",
     "cc_batch_info", "cc_batch_plan", "cc_batch_free", "cc_server_create", "cc_server_submit",
-    "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_free",
+    "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_cache_stats",
+    "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
     "cc_estimate_adaptive", "cc_graph_set_node_weights", "cc_sample_varopt",
     "cc_estimate_node_weighted", "cc_reach_estimate",
@@ -118,6 +119,7 @@ def lib():
         L.cc_server_wait.argtypes = [P, i64, i32]
         L.cc_server_result.argtypes = [P, i64, P, P, P, P, P, P]
         L.cc_server_stats.argtypes = [P, P, P, P, P, P]
+        L.cc_server_cache_stats.argtypes = [P, P, P, P, P]
         L.cc_server_free.argtypes = [P]
         L.cc_sampling_pivots_noalloc.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.cc_selftest_barrier_timeout.argtypes = [u64]
@@ -522,6 +524,14 @@ def cc_server_stats(s):
                                ctypes.byref(mean), ctypes.byref(pk)), "cc_server_stats")
     return dict(completed=c.value, p50_ms=p50.value, p99_ms=p99.value, mean_ms=mean.value,
                 peak_running=pk.value)
+
+
+def cc_server_cache_stats(s):
+    h, m, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    b = ctypes.c_uint64()
+    _chk(lib().cc_server_cache_stats(s, ctypes.byref(h), ctypes.byref(m), ctypes.byref(n),
+                                     ctypes.byref(b)), "cc_server_cache_stats")
+    return dict(hits=h.value, misses=m.value, states=n.value, resident_bytes=b.value)
 
 
 def cc_server_free(s):

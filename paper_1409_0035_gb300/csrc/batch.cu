@@ -103,7 +103,8 @@ __device__ void run_job(const BatchJob &B, unsigned rank, unsigned size, Ctl *ba
         if (B.j.band && !c1->band_ovf) {
             // classified on arrival: resolve the deferred bits
             d_band_resolve(n, k, 64 * W, B.j.sidx, B.j.pivot, B.j.delta, B.j.dcc, B.hp,
-                           B.j.bflag, B.j.band, B.j.sum2, B.lc2, gtid >> 5, gthreads >> 5);
+                           B.j.bflag, B.j.band, B.j.sum2, B.lc2, B.lc2, gtid >> 5,
+                           gthreads >> 5);
             if (!grid_sync(bar, rank, size, to)) return;
             break;
         }

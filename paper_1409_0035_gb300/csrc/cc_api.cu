@@ -93,7 +93,7 @@ struct cc_graph {
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
         distF, distR, mask, best, dmax, errflag, AL0, AL1, ACH0, ACH1, fstamp, AT0, AT1, ATa0,
-        ATa1, band, bflag, gate2, sp_far0, sp_far1, sp_far2, sp_nst, sp_fst;
+        ATa1, band, bflag, gate2, hc2, sp_far0, sp_far1, sp_far2, sp_nst, sp_fst;
     // error estimate of the hybrid (SqErrEst): squared errors, fallback
     // distances, per-node flags, farthest-sample table, staged output
     DevBuf hcse, fdist, sqflag, istar, sqe;
@@ -117,6 +117,7 @@ struct cc_graph {
     int alpha = 0;  // traversal tuning (0: default_alpha)
     bool band_off = false;  // CC_PARAM_HYBRID_ONE_PASS = 0: always two passes
     int64_t sssp_delta = 0;  // CC_PARAM_SSSP_DELTA (0: kDeltaMult x mean length, < 0: off)
+    uint32_t band_a = 0, band_b = 0;  // eps the last first pass classified for (0: none)
     double w_mean = 0.0;     // mean arc length (weighted graphs)
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
     bool borrowed = false;  // CSR buffers belong to another handle
@@ -444,7 +445,7 @@ void free_graph(cc_graph *g)
                      &g->maxd, &g->sources, &g->npartial, &g->ctl, &g->shat, &g->clo,
                      &g->hyb, &g->ssum, &g->distF, &g->distR, &g->mask, &g->best,
                      &g->dmax, &g->errflag, &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
-                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2, &g->sp_far0, &g->sp_far1, &g->sp_far2, &g->sp_nst, &g->sp_fst,
+                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2, &g->hc2, &g->sp_far0, &g->sp_far1, &g->sp_far2, &g->sp_nst, &g->sp_fst,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
@@ -495,14 +496,16 @@ int bfs_pass1(cc_graph *g, int k, cudaStream_t st, uint32_t eps_a = 0, uint32_t 
     j.k = k;
     j.sources = g->sources.as<int32_t>();
     j.red = RED_SUM | RED_PIVOT | RED_DCC | RED_HIST;
+    g->band_a = eps_a;
+    g->band_b = eps_b;
     if (eps_a > 0) {
         RC(g->band.ensure((size_t)n * 64 * W));
         RC(g->bflag.ensure((size_t)n));
-        RC(g->lc2.ensure(n * 16));
+        RC(g->hc2.ensure(n * 16));
         j.red |= RED_BAND;
         j.band = g->band.as<uint8_t>();
         j.bflag = g->bflag.as<uint8_t>();
-        j.lc2 = g->lc2.as<uint64_t>();
+        j.lc2 = g->hc2.as<uint64_t>();  // the sums over HC(v) settled on arrival
         j.eps_a = eps_a;
         j.eps_b = eps_b;
     }
@@ -590,7 +593,7 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st, bool
         run_band_resolve(n, k, 64 * W, g->sidx.as<int32_t>(), g->pivot.as<int32_t>(),
                          g->delta.as<uint32_t>(), g->dcc.as<uint32_t>(), g->hp.as<HybPrep>(),
                          g->bflag.as<uint8_t>(), g->band.as<uint8_t>(),
-                         g->sum2.as<uint64_t>(), g->lc2.as<uint64_t>(),
+                         g->sum2.as<uint64_t>(), g->hc2.as<uint64_t>(), g->lc2.as<uint64_t>(),
                          &g->ctl.as<Ctl>()->band_ovf, g->gate2.as<unsigned>(),
                          g->npartial.as<unsigned>(), st);
         g->call_kernels += 2;
@@ -1089,7 +1092,7 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
                           &g->npartial, &g->ctl, &g->shat, &g->clo, &g->hyb, &g->ssum,
                           &g->distF, &g->distR, &g->mask, &g->best, &g->dmax, &g->errflag,
                           &g->AL0, &g->AL1, &g->ACH0, &g->ACH1, &g->fstamp, &g->AT0, &g->AT1,
-                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2, &g->sp_far0, &g->sp_far1, &g->sp_far2, &g->sp_nst, &g->sp_fst,
+                     &g->ATa0, &g->ATa1, &g->band, &g->bflag, &g->gate2, &g->hc2, &g->sp_far0, &g->sp_far1, &g->sp_far2, &g->sp_nst, &g->sp_fst,
                      &g->hcse, &g->fdist, &g->sqflag, &g->istar, &g->sqe,
                      &g->ad_est, &g->ad_sq, &g->ad_best, &g->ad_bsq, &g->ad_clo, &g->ad_choice,
                      &g->pt_clo1, &g->pt_est2, &g->pt_clo2, &g->pt_clo0,
@@ -1105,6 +1108,38 @@ size_t ccg::graph_workspace_bytes(cc_graph_t g)
 }
 
 void ccg::graph_set_max_ctas(cc_graph_t g, int c) { g->max_ctas = c; }
+
+// Estimates from the first pass resident in g's workspace (a completed
+// cc_estimate on the same sample and k): the hybrid part for this eps --
+// the deferred bits resolved when that first pass classified for the same
+// eps, the second pass otherwise -- and the finalisation; no first pass.
+int ccg::estimate_resident(cc_graph_t g, int32_t k, const cc_opts *opts, cc_out *out)
+{
+    if (!g || !opts || !out) return CC_ERR_ARG;
+    if (opts->eps_num == 0 || opts->eps_num > opts->eps_den) return CC_ERR_ARG;
+    reset_timing(g);
+    cudaStream_t st = (cudaStream_t)opts->stream;
+    const bool hyb = opts->want_hybrid != 0;
+    g->sq = hyb && out->sq_err != nullptr;
+    const bool chunked = g->weighted || g->directed;
+    int rc = CC_OK;
+    if (hyb) {
+        if (chunked) {
+            rc = chunked_hybrid(g, k, opts->eps_num, opts->eps_den, st);
+        } else {
+            const bool band = !g->sq && g->band_a == opts->eps_num && g->band_b == opts->eps_den;
+            rc = bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st, band);
+        }
+    }
+    if (rc == CC_OK) rc = finish_outputs(g, k, hyb, opts, out, st);  // synchronises
+    if (rc != CC_OK) {
+        cudaStreamSynchronize(st);
+        g->pend = 0;
+        return rc;
+    }
+    return chunked ? CC_OK : settle_passes(g);
+}
+
 
 int ccg::graph_view(cc_graph_t g, GraphView *v)
 {

@@ -208,6 +208,8 @@ __device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t c)
 cc_graph_t graph_new_empty();
 int graph_borrow(cc_graph_t dst, cc_graph_t src);
 size_t graph_workspace_bytes(cc_graph_t g);
+// Estimates from the first pass resident in g's workspace (see cc_api.cu).
+int estimate_resident(cc_graph_t g, int32_t k, const cc_opts *opts, cc_out *out);
 void graph_set_max_ctas(cc_graph_t g, int ctas);
 // Sample choice with caller-provided device buffers (no allocation).
 int choose_sample_ws(int64_t n, int k, uint64_t seed, int32_t *host_out, void *cand,

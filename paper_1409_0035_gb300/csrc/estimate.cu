@@ -75,10 +75,11 @@ __global__ void k_finalize(FinalizeArgs A)
 __global__ void k_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx,
                                const int32_t *pivot, const uint32_t *delta, const uint32_t *dcc,
                                const HybPrep *hp, const uint8_t *bflag, const uint8_t *band,
-                               const uint64_t *sum2, uint64_t *lc2, const int *band_ovf)
+                               const uint64_t *sum2, const uint64_t *hc2, uint64_t *lc2,
+                               const int *band_ovf)
 {
     if (*band_ovf) return;  // the second pass recomputes LCsum
-    d_band_resolve(n, k, rowb, sidx, pivot, delta, dcc, hp, bflag, band, sum2, lc2,
+    d_band_resolve(n, k, rowb, sidx, pivot, delta, dcc, hp, bflag, band, sum2, hc2, lc2,
                    (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
                    ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
@@ -228,11 +229,12 @@ void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivo
 void run_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx, const int32_t *pivot,
                       const uint32_t *delta, const uint32_t *dcc, const HybPrep *hp,
                       const uint8_t *bflag, const uint8_t *band, const uint64_t *sum2,
-                      uint64_t *lc2, const int *band_ovf, unsigned *gate,
+                      const uint64_t *hc2, uint64_t *lc2, const int *band_ovf, unsigned *gate,
                       const unsigned *npartial, cudaStream_t st)
 {
     k_band_resolve<<<grid_for(n * 32, 256), 256, 0, st>>>(n, k, rowb, sidx, pivot, delta, dcc,
-                                                          hp, bflag, band, sum2, lc2, band_ovf);
+                                                          hp, bflag, band, sum2, hc2, lc2,
+                                                          band_ovf);
     k_band_gate<<<1, 1, 0, st>>>(band_ovf, npartial, gate);
 }
 

@@ -84,12 +84,12 @@ void run_lmask(int64_t n, int W, int k, const int32_t *sidx, const int32_t *pivo
 void run_finalize(const FinalizeArgs &a, cudaStream_t st);
 // After a first pass with RED_BAND (rows of rowb bytes) and the hybrid
 // preparation: LCsum / LCsumSq into lc2 from the pass's sums over HC(v)
-// and the deferred bits, and gate[2] of the second pass (zero unless a band
+// (hc2) and the deferred bits, and gate[2] of the second pass (zero unless a band
 // offset overflowed).
 void run_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx, const int32_t *pivot,
                       const uint32_t *delta, const uint32_t *dcc, const HybPrep *hp,
                       const uint8_t *bflag, const uint8_t *band, const uint64_t *sum2,
-                      uint64_t *lc2, const int *band_ovf, unsigned *gate,
+                      const uint64_t *hc2, uint64_t *lc2, const int *band_ovf, unsigned *gate,
                       const unsigned *npartial, cudaStream_t st);
 // Tables of the pivoting estimators for FinalizeArgs (d <= D only).
 void run_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCount D, int64_t tstride,

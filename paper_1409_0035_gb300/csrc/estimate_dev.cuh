@@ -204,18 +204,19 @@ __device__ __forceinline__ void d_lmask(int64_t n, int W, int k, const int32_t *
 }
 
 // After a first pass with RED_BAND, for the nodes whose L(v) misses a
-// sampled node: lc2 holds the sums over the bits settled in HC(v) on
+// sampled node: hc2 holds the sums over the bits settled in HC(v) on
 // arrival (when bflag bit 2 is set); each deferred bit (a lane per source,
 // a warp per node: warp w0, w0 + wstride, ...) whose sampled node lies
 // beyond the threshold from the pivot joins them with its level l = thr -
 // Delta + offset; then LCsum = sum - those and LCsumSq = sumsq - their
-// squares.  Called by whole warps.
+// squares, into lc2 (hc2 may be lc2; apart, the first pass's state stays
+// intact for another eps-independent use).  Called by whole warps.
 __device__ __forceinline__ void d_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx,
                                                const int32_t *pivot, const uint32_t *delta,
                                                const uint32_t *dcc, const HybPrep *hp,
                                                const uint8_t *bflag, const uint8_t *band,
-                                               const uint64_t *sum2, uint64_t *lc2, int64_t w0,
-                                               int64_t wstride)
+                                               const uint64_t *sum2, const uint64_t *hc2,
+                                               uint64_t *lc2, int64_t w0, int64_t wstride)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t v = w0; v < n; v += wstride) {
@@ -242,7 +243,7 @@ __device__ __forceinline__ void d_band_resolve(int64_t n, int k, int rowb, const
             }
         }
         if (lane == 0) {
-            const uint64_t h1 = (f & 2) ? lc2[2 * v] : 0, h2 = (f & 2) ? lc2[2 * v + 1] : 0;
+            const uint64_t h1 = (f & 2) ? hc2[2 * v] : 0, h2 = (f & 2) ? hc2[2 * v + 1] : 0;
             lc2[2 * v] = sum2[2 * v] - h1 - s;
             lc2[2 * v + 1] = sum2[2 * v + 1] - h2 - s2;
         }

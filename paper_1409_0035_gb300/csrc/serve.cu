@@ -4,13 +4,19 @@
 // pivoting upper bound or hybrid -- section 2), k and a sample seed; its
 // answer is every node's estimate.  The server keeps the graphs resident
 // and runs requests with continuous batching: S slots, each a worker thread
-// with its own CUDA stream and its own workspace (a handle that borrows the
-// requested graph's CSR), whose cooperative launches are capped at 1/S of
-// the CTAs the GPU can hold of its least-resident kernel variant, so that
-// the grids of all slots fit on the device together and run concurrently.  A waiting request is admitted, first come first served,
-// as soon as a slot is free and its HBM footprint fits in what the running
-// requests leave of the budget.  Arrival, start and finish times give each
-// request's latency.
+// with its own CUDA stream, whose cooperative launches are capped at 1/S
+// of the CTAs the GPU can hold of its least-resident kernel variant, so
+// that the grids of all slots fit on the device together and run
+// concurrently.  The sampled state of a request -- the workspace holding
+// its first traversal pass (sums, pivots, Delta, distances between sampled
+// nodes, histograms, and for the hybrid the classification on arrival) --
+// stays resident after it, keyed by (graph, k, seed): a later request for
+// the same sample, with any estimator or eps, runs only its own part (the
+// finalisation, the hybrid's resolution or its second pass).  A waiting
+// request is admitted, first come first served, as soon as a slot is free
+// and its HBM footprint fits in what the running requests leave of the
+// budget; idle resident states are evicted, least recently used first, to
+// make room.  Arrival, start and finish times give each request's latency.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -45,8 +51,19 @@ struct Request {
     std::vector<uint64_t> sum;
 };
 
-struct Slot {
+// Resident sampled state: a workspace handle (borrowing the graph's CSR)
+// holding the first pass of (graph, k, seed).
+struct State {
+    int graph = 0, k = 0;
+    uint64_t seed = 0;
     cc_graph_t ws = nullptr;
+    std::vector<int32_t> sample;
+    size_t bytes = 0;  // workspace held while idle
+    bool busy = false;
+    uint64_t tick = 0;
+};
+
+struct Slot {
     cudaStream_t st = nullptr;
     void *cand = nullptr;
     unsigned *cnt = nullptr;
@@ -57,11 +74,12 @@ struct Slot {
 // Device bytes a request needs beyond the resident graph (workspace of one
 // estimate: traversal words, per-node statistics, outputs, per-source
 // tables).
-size_t footprint(int64_t n, int k, bool directed_or_weighted)
+size_t footprint(int64_t n, int k, bool directed_or_weighted, bool hybrid)
 {
     int W = 1;
     while (W * 64 < k) W <<= 1;
-    const size_t per_node = (size_t)W * 8 * 5 + 4 * 10 + 16 * 2 + 8 * 2 + 32 + 48 + 64;
+    size_t per_node = (size_t)W * 8 * 5 + 4 * 10 + 16 * 2 + 8 * 2 + 32 + 48 + 64;
+    if (hybrid) per_node += (size_t)64 * W + 1 + 16;  // band rows, flags, HC sums
     size_t b = (size_t)n * per_node + (size_t)k * k * 4 + (size_t)4096 * k * 20;
     if (directed_or_weighted) b += (size_t)n * 32 * 4 * 2 + (size_t)n * 16;
     return b;
@@ -73,7 +91,11 @@ struct cc_server {
     std::vector<cc_graph_t> graphs;
     std::vector<int64_t> n;
     std::vector<Slot> slots;
-    size_t budget = 0, in_use = 0;
+    std::vector<std::unique_ptr<State>> states;
+    size_t budget = 0, in_use = 0, resident = 0;
+    uint64_t tick = 0;
+    int64_t hits = 0, misses = 0;
+    int slot_ctas = 0;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request *> pending;
@@ -84,33 +106,89 @@ struct cc_server {
     bool stop = false;
 
     void worker(int s);
+    State *find_idle(const Request *r);
+    void evict_for(size_t need);
 };
+
+// An idle resident state of r's sample (caller holds mu).
+State *cc_server::find_idle(const Request *r)
+{
+    for (auto &p : states)
+        if (!p->busy && p->graph == r->graph && p->k == r->k && p->seed == r->seed)
+            return p.get();
+    return nullptr;
+}
+
+// Evict idle states, least recently used first, until `need` more bytes fit
+// the budget (caller holds mu).
+void cc_server::evict_for(size_t need)
+{
+    while (in_use + resident + need > budget) {
+        size_t at = states.size();
+        for (size_t i = 0; i < states.size(); ++i)
+            if (!states[i]->busy && (at == states.size() || states[i]->tick < states[at]->tick))
+                at = i;
+        if (at == states.size()) return;
+        resident -= states[at]->bytes;
+        cc_graph_free(states[at]->ws);
+        states.erase(states.begin() + (long)at);
+    }
+}
 
 void cc_server::worker(int si)
 {
     Slot &S = slots[si];
     for (;;) {
         Request *r = nullptr;
+        State *E = nullptr;
+        bool reuse = false;
+        size_t charged = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv.wait(lk, [&] {
-                return stop || (!pending.empty() &&
-                                in_use + pending.front()->footprint <= budget);
-            });
+            // the front request fits when its state is resident and idle, or
+            // its footprint fits beside the running requests (idle states
+            // can always be evicted)
+            auto admissible = [&] {
+                if (pending.empty()) return false;
+                const Request *f = pending.front();
+                return find_idle(f) != nullptr || in_use + f->footprint <= budget;
+            };
+            cv.wait(lk, [&] { return stop || admissible(); });
             if (stop && pending.empty()) return;
-            if (pending.empty() || in_use + pending.front()->footprint > budget) continue;
+            if (!admissible()) continue;
             r = pending.front();
             pending.pop_front();
-            in_use += r->footprint;
+            E = find_idle(r);
+            if (E) {
+                reuse = true;
+                resident -= E->bytes;
+            } else {
+                charged = r->footprint;
+                evict_for(charged);
+                auto fresh = std::make_unique<State>();
+                fresh->graph = r->graph;
+                fresh->k = r->k;
+                fresh->seed = r->seed;
+                fresh->ws = graph_new_empty();
+                if (fresh->ws) graph_set_max_ctas(fresh->ws, slot_ctas);
+                E = fresh.get();
+                states.push_back(std::move(fresh));
+            }
+            E->busy = true;
+            in_use += charged;
             running += 1;
             peak_running = std::max(peak_running, running);
             r->start = Clock::now();
         }
-        int rc = graph_borrow(S.ws, graphs[r->graph]);
         const int64_t n = this->n[r->graph];
-        std::vector<int32_t> sample(r->k);
-        if (rc == CC_OK)
-            rc = choose_sample_ws(n, r->k, r->seed, sample.data(), S.cand, S.cnt, S.dout, S.st);
+        int rc = E->ws ? CC_OK : CC_ERR_OOM;
+        if (rc == CC_OK && !reuse) {
+            rc = graph_borrow(E->ws, graphs[r->graph]);
+            E->sample.resize(r->k);
+            if (rc == CC_OK)
+                rc = choose_sample_ws(n, r->k, r->seed, E->sample.data(), S.cand, S.cnt, S.dout,
+                                      S.st);
+        }
         if (rc == CC_OK) {
             r->s_hat.resize(n);
             r->clo.resize(n);
@@ -133,14 +211,30 @@ void cc_server::worker(int si)
             out.pivot = r->pivot.data();
             out.delta = r->delta.data();
             out.sample_sum = r->sum.data();
-            rc = cc_estimate(S.ws, sample.data(), r->k, &o, &out);
+            rc = reuse ? estimate_resident(E->ws, r->k, &o, &out)
+                       : cc_estimate(E->ws, E->sample.data(), r->k, &o, &out);
         }
+        const size_t held = rc == CC_OK ? graph_workspace_bytes(E->ws) : 0;
         {
             std::lock_guard<std::mutex> lk(mu);
             r->done = Clock::now();
             r->status = rc;
-            in_use -= r->footprint;
+            in_use -= charged;
             running -= 1;
+            if (reuse) hits += 1; else misses += 1;
+            if (rc == CC_OK) {
+                E->busy = false;
+                E->bytes = held;
+                E->tick = ++tick;
+                resident += held;
+            } else {
+                for (size_t i = 0; i < states.size(); ++i)
+                    if (states[i].get() == E) {
+                        if (E->ws) cc_graph_free(E->ws);
+                        states.erase(states.begin() + (long)i);
+                        break;
+                    }
+            }
             lat_ms.push_back(std::chrono::duration<double, std::milli>(r->done - r->arrive).count());
         }
         cv.notify_all();
@@ -181,12 +275,9 @@ int cc_server_create(int32_t ngraphs, const cc_graph_t *graphs, int32_t slots,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = std::min(msbfs_min_blocks_per_sm(), mssp_blocks_per_sm());
-    const int ctas = std::max(1, sms * per_sm / slots);
+    srv->slot_ctas = std::max(1, sms * per_sm / slots);
     srv->slots.resize(slots);
     for (auto &S : srv->slots) {
-        S.ws = graph_new_empty();
-        if (!S.ws) return CC_ERR_OOM;
-        graph_set_max_ctas(S.ws, ctas);
         if (cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaMalloc(&S.cand, sample_candidate_bytes()) != cudaSuccess ||
             cudaMalloc(&S.cnt, 4) != cudaSuccess ||
@@ -218,7 +309,7 @@ int cc_server_submit(cc_server_t s, int32_t graph, int32_t estimator, int32_t k,
     r->seed = seed;
     r->a = eps_num;
     r->b = eps_den;
-    r->footprint = footprint(s->n[graph], k, directed || weighted);
+    r->footprint = footprint(s->n[graph], k, directed || weighted, estimator == CC_EST_HYBRID);
     if (r->footprint > s->budget) return CC_ERR_TOO_LARGE;
     r->arrive = Clock::now();
     {
@@ -300,6 +391,18 @@ int cc_server_stats(cc_server_t s, int64_t *completed, double *p50_ms, double *p
     return CC_OK;
 }
 
+int cc_server_cache_stats(cc_server_t s, int64_t *hits, int64_t *misses, int32_t *states,
+                          uint64_t *resident_bytes)
+{
+    if (!s) return CC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (hits) *hits = s->hits;
+    if (misses) *misses = s->misses;
+    if (states) *states = (int32_t)s->states.size();
+    if (resident_bytes) *resident_bytes = (uint64_t)s->resident;
+    return CC_OK;
+}
+
 int cc_server_free(cc_server_t s)
 {
     if (!s) return CC_ERR_ARG;
@@ -310,8 +413,9 @@ int cc_server_free(cc_server_t s)
     s->cv.notify_all();
     for (auto &S : s->slots)
         if (S.th.joinable()) S.th.join();
+    for (auto &p : s->states)
+        if (p->ws) cc_graph_free(p->ws);
     for (auto &S : s->slots) {
-        if (S.ws) cc_graph_free(S.ws);
         if (S.st) cudaStreamDestroy(S.st);
         cudaFree(S.cand);
         cudaFree(S.cnt);
