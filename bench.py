@@ -57,7 +57,7 @@ def parse():
                          "20, grids to 2048^2)")
     ap.add_argument("--workload", default="rmat20",
                     choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive",
-                             "nodeweighted", "reach"],
+                             "nodeweighted", "reach", "grid"],
                     help="rmat20 is the headline; the others print their own line")
     return ap.parse_args()
 
@@ -785,6 +785,32 @@ def run_extra(args):
         cc.cc_batch_free(b)
         for g in handles:
             cc.cc_graph_free(g)
+    elif args.workload == "grid":
+        # The high-diameter case of the batch and serving pools: a 1024^2
+        # grid (stand-in for the paper's grid20), k = 256, every estimator
+        # with the hybrid at eps = 1/16 (device outputs).
+        side, kg = 1024, 256
+        n, s, d = synth.grid_edges(side, side)
+        g, _ = cc.cc_graph_from_edges(n, s, d)
+        nn, arcs, _, _ = cc.cc_graph_info(g)
+        C = cc.cc_sample_choose(g, kg, SSEED)
+        dev = torch.device("cuda", 0)
+        shat = torch.empty((4, nn), dtype=torch.float64, device=dev)
+        o = cc.cc_out()
+        for e in range(4):
+            o.s_hat[e] = shat[e].data_ptr()
+        opts = cc.cc_opts_default(kg)
+        opts.device_outputs = 1
+        opts.stream = torch.cuda.current_stream().cuda_stream
+        ms = _time_steps(lambda: cc.cc_estimate(g, C, opts, o), args.steps, args.warmup, flush)
+        st = cc.cc_last_pass_stats(g)
+        nl, kms, kb, nk = cc.cc_last_call_timing(g)
+        line.update(value=kg * (arcs // 2) / (ms / 1e3) / 1e9, ms_per_step=ms,
+                    traversal_launches=nl, traversal_ms=kms, levels=st["levels"],
+                    td_levels=st["td_levels"], bu_levels=st["bu_levels"],
+                    config={"workload": "grid", "graph": f"{side} x {side} grid", "n": nn,
+                            "m": arcs // 2, "k": kg, "eps": "1/16"})
+        cc.cc_graph_free(g)
     elif args.workload in ("road4m", "rt22", "config1"):
         if args.workload == "road4m":
             n, s, d, length = synth.road_like_edges(4 << 20, seed=1)

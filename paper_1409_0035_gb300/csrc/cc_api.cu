@@ -596,7 +596,7 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st, bool
                          g->sum2.as<uint64_t>(), g->hc2.as<uint64_t>(), g->lc2.as<uint64_t>(),
                          &g->ctl.as<Ctl>()->band_ovf, g->gate2.as<unsigned>(),
                          g->npartial.as<unsigned>(), st);
-        g->call_kernels += 2;
+        g->call_kernels += 1;
         gate = g->gate2.as<unsigned>();
     }
     RC(g->Lmask.ensure((size_t)n * W * 8));
@@ -630,12 +630,13 @@ int bfs_hybrid(cc_graph *g, int k, uint32_t a, uint32_t b, cudaStream_t st, bool
 bool use_band(cc_graph *g, int k, const cc_opts *opts)
 {
     if (!opts->want_hybrid || g->sq || g->band_off) return false;
+    const double need = (double)g->n * 64.0 * pow2_words(k);
+    if ((double)g->band.cap >= need) return true;  // rows held from an earlier call
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    const double need = (double)g->n * 64.0 * pow2_words(k);
     return need <= ((double)free_b + (double)g->band.cap) / 3.0;
 }
 

@@ -70,26 +70,25 @@ __global__ void k_finalize(FinalizeArgs A)
     d_finalize(A, GSTART, GSTRIDE);
 }
 
-// After a first pass with RED_BAND: LCsum / LCsumSq of the nodes whose
-// L(v) misses a sampled node (d_band_resolve).
+// After a first pass with RED_BAND: the gate of the second pass (it runs
+// only when a band offset overflowed and some node needs it), then LCsum /
+// LCsumSq of the nodes whose L(v) misses a sampled node (d_band_resolve);
+// nothing more when no node does.
 __global__ void k_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx,
                                const int32_t *pivot, const uint32_t *delta, const uint32_t *dcc,
                                const HybPrep *hp, const uint8_t *bflag, const uint8_t *band,
                                const uint64_t *sum2, const uint64_t *hc2, uint64_t *lc2,
-                               const int *band_ovf)
+                               const int *band_ovf, const unsigned *npartial, unsigned *gate)
 {
-    if (*band_ovf) return;  // the second pass recomputes LCsum
+    const bool ovf = *band_ovf != 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gate[0] = ovf ? npartial[0] + npartial[1] : 0u;
+        gate[1] = 0u;
+    }
+    if (ovf || npartial[0] == 0) return;  // the second pass, or nothing, to do
     d_band_resolve(n, k, rowb, sidx, pivot, delta, dcc, hp, bflag, band, sum2, hc2, lc2,
                    (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
                    ((int64_t)gridDim.x * blockDim.x) >> 5);
-}
-
-// Gate of the second pass after a RED_BAND first pass: it runs only when a
-// band offset overflowed and some node needs it.
-__global__ void k_band_gate(const int *band_ovf, const unsigned *npartial, unsigned *gate)
-{
-    gate[0] = *band_ovf ? npartial[0] + npartial[1] : 0u;
-    gate[1] = 0u;
 }
 
 inline int grid_for(int64_t n, int block)
@@ -234,8 +233,7 @@ void run_band_resolve(int64_t n, int k, int rowb, const int32_t *sidx, const int
 {
     k_band_resolve<<<grid_for(n * 32, 256), 256, 0, st>>>(n, k, rowb, sidx, pivot, delta, dcc,
                                                           hp, bflag, band, sum2, hc2, lc2,
-                                                          band_ovf);
-    k_band_gate<<<1, 1, 0, st>>>(band_ovf, npartial, gate);
+                                                          band_ovf, npartial, gate);
 }
 
 void run_finalize(const FinalizeArgs &a, cudaStream_t st)

@@ -750,11 +750,22 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 qn = ((volatile LevelCtl *)C)->qcnt;
             }
             int32_t *Tout = (Qin == J.T) ? J.Q1 : J.T;
-            // P1: push the frontier words of the queued nodes.  Nodes of at
-            // most kLightMaxDeg entries: a lane group each, NPW per warp
-            // (a grid's frontier node has 4 entries: a warp each would leave
-            // most lanes idle and chain one node after another).
-            for (int64_t t0 = gwarp * NPW; t0 < qn; t0 += nwarps * NPW) {
+            // P1: push the frontier words of the queued nodes.  A frontier
+            // of at most one node per warp: a warp per node (heavy nodes
+            // pushed by their chunk tasks below).
+            const bool few = qn <= nwarps;
+            for (int64_t t = gwarp; few && t < qn; t += nwarps) {
+                const int u = Qin[t];
+                const int64_t b = rp[u], e = rp[u + 1];
+                if (J.ntH > 0 && e - b > kMediumMaxDeg) continue;
+                const uint64_t f = Fin[(int64_t)u * W + w];
+                td_push<W>(J, col, f, b, e, C, Tout, A, stage);
+            }
+            // Otherwise nodes of at most kLightMaxDeg entries: a lane group
+            // each, NPW per warp (a grid's frontier node has 4 entries: a
+            // warp each would leave most lanes idle and chain one node after
+            // another).
+            for (int64_t t0 = gwarp * NPW; !few && t0 < qn; t0 += nwarps * NPW) {
                 const int64_t t = t0 + grp;
                 if (t < qn) {
                     const int u = Qin[t];
@@ -769,7 +780,7 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             // so that consecutive ones go to different warps) 32 at a time
             // by ballot and pushes each larger one whole; when the graph has
             // chunk tasks, a heavy node's list is pushed by them.
-            for (int64_t j0 = 0; gwarp + j0 * nwarps < qn; j0 += 32) {
+            for (int64_t j0 = 0; !few && gwarp + j0 * nwarps < qn; j0 += 32) {
                 const int64_t t = gwarp + (j0 + lane) * nwarps;
                 int u = 0;
                 int64_t b = 0, e = 0;
