@@ -281,9 +281,10 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
  *   T         int64[n]: rank position (1-based, not counting v) of the k-th
  *             sample; 0 when count < k
  * Outputs are host arrays, any may be NULL.  Runs one cooperative launch
- * over the order in groups of up to 256 sources: bit-packed searches on G^T
- * (outbound) or G (inbound) that skip nodes already holding k + 1 nodes of
- * smaller rank (themselves included); breadth-first on unit lengths,
+ * over the order in groups of 512 sources by default (CC_PARAM_REACH_WORDS):
+ * bit-packed searches on G^T (outbound) or G (inbound) that skip nodes
+ * already holding k + 1 nodes of smaller rank (themselves included);
+ * breadth-first on unit lengths,
  * label-correcting shortest paths with arc lengths (distances must stay
  * below 2^32 - 1).  Errors: CC_ERR_ARG (k < 1), CC_ERR_OOM, CC_ERR_CUDA,
  * CC_ERR_TIMEOUT (a bounded device-side wait ran out).
@@ -496,10 +497,15 @@ int cc_set_tuning(cc_graph_t g, int32_t alpha);
  *                             0 restores the default (96 mean arc
  *                             lengths), a negative value relaxes every
  *                             label at once (plain label-correcting
- *                             rounds) */
+ *                             rounds)
+ *   CC_PARAM_REACH_WORDS      words per node of cc_reach_estimate's groups
+ *                             (1, 2, 4, 8 or 16: groups of 64 x that many
+ *                             sources searched together); 0 restores the
+ *                             default */
 #define CC_PARAM_ALPHA 0
 #define CC_PARAM_HYBRID_ONE_PASS 1
 #define CC_PARAM_SSSP_DELTA 2
+#define CC_PARAM_REACH_WORDS 3
 int cc_set_param(cc_graph_t g, int32_t param, int32_t value);
 
 /* ---- diagnostics --------------------------------------------------------- */

@@ -374,7 +374,7 @@ def cc_set_tuning(g, alpha=0):
     _chk(lib().cc_set_tuning(g, int(alpha)), "cc_set_tuning")
 
 
-CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS, CC_PARAM_SSSP_DELTA = 0, 1, 2
+CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS, CC_PARAM_SSSP_DELTA, CC_PARAM_REACH_WORDS = 0, 1, 2, 3
 
 
 def cc_set_param(g, param, value):

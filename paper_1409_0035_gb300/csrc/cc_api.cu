@@ -19,6 +19,12 @@ using namespace ccg;
 namespace {
 
 constexpr uint64_t kTimeoutNs = 10ull * 1000 * 1000 * 1000;  // 10 s per wait
+// Words per node of the reachability groups (64 sources each; default of
+// CC_PARAM_REACH_WORDS).  Directed R-MAT 20 kept whole, k = 64, outbound /
+// inbound: 2 words 156 / 154 ms, 4 words 101 / 94 ms, 8 words 85 / 81 ms,
+// 16 words 96 / 92 ms (fewer groups and barriers against less pruning).
+constexpr int kReachDefaultW = 8;
+
 // Bucket width of the shortest-path rounds in mean arc lengths (default of
 // CC_PARAM_SSSP_DELTA).  Measured on the road-like graph (3.9 M nodes, 32
 // sources, lengths round(1e3 len)+1 and round(1e6 len)+1): 1 -> 409 / 979
@@ -118,6 +124,7 @@ struct cc_graph {
     bool band_off = false;  // CC_PARAM_HYBRID_ONE_PASS = 0: always two passes
     int64_t sssp_delta = 0;  // CC_PARAM_SSSP_DELTA (0: kDeltaMult x mean length, < 0: off)
     uint32_t band_a = 0, band_b = 0;  // eps the last first pass classified for (0: none)
+    int reach_words = 0;     // CC_PARAM_REACH_WORDS (0: kReachDefaultW)
     double w_mean = 0.0;     // mean arc length (weighted graphs)
     int max_ctas = 0;    // cap on the CTAs of each launch (0: whole GPU)
     bool borrowed = false;  // CSR buffers belong to another handle
@@ -648,23 +655,24 @@ int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
     return bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st, band);
 }
 
-// One 32-source chunk of shortest paths (forward, and reversed for round
-// trips) into g->distF / g->distR.  Unit lengths use the bit-packed
-// traversal writing levels; arc lengths the label-correcting kernel.
-// Sources per chunk: 32 for shortest paths (one 128-byte row per node);
-// for unit lengths up to 128 (two bit-packed words per node) so that fewer,
-// wider traversals fill the rows, while the distance rows (one or two
-// n x cw tables) take at most a third of the free device memory.
+// One chunk of shortest paths (forward, and reversed for round trips)
+// into g->distF / g->distR.  Unit lengths use the bit-packed traversal
+// writing levels; arc lengths the delta-stepping kernel.  Sources per
+// chunk: with arc lengths 64 (two per lane of a 256-byte row: the rounds,
+// whose fixed cost bounds a chunk on graphs of large diameter, are shared
+// by twice the sources) or 32; with unit lengths up to 128 (two bit-packed
+// words per node) so that fewer, wider traversals fill the rows; always
+// while the distance rows (one or two n x cw tables) take at most a third
+// of the free device memory.
 int chunk_width(cc_graph *g, int64_t k)
 {
-    if (g->weighted) return kChunkSrc;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();
         return kChunkSrc;
     }
     const double tables = g->directed ? 2.0 : 1.0;
-    int cw = 128;
+    int cw = g->weighted ? 2 * kChunkSrc : 128;
     while (cw > kChunkSrc && (double)g->n * cw * 4.0 * tables > (double)free_b / 3.0) cw /= 2;
     while (cw > kChunkSrc && cw / 2 >= k) cw /= 2;
     return cw;
@@ -732,7 +740,8 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
         j.kc = kc;
         j.sources = d_sources;
         j.dist = (dir ? g->distR : g->distF).as<uint32_t>() + off;
-        j.mask = g->mask.as<unsigned>();
+        j.mask = g->mask.as<unsigned long long>();
+        j.spl = cw / kChunkSrc;
         j.Q0 = g->Q0.as<int32_t>();
         j.Q1 = g->Q1.as<int32_t>();
         j.delta = sssp_delta(g);
@@ -767,7 +776,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
         g->call_kernels += 1;
         g->call_ms += ms;
         // relaxations x (row read 4 B + arc 8 B) + the n x 32 rows written once
-        g->call_bytes += (double)g->last.words * 12.0 + (double)n * kChunkSrc * 4.0;
+        g->call_bytes += (double)g->last.words * 12.0 + (double)n * cw * 4.0;
         if (g->last.err < 0) return g->last.err;
     }
     return CC_OK;
@@ -813,7 +822,7 @@ int chunked_pass1(cc_graph *g, int k, cudaStream_t st, const NwJob *nw = nullptr
     const size_t rows = (size_t)n * cw * (g->resident ? nch : 1) * 4;
     RC(g->distF.ensure(rows));
     if (g->directed) RC(g->distR.ensure(rows));
-    RC(g->mask.ensure(n * 4));
+    RC(g->mask.ensure(n * 8));
     RC(g->Q0.ensure(n * 4));
     RC(g->Q1.ensure(n * 4));
     RC(g->best.ensure(n * 8));
@@ -1078,6 +1087,7 @@ int ccg::graph_borrow(cc_graph_t dst, cc_graph_t src)
     dst->alpha = src->alpha;
     dst->band_off = src->band_off;
     dst->sssp_delta = src->sssp_delta;
+    dst->reach_words = src->reach_words;
     dst->w_mean = src->w_mean;
     dst->borrowed = true;
     return CC_OK;
@@ -1349,6 +1359,10 @@ int cc_set_param(cc_graph_t g, int32_t param, int32_t value)
         return CC_OK;
     case CC_PARAM_SSSP_DELTA:
         g->sssp_delta = value;
+        return CC_OK;
+    case CC_PARAM_REACH_WORDS:
+        if (value < 0 || value > kReachMaxW || (value & (value - 1))) return CC_ERR_ARG;
+        g->reach_words = value;
         return CC_OK;
     default:
         return CC_ERR_ARG;
@@ -1759,7 +1773,20 @@ int cc_reach_estimate(cc_graph_t g, int32_t k, uint64_t seed, int32_t inbound, v
     reset_timing(g);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)g->n;
-    const int W = (int)std::min<int64_t>(kReachMaxW, (g->n + 63) / 64);
+    // Group width: CC_PARAM_REACH_WORDS words (64 sources each) or the
+    // default, at most what n needs and while the per-bit levels (64 W
+    // uint32 per node) take at most a quarter of the free memory.
+    int W = g->reach_words > 0 ? g->reach_words : kReachDefaultW;
+    while (W > 1 && 64 * W >= 2 * (int64_t)g->n) W /= 2;
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            return CC_ERR_CUDA;
+        }
+        const double avail = (double)free_b + (double)g->rc_lev.cap;
+        while (W > 1 && (double)n * 64.0 * W * 4.0 > avail / 4.0) W /= 2;
+    }
     const DevCSR &sg = (g->directed && !inbound) ? g->rv : g->fw;
     RC(g->nw_keys.ensure(n * 8));
     RC(g->nw_tk.ensure(n * 8));
@@ -1862,7 +1889,7 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
         const int cw = chunk_width(g, n);
         RC(g->distF.ensure((size_t)n * cw * 4));
         if (g->directed) RC(g->distR.ensure((size_t)n * cw * 4));
-        RC(g->mask.ensure(n * 4));
+        RC(g->mask.ensure(n * 8));
         RC(g->Q0.ensure(n * 4));
         RC(g->Q1.ensure(n * 4));
         RC(g->errflag.ensure(4));

@@ -8,7 +8,7 @@
 
 namespace ccg {
 
-constexpr int kReachMaxW = 4;  // words per node: groups of up to 256 sources
+constexpr int kReachMaxW = 16;  // words per node: groups of up to 1024 sources
 
 struct ReachJob {
     int64_t n;

@@ -29,8 +29,12 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+// Sources per row: 32 * SPL (SPL = 1 or 2), lane l holding sources l and
+// l + 32 of the chunk; masks are 64-bit either way.
+template <int SPL>
 __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
 {
+    constexpr int LD = 32 * SPL;  // row stride
     const int lane = threadIdx.x & 31;
     const int64_t gthreads = (int64_t)gridDim.x * kBlock;
     const int64_t gtid = (int64_t)blockIdx.x * kBlock + threadIdx.x;
@@ -49,9 +53,9 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
     }
 
     if (gtid < 3) ctl->far_min[gtid] = ~0ull;
-    for (int64_t i = gtid; i < n * kChunkSrc; i += gthreads) J.dist[i] = kInf;
+    for (int64_t i = gtid; i < n * LD; i += gthreads) J.dist[i] = kInf;
     for (int64_t v = gtid; v < n; v += gthreads) {
-        J.mask[v] = 0u;
+        J.mask[v] = 0ull;
         if (J.delta) {
             J.nstamp[v] = 0u;
             J.fstamp[v] = 0u;
@@ -60,8 +64,8 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
     if (!grid_sync(ctl, blockIdx.x, nb, J.timeout_ns)) return;
     if (gtid < J.kc) {
         const int v = J.sources[gtid];
-        J.dist[(int64_t)v * kChunkSrc + gtid] = 0u;
-        if (atomicOr(&J.mask[v], 1u << gtid) == 0u) {
+        J.dist[(int64_t)v * LD + gtid] = 0u;
+        if (atomicOr(&J.mask[v], 1ull << gtid) == 0ull) {
             const unsigned p = atomicAdd(&ctl->lev[0].qlen, 1u);
             J.Q0[p] = v;
             if (J.delta) J.nstamp[v] = 1u;  // queued for round 0
@@ -106,20 +110,28 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
         const unsigned fst = epoch + 1u;        // stamp: in this epoch's far queue
         for (int64_t t = gwarp; t < (int64_t)qn; t += nwarps) {
             const int u = Qin[t];
-            unsigned m = 0;
-            if (lane == 0) m = atomicExch(&J.mask[u], 0u);
+            unsigned long long m = 0;
+            if (lane == 0) m = atomicExch(&J.mask[u], 0ull);
             m = __shfl_sync(FULL, m, 0);
-            const bool pending = (m >> lane) & 1u;
             // The row may have been lowered by an atomicMin of another SM in
             // this round (that is what set the mask bit): read it from L2,
             // the point where those atomics are performed, not from a
-            // possibly stale L1 line.
-            const uint64_t du = pending ? __ldcg(J.dist + (int64_t)u * kChunkSrc + lane) : 0ull;
-            // Labels at or beyond the threshold wait in the far queue.
-            const bool active = pending && du < T;
-            const unsigned later = __ballot_sync(FULL, pending && !active);
+            // possibly stale L1 line.  Labels at or beyond the threshold
+            // wait in the far queue.
+            uint64_t du[SPL];
+            bool active[SPL];
+            unsigned long long later = 0, lo = ~0ull;
+#pragma unroll
+            for (int q = 0; q < SPL; ++q) {
+                const int i = lane + 32 * q;
+                const bool pending = (m >> i) & 1ull;
+                du[q] = pending ? __ldcg(J.dist + (int64_t)u * LD + i) : 0ull;
+                active[q] = pending && du[q] < T;
+                const unsigned b = __ballot_sync(FULL, pending && !active[q]);
+                later |= (unsigned long long)b << (32 * q);
+                if (pending && !active[q]) lo = du[q] < lo ? du[q] : lo;
+            }
             if (later) {
-                unsigned long long lo = pending && !active ? du : ~0ull;
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) {
                     const unsigned long long y = __shfl_xor_sync(FULL, lo, o);
@@ -132,38 +144,45 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                         stage_push(fstage, u, Fout, fout_len);
                 }
             }
-            if (!__any_sync(FULL, active)) continue;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < SPL; ++q) any |= active[q];
+            if (!__any_sync(FULL, any)) continue;
             const int64_t b = J.rp[u], e = J.rp[u + 1];
             for (int64_t x = b; x < e; ++x) {
                 const int v = __ldg(J.col + x);
                 const uint64_t wt = J.w ? (uint64_t)__ldg(J.w + x) : 1ull;
-                bool imp = false;
-                uint64_t nd = 0;
-                if (active) {
-                    nd = du + wt;
-                    relax += 1;
-                    if (nd >= (uint64_t)kInf) {
-                        atomicCAS(&ctl->err, 0, CC_ERR_TOO_LARGE);
-                    } else {
-                        unsigned *slot = &J.dist[(int64_t)v * kChunkSrc + lane];
-                        if ((unsigned)nd < *slot) imp = (unsigned)nd < atomicMin(slot, (unsigned)nd);
+                unsigned long long nbits = 0, fbits = 0, flo = ~0ull;
+#pragma unroll
+                for (int q = 0; q < SPL; ++q) {
+                    bool imp = false;
+                    uint64_t nd = 0;
+                    if (active[q]) {
+                        nd = du[q] + wt;
+                        relax += 1;
+                        if (nd >= (uint64_t)kInf) {
+                            atomicCAS(&ctl->err, 0, CC_ERR_TOO_LARGE);
+                        } else {
+                            unsigned *slot = &J.dist[(int64_t)v * LD + lane + 32 * q];
+                            if ((unsigned)nd < *slot)
+                                imp = (unsigned)nd < atomicMin(slot, (unsigned)nd);
+                        }
                     }
+                    nbits |= (unsigned long long)__ballot_sync(FULL, imp && nd < T) << (32 * q);
+                    fbits |= (unsigned long long)__ballot_sync(FULL, imp && nd >= T) << (32 * q);
+                    if (imp && nd >= T) flo = nd < flo ? nd : flo;
                 }
-                if (!delta) {
-                    const unsigned bits = __ballot_sync(FULL, imp);
-                    if (bits && lane == 0 && atomicOr(&J.mask[v], bits) == 0u)
+                if (!(nbits | fbits)) continue;
+                if (!delta) {  // no buckets: one queue
+                    if (lane == 0 && atomicOr(&J.mask[v], nbits | fbits) == 0ull)
                         stage_push(stage, v, Qout, qout_len);
                     continue;
                 }
-                const unsigned nbits = __ballot_sync(FULL, imp && nd < T);
-                const unsigned fbits = __ballot_sync(FULL, imp && nd >= T);
-                if (!(nbits | fbits)) continue;
-                unsigned long long lo = imp && nd >= T ? nd : ~0ull;
                 if (fbits) {
 #pragma unroll
                     for (int o = 16; o >= 1; o >>= 1) {
-                        const unsigned long long y = __shfl_xor_sync(FULL, lo, o);
-                        lo = y < lo ? y : lo;
+                        const unsigned long long y = __shfl_xor_sync(FULL, flo, o);
+                        flo = y < flo ? y : flo;
                     }
                 }
                 if (lane == 0) {
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                     if (nbits && atomicExch(&J.nstamp[v], nst) != nst)
                         stage_push(stage, v, Qout, qout_len);
                     if (fbits) {
-                        atomicMin(&ctl->far_min[epoch % 3], lo);
+                        atomicMin(&ctl->far_min[epoch % 3], flo);
                         if (atomicExch(&J.fstamp[v], fst) != fst)
                             stage_push(fstage, v, Fout, fout_len);
                     }
@@ -392,43 +411,49 @@ int grid_of(int64_t n)
 
 int launch_mssp(const SsspJob &job, cudaStream_t st)
 {
-    static int blocks_per_sm = -1, sms = 0;
-    if (blocks_per_sm < 0) {
+    static int blocks_per_sm[2] = {-1, -1}, sms = 0;
+    const int q = job.spl == 2 ? 1 : 0;
+    const void *fn = q ? (const void *)mssp_kernel<2> : (const void *)mssp_kernel<1>;
+    if (blocks_per_sm[q] < 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return CC_ERR_CUDA;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return CC_ERR_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, mssp_kernel, kBlock,
-                                                          0) != cudaSuccess ||
-            blocks_per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[q], fn, kBlock, 0) !=
+                cudaSuccess ||
+            blocks_per_sm[q] < 1)
             return CC_ERR_CUDA;
     }
     SsspJob j = job;
     void *args[] = {&j};
-    int grid = blocks_per_sm * sms;
+    int grid = blocks_per_sm[q] * sms;
     if (job.max_ctas > 0 && job.max_ctas < grid) grid = job.max_ctas;
-    return cudaLaunchCooperativeKernel((const void *)mssp_kernel, dim3(grid),
-                                       dim3(kBlock), args, 0, st) == cudaSuccess
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, st) == cudaSuccess
                ? CC_OK
                : CC_ERR_CUDA;
 }
 
+// One carveout for every persistent kernel of a server (see msbfs.cu).
 void mssp_set_carveout(int percent)
 {
-    cudaFuncSetAttribute((const void *)mssp_kernel,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, percent);
+    for (const void *f : {(const void *)mssp_kernel<1>, (const void *)mssp_kernel<2>})
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, percent);
     cudaGetLastError();
 }
 
+// Smallest residency over both variants.
 int mssp_blocks_per_sm()
 {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mssp_kernel, kBlock, 0) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return 1;
+    int m = 1 << 30;
+    for (const void *f : {(const void *)mssp_kernel<1>, (const void *)mssp_kernel<2>}) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        m = b < m ? b : m;
     }
-    return b < 1 ? 1 : b;
+    return m < 1 ? 1 : m;
 }
 
 void run_reduce1(const ReduceJob &r, cudaStream_t st)

@@ -15,10 +15,11 @@ struct SsspJob {
     const int64_t *rp;
     const int32_t *col;
     const uint32_t *w;      // arc lengths (NULL: unit lengths)
-    int kc;                 // sources in this chunk (<= 32)
+    int kc;                 // sources in this chunk (<= 32 spl)
+    int spl;                // sources per lane: 1 (rows of 32) or 2 (rows of 64)
     const int32_t *sources; // kc node ids
-    uint32_t *dist;         // n x 32
-    unsigned *mask;         // n
+    uint32_t *dist;         // n x 32 spl
+    unsigned long long *mask;  // n: sources whose distance dropped
     int32_t *Q0, *Q1;       // n each
     // Buckets (delta-stepping with a near and a far queue): labels below the
     // threshold T relax in rounds; labels at or beyond it wait in far queues

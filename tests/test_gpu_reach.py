@@ -108,3 +108,23 @@ def test_reach_arc_lengths_match_oracle(cc, case):
     w = synth.random_weights(s.size, lo, hi, seed=k)
     r = check(cc, n, s, d, k, seed=5, inbound=inbound, w=w)
     assert (r["count"] > 0).any()
+
+
+@pytest.mark.parametrize("inbound", [False, True])
+def test_reach_group_width_does_not_change_samples(cc, inbound):
+    """Groups of 1 to 16 words (64 to 1,024 sources searched together)
+    prune at different points but take the same bottom-k samples."""
+    n, s, d = synth.rmat_edges(12, 8, seed=31)
+    g, _ = cc.cc_graph_from_edges(n, s, d, directed=True, keep_component=False)
+    try:
+        ref = None
+        for words in (1, 2, 4, 8, 16):
+            cc.cc_set_param(g, cc.CC_PARAM_REACH_WORDS, words)
+            r = cc.cc_reach_estimate(g, 40, 5, inbound)
+            if ref is None:
+                ref = r
+                continue
+            for key in ("count", "distsum", "T", "avg", "R_hat"):
+                assert (r[key] == ref[key]).all(), (words, key)
+    finally:
+        cc.cc_graph_free(g)
