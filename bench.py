@@ -826,6 +826,7 @@ def run_extra(args):
             variants = [("unit", None)]
             k, directed = 64, False
         results = []
+        dev = torch.device("cuda", 0)
         for name, w in variants:
             g, _ = cc.cc_graph_from_edges(n, s, d, w, directed=directed)
             nn, arcs, _, _ = cc.cc_graph_info(g)
@@ -833,12 +834,26 @@ def run_extra(args):
             C = cc.cc_sample_choose(g, k, 2)
             o = cc.cc_opts_default(k)
             o.roundtrip = int(directed)
-            ms = _time_steps(lambda: cc.cc_estimate(g, C, o), args.steps, args.warmup, flush)
+            # device outputs (every estimator's estimate and closeness), as
+            # the headline line; the same call with host outputs is e2e
+            outs = [torch.empty(nn, dtype=torch.float64, device=dev) for _ in range(8)]
+            od = cc.cc_out()
+            for e in range(4):
+                od.s_hat[e], od.closeness[e] = outs[2 * e].data_ptr(), outs[2 * e + 1].data_ptr()
+            o.device_outputs = 1
+            o.stream = torch.cuda.current_stream().cuda_stream
+            ms = _time_steps(lambda: cc.cc_estimate(g, C, o, od), args.steps, args.warmup, flush)
+            tr = cc.cc_last_call_timing(g)
+            ps = cc.cc_last_pass_stats(g)
+            oh = cc.cc_opts_default(k)
+            oh.roundtrip = int(directed)
+            e2e_ms = _time_steps(lambda: cc.cc_estimate(g, C, oh), 1, 1, flush)
             units = k * m * (2 if directed else 1)
             r = {"weights": name, "n": nn, "m": m, "k": k, "ms_per_step": ms,
                  "value": units / (ms / 1e3) / 1e9,
-                 "kernel_launches": cc.cc_last_call_timing(g)[0],
-                 "levels_or_rounds": cc.cc_last_pass_stats(g)["levels"]}
+                 "traversal_ms": tr[1], "kernel_launches": tr[0],
+                 "levels_or_rounds": ps["levels"],
+                 "e2e_ms_host_outputs": e2e_ms}
             if args.workload == "config1":
                 t0 = time.perf_counter()
                 cc.cc_exact(g)

@@ -404,9 +404,20 @@ int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
 
 /* Graph i's place in the plan: its word width, the direction switch it
  * runs with, its team within its class, the class's team count, CTAs and
- * resident CTAs per SM.  Any pointer may be NULL. */
+ * resident CTAs per SM, and whether its tuning came from the autotune
+ * cache (1) or was measured (0).  Any pointer may be NULL. */
 int cc_batch_plan(cc_batch_t b, int32_t i, int32_t *words, int32_t *alpha, int32_t *team,
-                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm);
+                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm,
+                  int32_t *from_cache);
+
+/* Autotune cache of cc_batch_create (autotune = 1): a file of one JSON
+ * object per line, keyed by the GPU's name, n, arcs, k and the counts of
+ * the degree classes (nodes of <= 4, <= 32, <= 128 and more arcs), holding
+ * the direction switch that ran the graph fastest alone, that time and the
+ * level count.  A graph whose key is in the file skips its timing; the
+ * others are timed and appended.  path = NULL or "" turns the cache off
+ * (the default).  Process-wide. */
+int cc_batch_tune_cache(const char *path);
 
 int cc_batch_free(cc_batch_t b);
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
     "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
     "cc_set_tuning", "cc_set_param", "cc_batch_create", "cc_batch_run", "cc_batch_result",
-    "cc_batch_info", "cc_batch_plan", "cc_batch_free", "cc_server_create", "cc_server_submit",
+    "cc_batch_info", "cc_batch_plan", "cc_batch_tune_cache", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_cache_stats",
     "cc_server_free",
     "cc_selftest_barrier_timeout", "cc_strerror", "cc_last_pass_phases",
@@ -112,7 +112,8 @@ def lib():
         L.cc_batch_run.argtypes = [P, P]
         L.cc_batch_result.argtypes = [P, i32, P, i32]
         L.cc_batch_info.argtypes = [P, P, P, P, P]
-        L.cc_batch_plan.argtypes = [P, i32, P, P, P, P, P, P]
+        L.cc_batch_plan.argtypes = [P, i32, P, P, P, P, P, P, P]
+        L.cc_batch_tune_cache.argtypes = [ctypes.c_char_p]
         L.cc_batch_free.argtypes = [P]
         L.cc_server_create.argtypes = [i32, P, i32, u64, P]
         L.cc_server_submit.argtypes = [P, i32, i32, i32, u64, ctypes.c_uint32, ctypes.c_uint32, P]
@@ -471,11 +472,17 @@ def cc_batch_info(b):
 
 def cc_batch_plan(b, i):
     """Graph i's plan: word width, alpha, team, class teams, class CTAs,
-    CTAs per SM."""
-    v = [ctypes.c_int32() for _ in range(6)]
+    CTAs per SM, tuning taken from the autotune cache."""
+    v = [ctypes.c_int32() for _ in range(7)]
     _chk(lib().cc_batch_plan(b, int(i), *[ctypes.byref(x) for x in v]), "cc_batch_plan")
-    return dict(zip(("words", "alpha", "team", "class_teams", "class_ctas", "ctas_per_sm"),
-                    (x.value for x in v)))
+    return dict(zip(("words", "alpha", "team", "class_teams", "class_ctas", "ctas_per_sm",
+                     "from_cache"), (x.value for x in v)))
+
+
+def cc_batch_tune_cache(path):
+    """Autotune cache file of cc_batch_create (None: off)."""
+    _chk(lib().cc_batch_tune_cache(None if path is None else str(path).encode()),
+         "cc_batch_tune_cache")
 
 
 def cc_batch_free(b):

@@ -23,10 +23,14 @@
 // of it per SM), then times every plan for real and keeps the fastest.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "cc_internal.h"
@@ -195,7 +199,7 @@ struct BatchClass {
 struct cc_batch {
     int ngraphs = 0;
     std::vector<cc_graph_t> graphs;
-    std::vector<int> k, W, cls, alpha;
+    std::vector<int> k, W, cls, alpha, cached;
     std::vector<int64_t> n;
     std::vector<std::vector<DBuf>> bufs;  // per graph
     std::vector<BatchJob> hjobs;
@@ -239,6 +243,92 @@ int dalloc(DBuf &b, size_t bytes)
 }
 
 // Streaming multiprocessors and each class kernel's resident CTAs per SM.
+// ---- autotune cache ------------------------------------------------------
+//
+// One JSON object per line: the key (GPU name, n, arcs, k and the counts of
+// the degree classes the traversal treats apart: tiny, light, medium, heavy
+// nodes) and what the autotuner measured for the graph alone (the fastest
+// direction switch, its device time and level count).
+
+std::mutex g_tune_mu;
+std::string g_tune_path;
+
+struct TuneEntry {
+    std::string gpu;
+    int64_t n = 0, arcs = 0, k = 0, nT = 0, nL = 0, nM = 0, nH = 0;
+    int64_t alpha = 0, levels = 0;
+    double ms = 0;
+};
+
+bool json_num(const char *line, const char *key, double *out)
+{
+    char pat[64];
+    std::snprintf(pat, sizeof(pat), "\"%s\":", key);
+    const char *p = std::strstr(line, pat);
+    if (!p) return false;
+    char *end = nullptr;
+    *out = std::strtod(p + std::strlen(pat), &end);
+    return end != p + std::strlen(pat);
+}
+
+bool json_str(const char *line, const char *key, std::string *out)
+{
+    char pat[64];
+    std::snprintf(pat, sizeof(pat), "\"%s\": \"", key);
+    const char *p = std::strstr(line, pat);
+    if (!p) return false;
+    p += std::strlen(pat);
+    const char *q = std::strchr(p, '"');
+    if (!q) return false;
+    out->assign(p, q);
+    return true;
+}
+
+std::vector<TuneEntry> tune_load(const std::string &path)
+{
+    std::vector<TuneEntry> v;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return v;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        TuneEntry e;
+        double x[10];
+        const char *keys[] = {"n", "arcs", "k", "tiny", "light", "medium", "heavy", "alpha",
+                              "levels", "ms"};
+        bool ok = json_str(line, "gpu", &e.gpu);
+        for (int i = 0; i < 10 && ok; ++i) ok = json_num(line, keys[i], &x[i]);
+        if (!ok) continue;  // not an entry of this format
+        e.n = (int64_t)x[0]; e.arcs = (int64_t)x[1]; e.k = (int64_t)x[2];
+        e.nT = (int64_t)x[3]; e.nL = (int64_t)x[4]; e.nM = (int64_t)x[5]; e.nH = (int64_t)x[6];
+        e.alpha = (int64_t)x[7]; e.levels = (int64_t)x[8]; e.ms = x[9];
+        v.push_back(e);
+    }
+    std::fclose(f);
+    return v;
+}
+
+void tune_append(const std::string &path, const std::vector<TuneEntry> &add)
+{
+    if (add.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    for (const TuneEntry &e : add)
+        std::fprintf(f,
+                     "{\"gpu\": \"%s\", \"n\": %lld, \"arcs\": %lld, \"k\": %lld, "
+                     "\"tiny\": %lld, \"light\": %lld, \"medium\": %lld, \"heavy\": %lld, "
+                     "\"alpha\": %lld, \"levels\": %lld, \"ms\": %.6f}\n",
+                     e.gpu.c_str(), (long long)e.n, (long long)e.arcs, (long long)e.k,
+                     (long long)e.nT, (long long)e.nL, (long long)e.nM, (long long)e.nH,
+                     (long long)e.alpha, (long long)e.levels, e.ms);
+    std::fclose(f);
+}
+
+bool same_key(const TuneEntry &a, const TuneEntry &b)
+{
+    return a.gpu == b.gpu && a.n == b.n && a.arcs == b.arcs && a.k == b.k && a.nT == b.nT &&
+           a.nL == b.nL && a.nM == b.nM && a.nH == b.nH;
+}
+
 int batch_residency(cc_batch *b)
 {
     int dev = 0;
@@ -534,9 +624,47 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
     // or arcs * W as a proxy.
     b->solo_ms.assign(ngraphs, 0.0);
     b->levels.assign(ngraphs, 0);
+    std::string tpath;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tpath = g_tune_path;
+    }
+    std::vector<TuneEntry> cache, fresh;
+    std::string gpu;
+    if (autotune && !tpath.empty()) {
+        cudaDeviceProp prop;
+        int dev = 0;
+        B_CK(cudaGetDevice(&dev));
+        B_CK(cudaGetDeviceProperties(&prop, dev));
+        gpu = prop.name;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        cache = tune_load(tpath);
+    }
+    b->cached.assign(ngraphs, 0);
     if (autotune) {
         const int alphas[] = {0, 2, 4, 8, 14};
         for (int i = 0; i < ngraphs; ++i) {
+            TuneEntry key;
+            if (!tpath.empty()) {
+                GraphView v;
+                B_RC(graph_view(graphs[i], &v));
+                key.gpu = gpu;
+                key.n = v.n; key.arcs = v.arcs; key.k = b->k[i];
+                key.nT = v.nT; key.nL = v.nL; key.nM = v.nM; key.nH = v.nH;
+                const TuneEntry *hit = nullptr;
+                for (const TuneEntry &e : cache)
+                    if (same_key(e, key)) hit = &e;  // the last entry of a key wins
+                if (hit) {
+                    BfsJob &j = b->hjobs[i].j;
+                    b->alpha[i] = (int)hit->alpha;
+                    j.alpha = b->alpha[i];
+                    b->hjobs[i].j2.alpha = b->alpha[i];
+                    b->solo_ms[i] = hit->ms;
+                    b->levels[i] = (int)hit->levels;
+                    b->cached[i] = 1;
+                    continue;
+                }
+            }
             cc_opts o;
             cc_opts_default(&o, b->k[i]);
             o.eps_num = b->hjobs[i].a;
@@ -565,6 +693,17 @@ int cc_batch_create(int32_t ngraphs, const cc_graph_t *graphs, const int32_t *co
             b->hjobs[i].j2.alpha = b->alpha[i];
             b->solo_ms[i] = best;
             b->levels[i] = (int)best_lv;
+            if (!tpath.empty()) {
+                key.alpha = b->alpha[i];
+                key.levels = best_lv;
+                key.ms = best;
+                fresh.push_back(key);
+                cache.push_back(key);  // a repeated graph of this batch hits it
+            }
+        }
+        if (!fresh.empty()) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_append(tpath, fresh);
         }
     } else {
         for (int i = 0; i < ngraphs; ++i) {
@@ -676,10 +815,19 @@ int cc_batch_info(cc_batch_t b, int32_t *teams, int32_t *grid, double *last_ms,
     return CC_OK;
 }
 
+int cc_batch_tune_cache(const char *path)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_path = path ? path : "";
+    return CC_OK;
+}
+
 int cc_batch_plan(cc_batch_t b, int32_t i, int32_t *words, int32_t *alpha, int32_t *team,
-                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm)
+                  int32_t *class_teams, int32_t *class_ctas, int32_t *ctas_per_sm,
+                  int32_t *from_cache)
 {
     if (!b || i < 0 || i >= b->ngraphs) return CC_ERR_ARG;
+    if (from_cache) *from_cache = i < (int)b->cached.size() ? b->cached[i] : 0;
     const BatchClass &K = b->classes[b->cls[i]];
     int x = 0;
     while (x < (int)K.graphs.size() && K.graphs[x] != i) ++x;

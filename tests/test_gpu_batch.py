@@ -69,3 +69,47 @@ def test_batch_matches_single(cc, autotune):
     finally:
         for g in handles:
             cc.cc_graph_free(g)
+
+
+def test_autotune_cache(cc, tmp_path):
+    """The first autotuned batch times its graphs and writes one cache line
+    per graph; a second batch of the same graphs takes every graph's
+    tuning from the file (same direction switch) and still equals the
+    single-graph calls."""
+    gens, ks = mixed_batch()
+    path = tmp_path / "tune.jsonl"
+    handles, samples, ns = [], [], []
+    try:
+        for (n, s, d), k in zip(gens, ks):
+            g, _ = cc.cc_graph_from_edges(n, s, d)
+            handles.append(g)
+            nn = cc.cc_graph_info(g)[0]
+            ns.append(nn)
+            samples.append(cc.cc_sample_choose(g, min(k, nn), 7 + k))
+        cc.cc_batch_tune_cache(path)
+        try:
+            b1 = cc.cc_batch_create(handles, samples, autotune=True)
+            p1 = [cc.cc_batch_plan(b1, i) for i in range(len(handles))]
+            cc.cc_batch_free(b1)
+            lines = path.read_text().splitlines()
+            assert len(lines) == len(handles)
+            assert not any(p["from_cache"] for p in p1)
+            b2 = cc.cc_batch_create(handles, samples, autotune=True)
+            try:
+                p2 = [cc.cc_batch_plan(b2, i) for i in range(len(handles))]
+                assert all(p["from_cache"] for p in p2)
+                assert [p["alpha"] for p in p1] == [p["alpha"] for p in p2]
+                assert len(path.read_text().splitlines()) == len(handles)
+                cc.cc_batch_run(b2)
+                for i, g in enumerate(handles):
+                    got = cc.cc_batch_result(b2, i, ns[i], len(samples[i]))
+                    want = cc.cc_estimate(g, samples[i])
+                    for key in want:
+                        assert (got[key] == want[key]).all(), (i, key)
+            finally:
+                cc.cc_batch_free(b2)
+        finally:
+            cc.cc_batch_tune_cache(None)
+    finally:
+        for g in handles:
+            cc.cc_graph_free(g)
