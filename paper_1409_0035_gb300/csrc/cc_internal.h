@@ -62,7 +62,7 @@ struct LevelCtl {
     unsigned int hlen;          // rebuilt heavy list length (bottom-up)
     unsigned int hclen;         // rebuilt heavy chunk list length (bottom-up)
     unsigned int tlen2;         // rebuilt tiny list length (bottom-up)
-    unsigned int pad_;
+    unsigned int hnext;         // next heavy chunk task to take (bottom-up)
     unsigned long long ef;      // sum of degrees of the frontier nodes
     unsigned long long eu_dec;  // sum of degrees of nodes completed
 };
