@@ -327,7 +327,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    t_total, kms, kbytes, klaunch, kall = 0.0, 0.0, 0.0, 0, 0
+    t_total, kms, kbytes, klaunch, kall, replays = 0.0, 0.0, 0.0, 0, 0, 0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
@@ -338,6 +338,7 @@ def run_ours(args):
         ev1.synchronize()
         t_total += ev0.elapsed_time(ev1)
         nl, ms, b, nk = cc.cc_last_call_timing(g)
+        replays += int(cc.cc_last_call_graph(g))
         kall += nk
         klaunch += nl
         kms += ms
@@ -415,6 +416,7 @@ def run_ours(args):
             "e2e": {"value": e2e, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
+            "steps_replaying_captured_graph": replays,
             "clocks": clk,
             "single_source_per_launch": {"value": single_gteps, "unit": "GTEPS",
                                          "sources": nsingle,

@@ -512,11 +512,21 @@ int cc_set_tuning(cc_graph_t g, int32_t alpha);
  *   CC_PARAM_REACH_WORDS      words per node of cc_reach_estimate's groups
  *                             (1, 2, 4, 8 or 16: groups of 64 x that many
  *                             sources searched together); 0 restores the
- *                             default */
+ *                             default
+ *   CC_PARAM_ESTIMATE_GRAPH   1 (default): a bit-packed cc_estimate called
+ *                             again with the same k, options and output
+ *                             buffers (and no device buffer of the library
+ *                             resized since) captures its device work --
+ *                             every kernel and memset between the sample
+ *                             upload and the output copies -- in a CUDA
+ *                             graph once and replays it on later such
+ *                             calls (one launch instead of about twenty);
+ *                             0: always launched one by one */
 #define CC_PARAM_ALPHA 0
 #define CC_PARAM_HYBRID_ONE_PASS 1
 #define CC_PARAM_SSSP_DELTA 2
 #define CC_PARAM_REACH_WORDS 3
+#define CC_PARAM_ESTIMATE_GRAPH 4
 int cc_set_param(cc_graph_t g, int32_t param, int32_t value);
 
 /* ---- diagnostics --------------------------------------------------------- */
@@ -573,12 +583,19 @@ int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
 int cc_last_call_timing(cc_graph_t g, int32_t *launches, double *kernel_ms,
                         double *alg_bytes, int32_t *all_kernels);
 
+/* *replayed = 1 when the last cc_estimate on g replayed its captured CUDA
+ * graph (CC_PARAM_ESTIMATE_GRAPH), else 0. */
+int cc_last_call_graph(cc_graph_t g, int32_t *replayed);
+
 /* Run the device-side bounded wait on a barrier that can never complete
  * (a team larger than the blocks launched) with the given limit; returns
  * CC_ERR_TIMEOUT when the wait gives up as designed. */
 int cc_selftest_barrier_timeout(uint64_t timeout_ns);
 
 const char *cc_strerror(int code);
+/* With the environment variable CC_DEBUG set, every CUDA runtime call that
+ * fails inside the library (before it is reported as CC_ERR_CUDA) is named
+ * on stderr with its source position. */
 
 #ifdef __cplusplus
 }

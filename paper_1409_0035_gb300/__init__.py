@@ -33,7 +33,8 @@ EXPORTS = (
     "cc_graph_from_edges", "cc_graph_load_csr", "cc_graph_free", "cc_graph_info",
     "cc_graph_copy_csr", "cc_sample_choose", "cc_opts_default", "cc_estimate",
     "cc_exact", "cc_sampling_sums_single", "cc_last_pass_stats",
-    "cc_last_call_timing", "cc_sampling_pivots_noalloc", "cc_last_pass_trace",
+    "cc_last_call_timing", "cc_last_call_graph", "cc_sampling_pivots_noalloc",
+    "cc_last_pass_trace",
     "cc_set_tuning", "cc_set_param", "cc_batch_create", "cc_batch_run", "cc_batch_result",
     "cc_batch_info", "cc_batch_plan", "cc_batch_tune_cache", "cc_batch_free", "cc_server_create", "cc_server_submit",
     "cc_server_wait", "cc_server_result", "cc_server_stats", "cc_server_cache_stats",
@@ -105,6 +106,7 @@ def lib():
         L.cc_last_pass_stats.argtypes = [P, P, P, P, P, P]
         L.cc_last_pass_phases.argtypes = [P, P]
         L.cc_last_call_timing.argtypes = [P, P, P, P, P]
+        L.cc_last_call_graph.argtypes = [P, P]
         L.cc_last_pass_trace.argtypes = [P, i32, P, P, P, P, P]
         L.cc_set_tuning.argtypes = [P, i32]
         L.cc_set_param.argtypes = [P, i32, i32]
@@ -376,6 +378,7 @@ def cc_set_tuning(g, alpha=0):
 
 
 CC_PARAM_ALPHA, CC_PARAM_HYBRID_ONE_PASS, CC_PARAM_SSSP_DELTA, CC_PARAM_REACH_WORDS = 0, 1, 2, 3
+CC_PARAM_ESTIMATE_GRAPH = 4
 
 
 def cc_set_param(g, param, value):
@@ -405,6 +408,13 @@ def cc_last_call_timing(g):
     _chk(lib().cc_last_call_timing(g, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
                                    ctypes.byref(a)), "cc_last_call_timing")
     return n.value, ms.value, b.value, a.value
+
+
+def cc_last_call_graph(g):
+    """True when the last cc_estimate on g replayed its captured CUDA graph."""
+    r = ctypes.c_int32()
+    _chk(lib().cc_last_call_graph(g, ctypes.byref(r)), "cc_last_call_graph")
+    return bool(r.value)
 
 
 def cc_sampling_pivots_noalloc(n, d_row_ptr, d_col, sample, d_sample_sum, d_pivot,

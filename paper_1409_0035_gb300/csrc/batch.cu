@@ -219,12 +219,14 @@ struct cc_batch {
 
 namespace {
 
-#define B_CK(x)                      \
-    do {                             \
-        if ((x) != cudaSuccess) {    \
-            cudaGetLastError();      \
-            return CC_ERR_CUDA;      \
-        }                            \
+#define B_CK(x)                                  \
+    do {                                         \
+        const cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) {                 \
+            note_cuda_error(e_, __FILE__, __LINE__); \
+            cudaGetLastError();                  \
+            return CC_ERR_CUDA;                  \
+        }                                        \
     } while (0)
 #define B_RC(x)                      \
     do {                             \

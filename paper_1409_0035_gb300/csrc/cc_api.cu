@@ -2,7 +2,10 @@
 // and the estimator pipeline (section 3, Algorithm 1: a pivot/sum pass over
 // all k sources, then the hybrid pass when eq. (4) needs per-node L(v)).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -35,12 +38,17 @@ constexpr int kReachDefaultW = 8;
 constexpr double kDeltaMult = 96.0;
 constexpr double kMaxHistBytes = 4.0 * (1ull << 30);  // distance histogram cap
 
+// Bumped whenever a device buffer is (re)allocated or freed: a captured
+// estimate graph holds raw pointers and is valid only while it is unchanged.
+std::atomic<uint64_t> g_alloc_gen{1};
+
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
     int ensure(size_t bytes)
     {
         if (bytes <= cap) return CC_OK;
+        g_alloc_gen.fetch_add(1);
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -53,6 +61,7 @@ struct DevBuf {
     }
     void release()
     {
+        if (p) g_alloc_gen.fetch_add(1);
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -143,6 +152,21 @@ struct cc_graph {
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     int pend = 0, pend_W[2] = {0, 0};
     uint32_t pend_red[2] = {0, 0};
+    // Repeated bit-packed estimates with the same arguments replay one CUDA
+    // graph of the whole call (every kernel, memset and control-block copy
+    // between the sample upload and the output copies): the call before
+    // sizes the buffers, the next one captures.  key: the arguments and
+    // buffer generation it was captured for; the queued-pass bookkeeping
+    // the capture left is restored on each replay.
+    struct EstGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cap = nullptr;
+        std::vector<uint64_t> key, seen, failed;
+        bool off = false;      // CC_PARAM_ESTIMATE_GRAPH = 0
+        int replayed = 0;      // the last call replayed exec
+        int pend = 0, pend_W[2] = {0, 0}, kernels = 0;
+        uint32_t pend_red[2] = {0, 0};
+    } eg;
 };
 
 namespace {
@@ -150,7 +174,11 @@ namespace {
 #define CK(x)                                                   \
     do {                                                        \
         cudaError_t e_ = (x);                                   \
-        if (e_ != cudaSuccess) { cudaGetLastError(); return CC_ERR_CUDA; } \
+        if (e_ != cudaSuccess) {                                \
+            note_cuda_error(e_, __FILE__, __LINE__);            \
+            cudaGetLastError();                                 \
+            return CC_ERR_CUDA;                                 \
+        }                                                       \
     } while (0)
 #define RC(x)                      \
     do {                           \
@@ -343,9 +371,13 @@ int queue_pass(cc_graph *g, int slot, int W, BfsJob j, cudaStream_t st)
     Ctl *dctl = slot == 0 ? g->ctl.as<Ctl>() : g->ctl2.as<Ctl>();
     j.ctl = dctl;
     CK(cudaMemsetAsync(dctl, 0, sizeof(Ctl), st));
-    CK(cudaEventRecord(g->pev[2 * slot], st));
+    // Inside a stream capture, a timing record must be an external one.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    const unsigned rf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    CK(cudaEventRecordWithFlags(g->pev[2 * slot], st, rf));
     RC(launch_msbfs(W, j, st, nullptr));
-    CK(cudaEventRecord(g->pev[2 * slot + 1], st));
+    CK(cudaEventRecordWithFlags(g->pev[2 * slot + 1], st, rf));
     CK(cudaMemcpyAsync(&g->hctl[slot], dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     g->pend |= 1 << slot;
     g->pend_W[slot] = W;
@@ -385,15 +417,16 @@ int run_pass(cc_graph *g, int W, const BfsJob &j, cudaStream_t st)
     return settle_passes(g);
 }
 
+// Ids in range and distinct, from a sorted copy of the k ids: the check runs
+// on every call, so it takes no per-node host array.
 int validate_sample(const cc_graph *g, const int32_t *sample, int32_t k)
 {
     if (!sample || k < 1 || k > CC_MAX_K || k > g->n) return CC_ERR_ARG;
-    std::vector<char> seen((size_t)g->n, 0);
-    for (int i = 0; i < k; ++i) {
-        const int32_t c = sample[i];
-        if (c < 0 || c >= g->n || seen[c]) return CC_ERR_ARG;
-        seen[c] = 1;
-    }
+    std::vector<int32_t> s(sample, sample + k);
+    std::sort(s.begin(), s.end());
+    if (s[0] < 0 || s[(size_t)k - 1] >= g->n) return CC_ERR_ARG;
+    for (int i = 1; i < k; ++i)
+        if (s[(size_t)i] == s[(size_t)i - 1]) return CC_ERR_ARG;
     return CC_OK;
 }
 
@@ -469,6 +502,8 @@ void free_graph(cc_graph *g)
     for (cudaEvent_t &e : g->pev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
     if (g->hctl) { cudaFreeHost(g->hctl); g->hctl = nullptr; }
+    if (g->eg.exec) { cudaGraphExecDestroy(g->eg.exec); g->eg.exec = nullptr; }
+    if (g->eg.cap) { cudaStreamDestroy(g->eg.cap); g->eg.cap = nullptr; }
 }
 
 
@@ -647,9 +682,8 @@ bool use_band(cc_graph *g, int k, const cc_opts *opts)
     return need <= ((double)free_b + (double)g->band.cap) / 3.0;
 }
 
-int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
+int estimate_bfs(cc_graph *g, int k, const cc_opts *opts, bool band, cudaStream_t st)
 {
-    const bool band = use_band(g, k, opts);
     RC(bfs_pass1(g, k, st, band ? opts->eps_num : 0, band ? opts->eps_den : 0));
     if (!opts->want_hybrid) return CC_OK;
     return bfs_hybrid(g, k, opts->eps_num, opts->eps_den, st, band);
@@ -958,12 +992,12 @@ int estimate_chunked(cc_graph *g, int k, const cc_opts *opts, cudaStream_t st)
 }
 
 // Finalise into device buffers (or straight into device outputs) and copy.
-int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
-                   cudaStream_t st)
+// Arguments of the finalisation (host only: buffers sized, no stream work).
+int prepare_finalize(cc_graph *g, int k, bool hyb, const cc_opts *opts, const cc_out *out,
+                     FinalizeArgs &fa)
 {
     const int64_t n = g->n;
     const bool dev_out = opts->device_outputs != 0;
-    FinalizeArgs fa{};
     std::memset(&fa, 0, sizeof(fa));
     fa.n = n;
     fa.k = k;
@@ -1007,15 +1041,9 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
         RC(g->pt_clo1.ensure((size_t)k * 8));
         RC(g->pt_est2.ensure((size_t)k * ts * 8));
         RC(g->pt_clo2.ensure((size_t)k * ts * 8));
-        const DevCount D = chunked ? DevCount{nullptr, g->D1}
-                                   : DevCount{&g->ctl.as<Ctl>()->levels, 0};
         // Sums of the bit-packed path are at most k * D < k * hist_cap.
         const int64_t c0 = chunked ? 0 : std::min<int64_t>((int64_t)k * g->hist_cap, 1 << 20);
         if (c0) RC(g->pt_clo0.ensure((size_t)c0 * 8));
-        run_pivot_tables(n, k, g->Ssamp.as<uint64_t>(), D, ts, g->pt_clo1.as<double>(),
-                         g->pt_est2.as<double>(), g->pt_clo2.as<double>(), fa.inv_k, c0,
-                         c0 ? g->pt_clo0.as<double>() : nullptr, st);
-        g->call_kernels += 1;
         fa.clo1 = g->pt_clo1.as<double>();
         fa.est2t = g->pt_est2.as<double>();
         fa.clo2t = g->pt_clo2.as<double>();
@@ -1035,8 +1063,34 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
         fa.dcc = g->dcc.as<uint32_t>();
         fa.istar = g->istar.as<int32_t>();
     }
+    // Every buffer the finalisation reads must exist by now (the passes and
+    // the hybrid's preparation size them); never launch it otherwise.
+    if (!fa.sidx || !fa.pivot || !fa.delta || !fa.sum2 || !fa.S_samp ||
+        (hyb && (!fa.lc2 || !fa.hp)) ||
+        (fa.sq_err && (!fa.hcse || !fa.fdist || !fa.dcc || !fa.istar)))
+        return CC_ERR_CUDA;
+    return CC_OK;
+}
+
+// The estimator tables and the finalisation kernel (stream work only).
+void enqueue_finalize(cc_graph *g, int k, const FinalizeArgs &fa, cudaStream_t st)
+{
+    const bool chunked = g->weighted || g->directed;
+    const DevCount D = chunked ? DevCount{nullptr, g->D1} : DevCount{&g->ctl.as<Ctl>()->levels, 0};
+    run_pivot_tables(g->n, k, g->Ssamp.as<uint64_t>(), D, fa.tstride, g->pt_clo1.as<double>(),
+                     g->pt_est2.as<double>(), g->pt_clo2.as<double>(), fa.inv_k, fa.c0len,
+                     fa.c0len ? g->pt_clo0.as<double>() : nullptr, st);
     run_finalize(fa, st);
-    g->call_kernels += 1;
+    g->call_kernels += 2;
+}
+
+// Copies of the outputs the caller asked for (to the host, or between
+// device buffers), then the stream is synchronised.
+int copy_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
+                 const FinalizeArgs &fa, cudaStream_t st)
+{
+    const int64_t n = g->n;
+    const bool dev_out = opts->device_outputs != 0;
     const cudaMemcpyKind kind = dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (!dev_out) {
         for (int e = 0; e < CC_NUM_EST; ++e) {
@@ -1063,7 +1117,133 @@ int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *ou
     return CC_OK;
 }
 
+int finish_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
+                   cudaStream_t st)
+{
+    FinalizeArgs fa;
+    RC(prepare_finalize(g, k, hyb, opts, out, fa));
+    enqueue_finalize(g, k, fa, st);
+    return copy_outputs(g, k, hyb, opts, out, fa, st);
+}
+
+// Everything a bit-packed estimate queues between the sample upload and the
+// output copies.  The finalisation's arguments are taken after the passes
+// are queued, once every buffer they point to is sized.
+int enqueue_bfs_estimate(cc_graph *g, int k, bool hyb, const cc_opts *opts, const cc_out *out,
+                         bool band, FinalizeArgs &fa, cudaStream_t st)
+{
+    run_fill_i32(g->sidx.as<int32_t>(), g->n, -1, st);
+    run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
+    g->call_kernels += 2;
+    RC(estimate_bfs(g, k, opts, band, st));
+    RC(prepare_finalize(g, k, hyb, opts, out, fa));
+    enqueue_finalize(g, k, fa, st);
+    return CC_OK;
+}
+
+// The arguments a captured estimate graph depends on.
+std::vector<uint64_t> est_key(const cc_graph *g, int k, const cc_opts *opts, const cc_out *out,
+                              bool band)
+{
+    std::vector<uint64_t> key = {g_alloc_gen.load(), (uint64_t)k, (uint64_t)opts->want_hybrid,
+                                 opts->eps_num, opts->eps_den, (uint64_t)opts->device_outputs,
+                                 (uint64_t)g->sq, (uint64_t)band, (uint64_t)g->hist_cap,
+                                 (uint64_t)g->alpha, (uint64_t)g->max_ctas};
+    // The finalisation writes device outputs in place (their addresses are
+    // in the graph); host outputs are copied after it, from the library's
+    // buffers, so only whether each is asked for matters.
+    auto put = [&](const void *q) {
+        key.push_back(opts->device_outputs ? (uint64_t)(uintptr_t)q : (uint64_t)(q != nullptr));
+    };
+    for (int e = 0; e < CC_NUM_EST; ++e) {
+        put(out->s_hat[e]);
+        put(out->closeness[e]);
+    }
+    put(out->hyb_int);
+    put(out->sample_sum);
+    put(out->sq_err);
+    return key;
+}
+
+// A bit-packed estimate: replayed from the captured graph when the
+// arguments and buffers match the capture, captured when they match the
+// previous call, queued directly otherwise (and whenever capture fails).
+int run_bfs_estimate(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
+                     cudaStream_t st)
+{
+    if (g->hist_cap == 0) g->hist_cap = (int)std::min<int64_t>(g->n + 1, 4096);
+    FinalizeArgs fa;
+    const bool band = use_band(g, k, opts);
+    std::vector<uint64_t> key = est_key(g, k, opts, out, band);
+    auto &E = g->eg;
+    E.replayed = 0;
+    if (E.off) {
+        RC(enqueue_bfs_estimate(g, k, hyb, opts, out, band, fa, st));
+        return copy_outputs(g, k, hyb, opts, out, fa, st);
+    }
+    if (E.exec && E.key != key) {
+        cudaGraphExecDestroy(E.exec);
+        E.exec = nullptr;
+    }
+    if (!E.exec && E.failed != key && E.seen == key) {
+        // Same arguments and buffers as the previous call: capture once.
+        if (!E.cap) CK(cudaStreamCreateWithFlags(&E.cap, cudaStreamNonBlocking));
+        const int kernels0 = g->call_kernels;
+        bool ok = cudaStreamBeginCapture(E.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) ok = enqueue_bfs_estimate(g, k, hyb, opts, out, band, fa, E.cap) == CC_OK;
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamEndCapture(E.cap, &gr) != cudaSuccess) ok = false;
+        // Buffers must not have moved during the capture (nothing is sized
+        // there once the previous call ran with the same arguments).
+        ok = ok && gr && est_key(g, k, opts, out, band) == key;
+        if (ok && cudaGraphInstantiate(&E.exec, gr, 0) != cudaSuccess) {
+            E.exec = nullptr;
+            ok = false;
+        }
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        if (ok) {
+            E.key = key;
+            E.pend = g->pend;
+            E.pend_W[0] = g->pend_W[0]; E.pend_W[1] = g->pend_W[1];
+            E.pend_red[0] = g->pend_red[0]; E.pend_red[1] = g->pend_red[1];
+            E.kernels = g->call_kernels - kernels0;
+        } else {
+            E.failed = key;  // not again for these arguments
+        }
+        g->pend = 0;
+        g->call_kernels = kernels0;
+    }
+    E.seen = key;
+    if (E.exec) {
+        // Same arguments and buffers as at the capture: sizes nothing (if
+        // it did, the graph's pointers are stale and the call runs direct).
+        RC(prepare_finalize(g, k, hyb, opts, out, fa));
+        if (g_alloc_gen.load() != key[0]) {
+            cudaGraphExecDestroy(E.exec);
+            E.exec = nullptr;
+        }
+    }
+    if (E.exec) {
+        CK(cudaGraphLaunch(E.exec, st));
+        E.replayed = 1;
+        g->pend = E.pend;
+        g->pend_W[0] = E.pend_W[0]; g->pend_W[1] = E.pend_W[1];
+        g->pend_red[0] = E.pend_red[0]; g->pend_red[1] = E.pend_red[1];
+        g->call_kernels += E.kernels;
+    } else {
+        RC(enqueue_bfs_estimate(g, k, hyb, opts, out, band, fa, st));
+    }
+    return copy_outputs(g, k, hyb, opts, out, fa, st);
+}
+
 }  // namespace
+
+void ccg::note_cuda_error(cudaError_t e, const char *file, int line)
+{
+    static const bool on = std::getenv("CC_DEBUG") != nullptr;
+    if (on) std::fprintf(stderr, "cc: %s at %s:%d\n", cudaGetErrorString(e), file, line);
+}
 
 // Point `dst` (a handle with its own workspace) at the resident CSR of
 // `src`, borrowing it: used by the server's slots.
@@ -1364,9 +1544,20 @@ int cc_set_param(cc_graph_t g, int32_t param, int32_t value)
         if (value < 0 || value > kReachMaxW || (value & (value - 1))) return CC_ERR_ARG;
         g->reach_words = value;
         return CC_OK;
+    case CC_PARAM_ESTIMATE_GRAPH:
+        if (value != 0 && value != 1) return CC_ERR_ARG;
+        g->eg.off = value == 0;
+        return CC_OK;
     default:
         return CC_ERR_ARG;
     }
+}
+
+int cc_last_call_graph(cc_graph_t g, int32_t *replayed)
+{
+    if (!g || !replayed) return CC_ERR_ARG;
+    *replayed = g->eg.replayed;
+    return CC_OK;
 }
 
 int cc_last_pass_trace(cc_graph_t g, int32_t max_levels, int64_t *level_ns,
@@ -1431,14 +1622,19 @@ int cc_estimate(cc_graph_t g, const int32_t *sample, int32_t k, const cc_opts *o
     RC(g->sources.ensure((size_t)k * 4));
     RC(g->ctl.ensure(sizeof(Ctl)));
     CK(cudaMemcpyAsync(g->sources.p, sample, (size_t)k * 4, cudaMemcpyHostToDevice, st));
-    run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
-    run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
-    g->call_kernels += 2;
     const bool hyb = opts->want_hybrid != 0;
     g->sq = hyb && out->sq_err != nullptr;
     const bool chunked = g->weighted || g->directed;
-    int rc = chunked ? estimate_chunked(g, k, opts, st) : estimate_bfs(g, k, opts, st);
-    if (rc == CC_OK) rc = finish_outputs(g, k, hyb, opts, out, st);  // synchronises
+    int rc = CC_OK;
+    if (chunked) {
+        run_fill_i32(g->sidx.as<int32_t>(), n, -1, st);
+        run_scatter_sidx(g->sidx.as<int32_t>(), g->sources.as<int32_t>(), k, st);
+        g->call_kernels += 2;
+        rc = estimate_chunked(g, k, opts, st);
+        if (rc == CC_OK) rc = finish_outputs(g, k, hyb, opts, out, st);  // synchronises
+    } else {
+        rc = run_bfs_estimate(g, k, hyb, opts, out, st);  // synchronises
+    }
     if (rc != CC_OK) {
         cudaStreamSynchronize(st);
         g->pend = 0;

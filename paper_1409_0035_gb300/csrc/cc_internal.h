@@ -161,6 +161,10 @@ struct BfsJob {
 int launch_msbfs(int W, const BfsJob &job, cudaStream_t st, int *grid_used);
 
 int launch_barrier_selftest(uint64_t timeout_ns, int *err_out);
+
+// A failed CUDA runtime call (before it is turned into CC_ERR_CUDA): named
+// on stderr with its place when the environment sets CC_DEBUG.
+void note_cuda_error(cudaError_t e, const char *file, int line);
 int msbfs_min_blocks_per_sm();
 int mssp_blocks_per_sm();
 void msbfs_set_carveout(int percent);

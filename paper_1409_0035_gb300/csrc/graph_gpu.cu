@@ -694,7 +694,9 @@ struct Buf {
     } while (0)
 #define G_CK(x)                                          \
     do {                                                 \
-        if ((x) != cudaSuccess) {                        \
+        const cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) {                         \
+            note_cuda_error(e_, __FILE__, __LINE__);     \
             cudaGetLastError();                          \
             return CC_ERR_CUDA;                          \
         }                                                \

@@ -420,8 +420,18 @@ __device__ void block_compact_put(int64_t N, Keep keep, Put put, unsigned *count
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t per = (N + team_size - 1) / team_size;
     const int64_t lo = (int64_t)team_rank * per, hi = min(N, lo + per);
-    unsigned c = 0;
-    for (int64_t i = lo + tid; i < hi; i += kBlock) c += keep(i) ? 1u : 0u;
+    // keep(i) of this thread's first 32 entries, reused by the second sweep
+    // (each test costs dependent loads).
+    unsigned c = 0, kbits = 0;
+    {
+        int j = 0;
+#pragma unroll 4
+        for (int64_t i = lo + tid; i < hi; i += kBlock, ++j) {
+            const bool k = keep(i);
+            c += k ? 1u : 0u;
+            if (k && j < 32) kbits |= 1u << j;
+        }
+    }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
     if (lane == 0) s_w[wid] = c;
@@ -433,9 +443,10 @@ __device__ void block_compact_put(int64_t N, Keep keep, Put put, unsigned *count
     }
     __syncthreads();
     unsigned base = s_base;
-    for (int64_t c0 = lo; c0 < hi; c0 += kBlock) {
+    int j = 0;
+    for (int64_t c0 = lo; c0 < hi; c0 += kBlock, ++j) {
         const int64_t i = c0 + tid;
-        const bool k = i < hi && keep(i);
+        const bool k = i < hi && (j < 32 ? ((kbits >> j) & 1u) != 0u : keep(i));
         const unsigned bal = __ballot_sync(FULL, k);
         if (lane == 0) s_w[wid] = __popc(bal);
         __syncthreads();
@@ -750,15 +761,22 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
             }
             int32_t *Tout = (Qin == J.T) ? J.Q1 : J.T;
             // P1: push the frontier words of the queued nodes.  A frontier
-            // of at most one node per warp: a warp per node (heavy nodes
-            // pushed by their chunk tasks below).
+            // of at most one node per warp: each node's entries split over
+            // S = nwarps / qn warps, so that the level takes one push step
+            // where a warp per node took several (heavy nodes pushed by
+            // their chunk tasks below).
             const bool few = qn <= nwarps;
-            for (int64_t t = gwarp; few && t < qn; t += nwarps) {
-                const int u = Qin[t];
+            const int64_t S = few && qn > 0 ? nwarps / qn : 1;
+            for (int64_t t = gwarp; few && t < qn * S; t += nwarps) {
+                const int u = Qin[t / S];
+                const int64_t part = t % S;
                 const int64_t b = rp[u], e = rp[u + 1];
                 if (J.ntH > 0 && e - b > kMediumMaxDeg) continue;
+                const int64_t per = (e - b + S - 1) / S;
+                const int64_t bb = b + part * per, ee = min(e, bb + per);
+                if (bb >= ee) continue;
                 const uint64_t f = Fin[(int64_t)u * W + w];
-                td_push<W>(J, col, f, b, e, C, Tout, A, stage);
+                td_push<W>(J, col, f, bb, ee, C, Tout, A, stage);
             }
             // Otherwise nodes of at most kLightMaxDeg entries: a lane group
             // each, NPW per warp (a grid's frontier node has 4 entries: a
@@ -1035,11 +1053,11 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const int v = J.Hch_node[ti];
                 const int64_t vw = (int64_t)v * W + w;
                 const int64_t b = J.Hch_begin[ti];
-                if (lane <= kChunk / 32) prefetch_l2(pcol + min(b + 32 * lane, J.arcs - 1));
                 const int64_t e = min(b + (int64_t)kChunk, prp[v + 1]);
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) return;
+                if (lane <= kChunk / 32) prefetch_l2(pcol + min(b + 32 * lane, e - 1));
                 const uint64_t acc = gather_scan<W, kUnrollH>(
                     pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
                         return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);

@@ -249,12 +249,14 @@ int grid_of(int64_t n)
     return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 16);
 }
 
-#define R_CK(x)                    \
-    do {                           \
-        if ((x) != cudaSuccess) {  \
-            cudaGetLastError();    \
-            return CC_ERR_CUDA;    \
-        }                          \
+#define R_CK(x)                                  \
+    do {                                         \
+        const cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) {                 \
+            note_cuda_error(e_, __FILE__, __LINE__); \
+            cudaGetLastError();                  \
+            return CC_ERR_CUDA;                  \
+        }                                        \
     } while (0)
 #define R_RC(x)                      \
     do {                             \

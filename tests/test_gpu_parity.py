@@ -340,6 +340,60 @@ def test_repeatable(cc):
         cc.cc_graph_free(g)
 
 
+def test_repeated_estimate_replays_one_graph(cc):
+    """A bit-packed estimate called again with the same arguments and device
+    output buffers replays a captured CUDA graph from the third call on:
+    every call equals the oracle, across a change of eps and back, a
+    change of the direction switch, and with capture switched off."""
+    torch = pytest.importorskip("torch")
+    n, s, d = synth.rmat_edges(12, 8, seed=3)
+    g, _, og = both(cc, n, s, d)
+    try:
+        k = 100
+        C = orc.choose_sample(og.n, k, 5)
+        dev = torch.device("cuda", 0)
+        shat = torch.zeros((4, og.n), dtype=torch.float64, device=dev)
+        clo = torch.zeros((4, og.n), dtype=torch.float64, device=dev)
+        o = cc.cc_out()
+        for e in range(4):
+            o.s_hat[e], o.closeness[e] = shat[e].data_ptr(), clo[e].data_ptr()
+        opts = cc.cc_opts_default(k)
+        opts.device_outputs = 1
+        e0 = orc.default_eps(k)
+        want = {e0: orc.estimate(og, C, eps=e0), (1, 2): orc.estimate(og, C, eps=(1, 2))}
+        replays = []
+        plan = [e0] * 4 + [(1, 2)] * 4 + [e0] * 4
+        for i, eps in enumerate(plan):
+            if i == 10:
+                cc.cc_set_tuning(g, 3)
+            opts.eps_num, opts.eps_den = eps
+            shat.zero_()
+            clo.zero_()
+            cc.cc_estimate(g, C, opts, o)
+            torch.cuda.synchronize()
+            replays.append(cc.cc_last_call_graph(g))
+            assert cc.cc_last_call_timing(g)[0] >= 1
+            for e in range(4):
+                assert_close(shat[e].cpu().numpy(), want[eps]["s_hat"][e], f"{i} s_hat[{e}]")
+                assert_close(clo[e].cpu().numpy(), want[eps]["closeness"][e], f"{i} clo[{e}]")
+        # arguments first seen run directly; their next call captures and
+        # replays; a change of eps or of the direction switch (call 10)
+        # starts over (the first call of all also sizes the buffers)
+        assert replays[:4] == [False, False, True, True], replays
+        assert replays[4] is False and replays[7] is True, replays
+        assert replays[8] is False and replays[9] is True, replays
+        assert replays[10] is False and replays[11] is True, replays
+        cc.cc_set_param(g, cc.CC_PARAM_ESTIMATE_GRAPH, 0)
+        for _ in range(3):
+            shat.zero_()
+            cc.cc_estimate(g, C, opts, o)
+            torch.cuda.synchronize()
+            assert not cc.cc_last_call_graph(g)
+            assert_close(shat[3].cpu().numpy(), want[e0]["s_hat"][3], "no graph")
+    finally:
+        cc.cc_graph_free(g)
+
+
 def check_chunked(cc, g, og, C, eps, roundtrip=False, hybrid=True):
     o = cc.cc_opts_default(len(C))
     o.eps_num, o.eps_den, o.want_hybrid, o.roundtrip = eps[0], eps[1], int(hybrid), int(roundtrip)
