@@ -98,12 +98,70 @@ struct DevCSR {
     Classes cls;
 };
 
+// Row i of the renumbered CSR is row perm[i] of (rp, col, w) with its
+// entries renumbered through iperm (same order).  A warp per row.
+__global__ void k_relabel_rows(int64_t n, const int32_t *perm, const int32_t *iperm,
+                               const int64_t *rp, const int32_t *col, const uint32_t *w,
+                               const int64_t *nrp, int32_t *ncol, uint32_t *nw)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nwp) {
+        const int32_t v = perm[i];
+        const int64_t b = rp[v], d = rp[v + 1] - b, o = nrp[i];
+        for (int64_t e = lane; e < d; e += 32) {
+            ncol[o + e] = iperm[col[b + e]];
+            nw[o + e] = w[b + e];
+        }
+    }
+}
+
+__global__ void k_map_ids(const int32_t *in, int k, const int32_t *map, int32_t *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) out[i] = map[in[i]];
+}
+
+// Breadth-first order of the nodes (from node 0, then from each node not
+// reached yet): order[i] = the node numbered i.
+void bfs_order(int64_t n, const int64_t *rp, const int32_t *col, std::vector<int32_t> &order)
+{
+    order.clear();
+    order.reserve((size_t)n);
+    std::vector<uint8_t> seen((size_t)n, 0);
+    for (int64_t s0 = 0; s0 < n; ++s0) {
+        if (seen[(size_t)s0]) continue;
+        seen[(size_t)s0] = 1;
+        size_t head = order.size();
+        order.push_back((int32_t)s0);
+        while (head < order.size()) {
+            const int32_t u = order[head++];
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t v = col[e];
+                if (!seen[(size_t)v]) {
+                    seen[(size_t)v] = 1;
+                    order.push_back(v);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 struct cc_graph {
     int64_t n = 0, arcs = 0;
     bool directed = false, weighted = false;
     DevCSR fw, rv;
+    // Undirected graphs with arc lengths: the shortest-path rounds run on
+    // lw, the CSR renumbered in breadth-first order (lw_perm: internal ->
+    // node id, lw_iperm: node id -> internal; lw_src: a chunk's sources
+    // renumbered), so that the nodes a round touches together sit together
+    // in memory; their distance rows are read back through lw_iperm.
+    DevCSR lw;
+    DevBuf lw_perm, lw_iperm, lw_src;
+    bool has_lw = false;
     // workspace
     DevBuf vis, F0, F1, nxt, Q0, Q1, T, tflag, sidx, sum2, pivot, delta, lc2, Lmask, hp,
         dcc, hist, TN, TS, Ssamp, maxd, sources, npartial, ctl, shat, clo, hyb, ssum,
@@ -465,17 +523,50 @@ int adopt_device_csr(cc_graph *g, DeviceCSR &d)
                          g->fw.col.as<int32_t>());
 }
 
+// The breadth-first renumbering of an undirected graph with arc lengths
+// (cc_graph::lw), from the host copy of its row offsets.
+int build_locality(cc_graph *g, const std::vector<int64_t> &rp)
+{
+    const int64_t n = g->n, arcs = g->arcs;
+    std::vector<int32_t> col((size_t)arcs);
+    if (arcs) CK(cudaMemcpy(col.data(), g->fw.col.p, (size_t)arcs * 4, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> perm, iperm((size_t)n);
+    bfs_order(n, rp.data(), col.data(), perm);
+    for (int64_t i = 0; i < n; ++i) iperm[(size_t)perm[(size_t)i]] = (int32_t)i;
+    std::vector<int64_t> nrp((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t v = perm[(size_t)i];
+        nrp[(size_t)i + 1] = nrp[(size_t)i] + (rp[(size_t)v + 1] - rp[(size_t)v]);
+    }
+    RC(upload(g->lw_perm, perm.data(), (size_t)n * 4));
+    RC(upload(g->lw_iperm, iperm.data(), (size_t)n * 4));
+    RC(upload(g->lw.rp, nrp.data(), ((size_t)n + 1) * 8));
+    RC(g->lw.col.ensure((size_t)std::max<int64_t>(arcs, 1) * 4));
+    RC(g->lw.w.ensure((size_t)std::max<int64_t>(arcs, 1) * 4));
+    const int64_t grid = std::min<int64_t>((n * 32 + 255) / 256, 152 * 32);
+    k_relabel_rows<<<(int)std::max<int64_t>(grid, 1), 256>>>(
+        n, g->lw_perm.as<int32_t>(), g->lw_iperm.as<int32_t>(), g->fw.rp.as<int64_t>(),
+        g->fw.col.as<int32_t>(), g->fw.w.as<uint32_t>(), g->lw.rp.as<int64_t>(),
+        g->lw.col.as<int32_t>(), g->lw.w.as<uint32_t>());
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());  // estimates may run on other streams
+    g->has_lw = true;
+    return CC_OK;
+}
+
 void free_graph(cc_graph *g)
 {
     if (g->borrowed) {  // drop the borrowed CSR pointers unfreed
-        DevBuf *csr[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
+        DevBuf *csr[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->lw.rp, &g->lw.col, &g->lw.w,
+                         &g->lw_perm, &g->lw_iperm, &g->fw.cls.L, &g->fw.cls.M,
                          &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->fw.cls.T, &g->fw.cls.Tadj,
                      &g->rv.rp, &g->rv.col,
                          &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
                          &g->rv.cls.Hb, &g->rv.cls.T, &g->rv.cls.Tadj};
         for (DevBuf *b : csr) { b->p = nullptr; b->cap = 0; }
     }
-    DevBuf *all[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->fw.cls.L, &g->fw.cls.M,
+    DevBuf *all[] = {&g->fw.rp, &g->fw.col, &g->fw.w, &g->lw.rp, &g->lw.col, &g->lw.w,
+                     &g->lw_perm, &g->lw_iperm, &g->lw_src, &g->fw.cls.L, &g->fw.cls.M,
                      &g->fw.cls.H, &g->fw.cls.Hn, &g->fw.cls.Hb, &g->fw.cls.T, &g->fw.cls.Tadj,
                      &g->rv.rp, &g->rv.col,
                      &g->rv.w, &g->rv.cls.L, &g->rv.cls.M, &g->rv.cls.H, &g->rv.cls.Hn,
@@ -763,8 +854,17 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
         }
         return CC_OK;
     }
+    // Undirected: the breadth-first renumbered CSR, sources renumbered.
+    const bool lw = g->has_lw && !g->directed;
+    if (lw) {
+        RC(g->lw_src.ensure((size_t)kc * 4));
+        k_map_ids<<<(kc + 255) / 256, 256, 0, st>>>(d_sources, kc, g->lw_iperm.as<int32_t>(),
+                                                     g->lw_src.as<int32_t>());
+        CK(cudaGetLastError());
+        g->call_kernels += 1;
+    }
     for (int dir = 0; dir < (g->directed ? 2 : 1); ++dir) {
-        const DevCSR &c = dir ? g->rv : g->fw;
+        const DevCSR &c = lw ? g->lw : dir ? g->rv : g->fw;
         SsspJob j;
         std::memset(&j, 0, sizeof(j));
         j.n = n;
@@ -772,7 +872,7 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
         j.col = c.col.as<int32_t>();
         j.w = g->weighted ? c.w.as<uint32_t>() : nullptr;
         j.kc = kc;
-        j.sources = d_sources;
+        j.sources = lw ? g->lw_src.as<int32_t>() : d_sources;
         j.dist = (dir ? g->distR : g->distF).as<uint32_t>() + off;
         j.mask = g->mask.as<unsigned long long>();
         j.spl = cw / kChunkSrc;
@@ -816,6 +916,10 @@ int run_chunk(cc_graph *g, const int32_t *d_sources, int kc, int cw, cudaStream_
     return CC_OK;
 }
 
+// Whether the chunk rows of g are indexed by the breadth-first numbering
+// (shortest-path rounds on cc_graph::lw).
+bool rows_renumbered(const cc_graph *g) { return g->weighted && g->has_lw && !g->directed; }
+
 ReduceJob base_reduce(cc_graph *g, int k, int W)
 {
     ReduceJob r;
@@ -825,6 +929,7 @@ ReduceJob base_reduce(cc_graph *g, int k, int W)
     r.W = W;
     r.distF = g->distF.as<uint32_t>();
     r.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+    r.row_of = rows_renumbered(g) ? g->lw_iperm.as<int32_t>() : nullptr;
     r.sidx = g->sidx.as<int32_t>();
     r.sum2 = g->sum2.as<uint64_t>();
     r.best = g->best.as<unsigned long long>();
@@ -1257,6 +1362,9 @@ int ccg::graph_borrow(cc_graph_t dst, cc_graph_t src)
     auto cp = [](DevBuf &d, const DevBuf &s) { d.p = s.p; d.cap = s.cap; };
     cp(dst->fw.rp, src->fw.rp); cp(dst->fw.col, src->fw.col); cp(dst->fw.w, src->fw.w);
     cp(dst->rv.rp, src->rv.rp); cp(dst->rv.col, src->rv.col); cp(dst->rv.w, src->rv.w);
+    cp(dst->lw.rp, src->lw.rp); cp(dst->lw.col, src->lw.col); cp(dst->lw.w, src->lw.w);
+    cp(dst->lw_perm, src->lw_perm); cp(dst->lw_iperm, src->lw_iperm);
+    dst->has_lw = src->has_lw;
     for (int d = 0; d < 2; ++d) {
         Classes &c = d ? dst->rv.cls : dst->fw.cls;
         const Classes &s = d ? src->rv.cls : src->fw.cls;
@@ -1415,6 +1523,7 @@ int cc_graph_from_edges(int64_t n, int64_t m, const uint32_t *src, const uint32_
         DeviceCSR d;
         rc = build_csr_device(n, m, src, dst, w, keep_component != 0, d);
         if (rc == CC_OK) rc = adopt_device_csr(g, d);
+        if (rc == CC_OK && w) rc = build_locality(g, d.rp_host);
         if (d.rp) cudaFree(d.rp);
         if (d.col) cudaFree(d.col);
         if (d.w) cudaFree(d.w);
@@ -1857,6 +1966,7 @@ int cc_estimate_node_weighted(cc_graph_t g, const int32_t *sample, int32_t k,
     std::memset(&j, 0, sizeof(j));
     j.n = n;
     j.k = k;
+    j.row_of = rows_renumbered(g) ? g->lw_iperm.as<int32_t>() : nullptr;
     j.beta = g->beta.as<uint32_t>();
     j.mu = g->nw_mu.as<uint64_t>();
     j.bsrc = g->nw_bsrc.as<uint32_t>();
@@ -2101,6 +2211,7 @@ int cc_exact(cc_graph_t g, double *closeness, uint64_t *S)
         r.k = (int)std::min<int64_t>(n, 0x7FFFFFFF);
         r.distF = g->distF.as<uint32_t>();
         r.distR = g->directed ? g->distR.as<uint32_t>() : nullptr;
+        r.row_of = rows_renumbered(g) ? g->lw_iperm.as<int32_t>() : nullptr;
         r.sidx = g->sidx.as<int32_t>();
         r.sum2 = g->sum2.as<uint64_t>();
         r.err = g->errflag.as<int>();

@@ -182,7 +182,8 @@ __global__ void k_mu(int k, const int32_t *sources, const uint32_t *beta, const 
 
 __device__ __forceinline__ uint64_t dist_at(const NwJob &J, int64_t v, int j)
 {
-    const size_t at = (size_t)v * J.ld + J.sub + j;
+    const size_t r = J.row_of ? (size_t)J.row_of[v] : (size_t)v;
+    const size_t at = r * J.ld + J.sub + j;
     uint64_t d = J.distF[at];
     if (J.distR) d += J.distR[at];
     return d;

@@ -45,6 +45,7 @@ struct NwJob {
     int64_t n;
     int k, base, kc;
     const uint32_t *distF, *distR;  // n x ld each (distR null unless round trip)
+    const int32_t *row_of;          // row of node v (null: row v)
     int ld, sub;                    // row stride; the slice's first column
     const uint32_t *beta;           // n
     const uint64_t *mu;             // k

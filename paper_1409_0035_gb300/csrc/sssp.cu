@@ -225,9 +225,10 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x)
 __device__ __forceinline__ uint64_t chunk_dist(const ReduceJob &R, int64_t v, int lane)
 {
     if (lane >= R.kc) return (uint64_t)kInf;
-    const uint64_t a = R.distF[v * R.ld + R.sub + lane];
+    const int64_t r = R.row_of ? (int64_t)R.row_of[v] : v;
+    const uint64_t a = R.distF[r * R.ld + R.sub + lane];
     if (!R.distR) return a;
-    const uint64_t b = R.distR[v * R.ld + R.sub + lane];
+    const uint64_t b = R.distR[r * R.ld + R.sub + lane];
     if (a == kInf || b == kInf) return (uint64_t)kInf;
     return a + b;
 }

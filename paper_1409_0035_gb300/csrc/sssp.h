@@ -38,6 +38,7 @@ struct ReduceJob {
     int k, kc, base, W;
     int sum_only;                   // exact mode: only sum2 and the reachability check
     const uint32_t *distF, *distR;  // n x ld each (distR NULL unless round trip)
+    const int32_t *row_of;          // row of node v (NULL: row v)
     int ld, sub;                    // row stride; this job's first column
     const int32_t *sidx;
     uint64_t *sum2;                 // n x 2
