@@ -25,6 +25,14 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef CC_MSBFS_UNROLL_H
 #define CC_MSBFS_UNROLL_H 4
 #endif
+// Heavy chunk tasks' column indices staged in shared memory by cp.async (1)
+// or read from global memory after an L2 prefetch (0).
+#ifndef CC_MSBFS_STAGE
+#define CC_MSBFS_STAGE 1
+#endif
+// Shared-memory slots of a warp's staged chunk: entries from b & ~3 (so
+// that every 16-byte copy is aligned) up to 3 past its end.
+constexpr int kHubSlots = CC_CHUNK + 8;
 // Heavy chunk tasks a warp takes from the level's counter at a time.
 #ifndef CC_MSBFS_GRAB
 #define CC_MSBFS_GRAB 4
@@ -323,15 +331,37 @@ __device__ __forceinline__ uint64_t gather_cols(const uint64_t *Fin, const int (
 // is about as large as the L2, so its loads are marked streaming (evicted
 // first) and the W-word state arrays, gathered at random, keep the L2
 // (headline kernel 0.844 -> 0.829 ms).
-template <int U>
+template <int U, bool kShared = false>
 __device__ __forceinline__ void load_row(const int32_t *__restrict__ row, int x, int len,
                                          int stride, int (&c)[U])
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int ee = x + u * stride;
-        c[u] = ee < len ? __ldcs(row + ee) : -1;
+        c[u] = ee < len ? (kShared ? row[ee] : __ldcs(row + ee)) : -1;
     }
+}
+
+// Stage the column indices col[b, e) (e - b <= kChunk) into a warp's slot
+// of kHubSlots entries in shared memory; returns the address of col[b]'s
+// copy.  Called by the whole warp.  Whole 16-byte pieces inside the array
+// go by cp.async; the at most 3 entries past the array's last whole piece
+// by plain loads.
+__device__ __forceinline__ const int32_t *stage_cols(int32_t *slot, const int32_t *col,
+                                                     int64_t arcs, int64_t b, int64_t e,
+                                                     int lane)
+{
+    const int64_t b4 = b & ~3ll;
+    const int64_t e4 = min((e + 3) & ~3ll, arcs & ~3ll);
+    for (int64_t x = b4 + 4 * lane; x < e4; x += 128) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(slot + (x - b4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(col + x)
+                     : "memory");
+    }
+    for (int64_t x = max(e4, b) + lane; x < e; x += 32) slot[x - b4] = col[x];
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    return slot + (b - b4);
 }
 
 // OR of the frontier words (word w) of the neighbours col[base + off],
@@ -341,7 +371,7 @@ __device__ __forceinline__ void load_row(const int32_t *__restrict__ row, int x,
 // uniform over lanes that share them (`done` may be warp-collective).  The
 // column indices of the next step are loaded while the current frontier
 // words are in flight: a step costs one dependent round trip, not two.
-template <int W, int U, class Done>
+template <int W, int U, bool kShared = false, class Done>
 __device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
                                                 const uint64_t *Fin, int64_t base, int off,
                                                 int64_t e, int stride, int w,
@@ -353,11 +383,11 @@ __device__ __forceinline__ uint64_t gather_scan(const int32_t *__restrict__ col,
     uint64_t acc = 0;
     unsigned wl = 0;
     int c[U];
-    load_row<U>(row, off, len, stride, c);
+    load_row<U, kShared>(row, off, len, stride, c);
     int step = 0;
     for (int t = 0; t < len; t += U * stride) {
         int cn[U];
-        load_row<U>(row, t + off + U * stride, len, stride, cn);
+        load_row<U, kShared>(row, t + off + U * stride, len, stride, cn);
         acc |= gather_cols<W, U>(Fin, c, w, wl);
         if (++step == chk) {
             step = 0;
@@ -618,7 +648,14 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
     const unsigned nb = team_size;
     const bool doHist = (J.red & RED_HIST) != 0;
 
-    __shared__ int32_t s_buf[kStage];
+    // Top-down: the touched-list stage; bottom-up heavy tasks: each warp's
+    // staged column indices (kHubSlots entries) for W <= 8 (wider variants
+    // keep their shared memory for the histogram, within the 25 % carveout
+    // a server gives every traversal variant at 4 CTAs/SM).
+    constexpr bool kStageHub = CC_MSBFS_STAGE && W <= 8;
+    constexpr int kHubN = kStageHub ? (kBlock / 32) * kHubSlots : 0;
+    constexpr int kBufN = kStage > kHubN ? kStage : kHubN;
+    __shared__ __align__(16) int32_t s_buf[kBufN];
     __shared__ unsigned s_cnt, s_base;
     const Stage stage{s_buf, &s_cnt, &s_base};
     if (threadIdx.x == 0) s_cnt = 0;
@@ -1057,11 +1094,20 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                 const uint64_t visw = J.vis[vw];
                 const uint64_t cur = J.nxt[vw];
                 if (__all_sync(FULL, (visw | cur) == ~0ull)) return;
-                if (lane <= kChunk / 32) prefetch_l2(pcol + min(b + 32 * lane, e - 1));
-                const uint64_t acc = gather_scan<W, kUnrollH>(
-                    pcol, Fin, b, grp, e, NPW, w, A.words, chk, [&](uint64_t a) {
-                        return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);
-                    });
+                auto done = [&](uint64_t a) {
+                    return __all_sync(FULL, (or_same_word<W>(a) | visw | cur) == ~0ull);
+                };
+                uint64_t acc;
+                if constexpr (kStageHub) {
+                    const int32_t *srow = stage_cols(s_buf + (threadIdx.x >> 5) * kHubSlots,
+                                                     pcol, J.arcs, b, e, lane);
+                    acc = gather_scan<W, kUnrollH, true>(srow, Fin, 0, grp, e - b, NPW, w,
+                                                         A.words, chk, done);
+                } else {
+                    if (lane <= kChunk / 32) prefetch_l2(pcol + min(b + 32 * lane, e - 1));
+                    acc = gather_scan<W, kUnrollH>(pcol, Fin, b, grp, e, NPW, w, A.words, chk,
+                                                   done);
+                }
                 const uint64_t nbits = or_same_word<W>(acc) & ~visw & ~cur;
                 if (lane < W && nbits) atomicOr((unsigned long long *)&J.nxt[vw], nbits);
             };
