@@ -28,11 +28,21 @@ namespace ccg {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
+// Arcs of a queued node relaxed together: their column indices, lengths,
+// neighbour labels and atomicMins are each in flight at once, so a node
+// of a few arcs costs one chain of dependent accesses, not one per arc.
+#ifndef CC_MSSP_ARCS
+#define CC_MSSP_ARCS 3
+#endif
+#ifndef CC_MSSP_MIN_CTAS
+#define CC_MSSP_MIN_CTAS 4
+#endif
+constexpr int kArcs = CC_MSSP_ARCS;
 
 // Sources per row: 32 * SPL (SPL = 1 or 2), lane l holding sources l and
 // l + 32 of the chunk; masks are 64-bit either way.
 template <int SPL>
-__global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
+__global__ void __launch_bounds__(kBlock, CC_MSSP_MIN_CTAS) mssp_kernel(SsspJob J)
 {
     constexpr int LD = 32 * SPL;  // row stride
     const int lane = threadIdx.x & 31;
@@ -110,6 +120,8 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
         const unsigned fst = epoch + 1u;        // stamp: in this epoch's far queue
         for (int64_t t = gwarp; t < (int64_t)qn; t += nwarps) {
             const int u = Qin[t];
+            // the row offsets do not depend on the mask: in flight with it
+            const int64_t b = J.rp[u], e = J.rp[u + 1];
             unsigned long long m = 0;
             if (lane == 0) m = atomicExch(&J.mask[u], 0ull);
             m = __shfl_sync(FULL, m, 0);
@@ -127,8 +139,8 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
                 const bool pending = (m >> i) & 1ull;
                 du[q] = pending ? __ldcg(J.dist + (int64_t)u * LD + i) : 0ull;
                 active[q] = pending && du[q] < T;
-                const unsigned b = __ballot_sync(FULL, pending && !active[q]);
-                later |= (unsigned long long)b << (32 * q);
+                const unsigned bl = __ballot_sync(FULL, pending && !active[q]);
+                later |= (unsigned long long)bl << (32 * q);
                 if (pending && !active[q]) lo = du[q] < lo ? du[q] : lo;
             }
             if (later) {
@@ -148,51 +160,77 @@ __global__ void __launch_bounds__(kBlock) mssp_kernel(SsspJob J)
 #pragma unroll
             for (int q = 0; q < SPL; ++q) any |= active[q];
             if (!__any_sync(FULL, any)) continue;
-            const int64_t b = J.rp[u], e = J.rp[u + 1];
-            for (int64_t x = b; x < e; ++x) {
-                const int v = __ldg(J.col + x);
-                const uint64_t wt = J.w ? (uint64_t)__ldg(J.w + x) : 1ull;
-                unsigned long long nbits = 0, fbits = 0, flo = ~0ull;
+            for (int64_t x0 = b; x0 < e; x0 += kArcs) {
+                int vv[kArcs];
+                uint32_t wt[kArcs];
 #pragma unroll
-                for (int q = 0; q < SPL; ++q) {
-                    bool imp = false;
-                    uint64_t nd = 0;
-                    if (active[q]) {
-                        nd = du[q] + wt;
+                for (int j = 0; j < kArcs; ++j) {
+                    const int64_t x = x0 + j;
+                    vv[j] = x < e ? __ldg(J.col + x) : -1;
+                    wt[j] = x < e && J.w ? __ldg(J.w + x) : 1u;
+                }
+                // Neighbour labels (a possibly stale L1 copy only lets more
+                // candidates through: labels only fall), then the atomicMins
+                // of every candidate: imp bit j * SPL + q = label improved.
+                unsigned cur[kArcs][SPL];
+#pragma unroll
+                for (int j = 0; j < kArcs; ++j)
+#pragma unroll
+                    for (int q = 0; q < SPL; ++q)
+                        cur[j][q] = vv[j] >= 0 && active[q]
+                                        ? J.dist[(int64_t)vv[j] * LD + lane + 32 * q]
+                                        : 0u;
+                unsigned imp = 0;
+#pragma unroll
+                for (int j = 0; j < kArcs; ++j)
+#pragma unroll
+                    for (int q = 0; q < SPL; ++q) {
+                        if (vv[j] < 0 || !active[q]) continue;
+                        const uint64_t nd = du[q] + wt[j];
                         relax += 1;
                         if (nd >= (uint64_t)kInf) {
                             atomicCAS(&ctl->err, 0, CC_ERR_TOO_LARGE);
-                        } else {
-                            unsigned *slot = &J.dist[(int64_t)v * LD + lane + 32 * q];
-                            if ((unsigned)nd < *slot)
-                                imp = (unsigned)nd < atomicMin(slot, (unsigned)nd);
+                        } else if ((unsigned)nd < cur[j][q]) {
+                            unsigned *slot = &J.dist[(int64_t)vv[j] * LD + lane + 32 * q];
+                            if ((unsigned)nd < atomicMin(slot, (unsigned)nd))
+                                imp |= 1u << (j * SPL + q);
                         }
                     }
-                    nbits |= (unsigned long long)__ballot_sync(FULL, imp && nd < T) << (32 * q);
-                    fbits |= (unsigned long long)__ballot_sync(FULL, imp && nd >= T) << (32 * q);
-                    if (imp && nd >= T) flo = nd < flo ? nd : flo;
-                }
-                if (!(nbits | fbits)) continue;
-                if (!delta) {  // no buckets: one queue
-                    if (lane == 0 && atomicOr(&J.mask[v], nbits | fbits) == 0ull)
-                        stage_push(stage, v, Qout, qout_len);
-                    continue;
-                }
-                if (fbits) {
 #pragma unroll
-                    for (int o = 16; o >= 1; o >>= 1) {
-                        const unsigned long long y = __shfl_xor_sync(FULL, flo, o);
-                        flo = y < flo ? y : flo;
+                for (int j = 0; j < kArcs; ++j) {
+                    if (vv[j] < 0) break;  // uniform over the warp
+                    const int v = vv[j];
+                    unsigned long long nbits = 0, fbits = 0, flo = ~0ull;
+#pragma unroll
+                    for (int q = 0; q < SPL; ++q) {
+                        const bool im = (imp >> (j * SPL + q)) & 1u;
+                        const uint64_t nd = du[q] + wt[j];
+                        nbits |= (unsigned long long)__ballot_sync(FULL, im && nd < T) << (32 * q);
+                        fbits |= (unsigned long long)__ballot_sync(FULL, im && nd >= T) << (32 * q);
+                        if (im && nd >= T) flo = nd < flo ? nd : flo;
                     }
-                }
-                if (lane == 0) {
-                    atomicOr(&J.mask[v], nbits | fbits);
-                    if (nbits && atomicExch(&J.nstamp[v], nst) != nst)
-                        stage_push(stage, v, Qout, qout_len);
+                    if (!(nbits | fbits)) continue;
+                    if (!delta) {  // no buckets: one queue
+                        if (lane == 0 && atomicOr(&J.mask[v], nbits | fbits) == 0ull)
+                            stage_push(stage, v, Qout, qout_len);
+                        continue;
+                    }
                     if (fbits) {
-                        atomicMin(&ctl->far_min[epoch % 3], flo);
-                        if (atomicExch(&J.fstamp[v], fst) != fst)
-                            stage_push(fstage, v, Fout, fout_len);
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) {
+                            const unsigned long long y = __shfl_xor_sync(FULL, flo, o);
+                            flo = y < flo ? y : flo;
+                        }
+                    }
+                    if (lane == 0) {
+                        atomicOr(&J.mask[v], nbits | fbits);
+                        if (nbits && atomicExch(&J.nstamp[v], nst) != nst)
+                            stage_push(stage, v, Qout, qout_len);
+                        if (fbits) {
+                            atomicMin(&ctl->far_min[epoch % 3], flo);
+                            if (atomicExch(&J.fstamp[v], fst) != fst)
+                                stage_push(fstage, v, Fout, fout_len);
+                        }
                     }
                 }
             }
