@@ -55,6 +55,9 @@ def parse():
                     help="serve workload: graph pool (paper: R-MAT scales 12..22, grids "
                          "256^2..4096^2, the serving configuration; small: R-MAT to scale "
                          "20, grids to 2048^2)")
+    ap.add_argument("--road-nodes", type=int, default=4 << 20,
+                    help="road4m workload: points of the road-like graph (a smaller "
+                         "graph for profiling runs)")
     ap.add_argument("--workload", default="rmat20",
                     choices=["rmat20", "config1", "batch64", "road4m", "rt22", "serve", "adaptive",
                              "nodeweighted", "reach", "grid"],
@@ -815,7 +818,7 @@ def run_extra(args):
         cc.cc_graph_free(g)
     elif args.workload in ("road4m", "rt22", "config1"):
         if args.workload == "road4m":
-            n, s, d, length = synth.road_like_edges(4 << 20, seed=1)
+            n, s, d, length = synth.road_like_edges(args.road_nodes, seed=1)
             variants = [("round(1000 len)+1", synth.edge_lengths_to_weights(length, 1e3)),
                         ("round(1e6 len)+1", synth.edge_lengths_to_weights(length, 1e6))]
             k, directed = 64, False

@@ -340,6 +340,24 @@ def test_repeatable(cc):
         cc.cc_graph_free(g)
 
 
+@pytest.mark.parametrize("k", [100, 301])
+def test_hub_row_at_the_end_of_the_csr(cc, k):
+    """A hub whose row is the last of the CSR, with an arc count that is not
+    a multiple of 4: its last 256-entry chunk ends inside the array's last
+    16 bytes, so the bottom-up scan stages those entries by plain loads
+    (k = 100: level 1 is bottom-up and the hub pulls from its leaves)."""
+    n = 302
+    s = np.arange(n - 1, dtype=np.uint32)
+    d = np.full(n - 1, n - 1, np.uint32)
+    g, _, og = both(cc, n, s, d)
+    try:
+        assert cc.cc_graph_info(g)[1] % 4 == 2
+        C = orc.choose_sample(og.n, k, 3)
+        check_estimate(cc, g, og, C, orc.default_eps(k))
+    finally:
+        cc.cc_graph_free(g)
+
+
 def test_repeated_estimate_replays_one_graph(cc):
     """A bit-packed estimate called again with the same arguments and device
     output buffers replays a captured CUDA graph from the third call on:
