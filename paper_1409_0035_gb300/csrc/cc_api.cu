@@ -1143,12 +1143,12 @@ int prepare_finalize(cc_graph *g, int k, bool hyb, const cc_opts *opts, const cc
     {
         const bool chunked = g->weighted || g->directed;
         const int64_t ts = std::min<int64_t>(chunked ? g->D1 + 1 : g->hist_cap, 256);
-        RC(g->pt_clo1.ensure((size_t)k * 8));
+        RC(g->pt_clo1.ensure((size_t)k * 16));
         RC(g->pt_est2.ensure((size_t)k * ts * 8));
         RC(g->pt_clo2.ensure((size_t)k * ts * 8));
         // Sums of the bit-packed path are at most k * D < k * hist_cap.
         const int64_t c0 = chunked ? 0 : std::min<int64_t>((int64_t)k * g->hist_cap, 1 << 20);
-        if (c0) RC(g->pt_clo0.ensure((size_t)c0 * 8));
+        if (c0) RC(g->pt_clo0.ensure((size_t)c0 * 16));
         fa.clo1 = g->pt_clo1.as<double>();
         fa.est2t = g->pt_est2.as<double>();
         fa.clo2t = g->pt_clo2.as<double>();

@@ -170,10 +170,12 @@ void run_adaptive_select(int64_t n, int e, const int32_t *sidx, const double *es
                                                         choice);
 }
 
-// clo1[p] = (n-1)/S(c_p); est2t / clo2t[p * tstride + d] = S(c_p) + (n-1) d
-// and its closeness, for d <= D (the pivoting estimators take only these
-// values); clo0t[s] = the sampling estimate's closeness for sum s (0 < s <
-// c0len, s <= k D), computed exactly as the finalisation would.
+// clo1[2p, 2p+1] = S(c_p) and (n-1)/S(c_p); est2t / clo2t[p * tstride + d]
+// = S(c_p) + (n-1) d and its closeness, for d <= D (the pivoting estimators
+// take only these values); clo0t[2s, 2s+1] = the sampling estimate and its
+// closeness for sum s (0 < s < c0len, s <= k D), computed exactly as the
+// finalisation would.  The pairs make a finalisation of a graph of small
+// diameter table lookups only (FP64 is slow on this part).
 __global__ void k_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCount D,
                                int64_t tstride, double *clo1, double *est2t, double *clo2t,
                                double inv_k, int64_t c0len, double *clo0t)
@@ -184,7 +186,8 @@ __global__ void k_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCoun
     for (int64_t s = GSTART + 1; s < smax; s += GSTRIDE) {
         const double x0 = u128_to_double((u128)nm1 * (uint64_t)s);
         const double e0 = inv_k != 0.0 ? x0 * inv_k : x0 / (double)k;
-        clo0t[s] = (double)nm1 / e0;
+        clo0t[2 * s] = e0;
+        clo0t[2 * s + 1] = (double)nm1 / e0;
     }
     const int64_t dn = min(tstride, Dv + 1);  // distances 0 .. dn-1 per pivot
     for (int64_t q = GSTART; q < (int64_t)k * dn; q += GSTRIDE) {
@@ -194,7 +197,10 @@ __global__ void k_pivot_tables(int64_t n, int k, const uint64_t *S_samp, DevCoun
         const double e2 = u128_to_double((u128)Sp + (u128)nm1 * (uint64_t)d);
         est2t[i] = e2;
         clo2t[i] = (double)nm1 / e2;
-        if (d == 0) clo1[p] = (double)nm1 / (double)Sp;
+        if (d == 0) {
+            clo1[2 * p] = (double)Sp;
+            clo1[2 * p + 1] = (double)nm1 / (double)Sp;
+        }
     }
 }
 

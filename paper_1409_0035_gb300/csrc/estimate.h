@@ -48,12 +48,14 @@ struct FinalizeArgs {
     const int32_t *istar;
     // Optional shortcuts, bit-identical to the divisions they replace:
     // inv_k = 1/k when k is a power of two (then x/k = x * inv_k exactly);
-    // clo1[p] = (n-1)/S(c_p); est2t / clo2t[p * tstride + d] = the pivoting
-    // upper bound S(c_p) + (n-1) d and its closeness, for d < tstride.
+    // clo1[2p, 2p+1] = S(c_p), (n-1)/S(c_p); est2t / clo2t[p * tstride + d] =
+    // the pivoting upper bound S(c_p) + (n-1) d and its closeness, for
+    // d < tstride.
     double inv_k;
     const double *clo1, *est2t, *clo2t;
     int64_t tstride;
-    // clo0t[s] = the sampling estimate's closeness for sum s < c0len.
+    // clo0t[2s, 2s+1] = the sampling estimate and its closeness for sum s,
+    // 0 < s < c0len.
     const double *clo0t;
     int64_t c0len;
 };

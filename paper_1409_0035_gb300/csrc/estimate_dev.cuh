@@ -267,16 +267,20 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
         } else {
             const int p = A.pivot[v];
             const uint64_t Sp = A.S_samp[p];
-            const double x0 = u128_to_double((u128)nm1 * sum);
-            est[0] = A.inv_k != 0.0 ? x0 * A.inv_k : x0 / (double)A.k;
+            const bool t0 = A.clo0t && sum > 0 && sum < (uint64_t)A.c0len;
+            if (t0) {
+                est[0] = A.clo0t[2 * sum];
+            } else {
+                const double x0 = u128_to_double((u128)nm1 * sum);
+                est[0] = A.inv_k != 0.0 ? x0 * A.inv_k : x0 / (double)A.k;
+            }
             // closeness of the sampling estimate, also reused by the hybrid
             auto clo_sampling = [&]() {
-                return (A.clo0t && sum < (uint64_t)A.c0len) ? A.clo0t[sum]
-                                                            : (double)nm1 / est[0];
+                return t0 ? A.clo0t[2 * sum + 1] : (double)nm1 / est[0];
             };
             clo[0] = A.clo[0] ? clo_sampling() : 0.0;
-            est[1] = (double)Sp;
-            clo[1] = A.clo1 ? A.clo1[p] : (A.clo[1] ? (double)nm1 / est[1] : 0.0);
+            est[1] = A.clo1 ? A.clo1[2 * p] : (double)Sp;
+            clo[1] = A.clo1 ? A.clo1[2 * p + 1] : (A.clo[1] ? (double)nm1 / est[1] : 0.0);
             const uint32_t d = A.delta[v];
             if (A.est2t && d < A.tstride) {
                 est[2] = A.est2t[(int64_t)p * A.tstride + d];
