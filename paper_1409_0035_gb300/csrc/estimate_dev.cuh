@@ -344,6 +344,8 @@ __device__ __forceinline__ void d_finalize(FinalizeArgs A, int64_t i0,
         if (A.hyb_int && A.hybrid)
             for (int q = 0; q < 6; ++q) A.hyb_int[6 * v + q] = h6[q];
         if (A.sample_sum) A.sample_sum[v] = sum;
+        if (A.pivot_out) A.pivot_out[v] = A.pivot[v];
+        if (A.delta_out) A.delta_out[v] = A.delta[v];
     }
 }
 

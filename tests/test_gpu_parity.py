@@ -358,6 +358,45 @@ def test_hub_row_at_the_end_of_the_csr(cc, k):
         cc.cc_graph_free(g)
 
 
+def test_pinned_host_outputs(cc):
+    """Pinned host output buffers get the same values as pageable ones, on
+    every repeat (the repeats replay the captured graph)."""
+    torch = pytest.importorskip("torch")
+    n, s, d = synth.rmat_edges(12, 16, seed=7)
+    g, _, og = both(cc, n, s, d)
+    try:
+        k = 200
+        C = orc.choose_sample(og.n, k, 9)
+        want = cc.cc_estimate(g, C)
+        nn = og.n
+        host = {"s_hat": torch.empty((4, nn), dtype=torch.float64, pin_memory=True),
+                "closeness": torch.empty((4, nn), dtype=torch.float64, pin_memory=True),
+                "pivot": torch.empty(nn, dtype=torch.int32, pin_memory=True),
+                "delta": torch.empty(nn, dtype=torch.int32, pin_memory=True),
+                "sum": torch.empty(nn, dtype=torch.int64, pin_memory=True),
+                "hyb": torch.empty((nn, 6), dtype=torch.int64, pin_memory=True)}
+        o = cc.cc_out()
+        for e in range(4):
+            o.s_hat[e] = host["s_hat"][e].data_ptr()
+            o.closeness[e] = host["closeness"][e].data_ptr()
+        o.pivot, o.delta = host["pivot"].data_ptr(), host["delta"].data_ptr()
+        o.sample_sum, o.hyb_int = host["sum"].data_ptr(), host["hyb"].data_ptr()
+        opts = cc.cc_opts_default(k)
+        for rep in range(4):
+            for t in host.values():
+                t.zero_()
+            cc.cc_estimate(g, C, opts, o)
+            assert (host["s_hat"].numpy() == want["s_hat"]).all(), rep
+            assert (host["closeness"].numpy() == want["closeness"]).all(), rep
+            assert (host["pivot"].numpy() == want["pivot"]).all(), rep
+            assert (host["delta"].numpy().view(np.uint32) == want["delta"]).all(), rep
+            assert (host["sum"].numpy().view(np.uint64) == want["sum"]).all(), rep
+            assert (host["hyb"].numpy().view(np.uint64) == want["hyb"]).all(), rep
+        assert cc.cc_last_call_graph(g)
+    finally:
+        cc.cc_graph_free(g)
+
+
 def test_repeated_estimate_replays_one_graph(cc):
     """A bit-packed estimate called again with the same arguments and device
     output buffers replays a captured CUDA graph from the third call on:
@@ -372,9 +411,12 @@ def test_repeated_estimate_replays_one_graph(cc):
         dev = torch.device("cuda", 0)
         shat = torch.zeros((4, og.n), dtype=torch.float64, device=dev)
         clo = torch.zeros((4, og.n), dtype=torch.float64, device=dev)
+        piv = torch.zeros(og.n, dtype=torch.int32, device=dev)
+        dlt = torch.zeros(og.n, dtype=torch.int32, device=dev)
         o = cc.cc_out()
         for e in range(4):
             o.s_hat[e], o.closeness[e] = shat[e].data_ptr(), clo[e].data_ptr()
+        o.pivot, o.delta = piv.data_ptr(), dlt.data_ptr()
         opts = cc.cc_opts_default(k)
         opts.device_outputs = 1
         e0 = orc.default_eps(k)
@@ -387,9 +429,13 @@ def test_repeated_estimate_replays_one_graph(cc):
             opts.eps_num, opts.eps_den = eps
             shat.zero_()
             clo.zero_()
+            piv.zero_()
+            dlt.zero_()
             cc.cc_estimate(g, C, opts, o)
             torch.cuda.synchronize()
             replays.append(cc.cc_last_call_graph(g))
+            assert (piv.cpu().numpy() == want[eps]["pivot"]).all(), i
+            assert (dlt.cpu().numpy().view(np.uint32) == want[eps]["delta"]).all(), i
             assert cc.cc_last_call_timing(g)[0] >= 1
             for e in range(4):
                 assert_close(shat[e].cpu().numpy(), want[eps]["s_hat"][e], f"{i} s_hat[{e}]")
