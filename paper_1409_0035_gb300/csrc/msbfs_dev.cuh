@@ -1078,11 +1078,14 @@ __device__ void bfs_pass(const BfsJob &J, unsigned team_rank, unsigned team_size
                                s_hist, false);
             }
             lap(CC_PH_BU_MEDIUM);
-            // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.  A task's
-            // column indices stream from DRAM one 128-byte line per step (the
-            // CSR does not stay in the L2), so its lines are prefetched to the
-            // L2 when it starts: a step then waits for the L2, not the DRAM
-            // (headline traversal 0.831 -> 0.803 ms).
+            // A3: heavy nodes, 256-entry warp tasks OR-ing into nxt.  Read in
+            // place, a task's column indices would stream from DRAM one
+            // 128-byte line per scan step (the CSR does not stay in the L2):
+            // a task that still scans stages its chunk of the hub's adjacency
+            // in the warp's slice of shared memory first (W <= 8) or
+            // prefetches its lines to the L2 (wider variants), so that a
+            // step waits only for its frontier gathers (headline traversal:
+            // prefetch 0.831 -> 0.803 ms, staging instead 0.779 -> 0.763).
             const int32_t *const HCcur = s_al.HC;
             const int64_t hc_len = s_al.nHC;
             auto heavy_task = [&](int64_t t) {
