@@ -251,9 +251,10 @@ class Clocks:
 
 
 def kernel_source_sha():
-    """sha256 over the traversal kernel's sources."""
+    """sha256 over the traversal kernel's sources (with the header of its
+    build-time constants)."""
     h = hashlib.sha256()
-    for f in ("msbfs_dev.cuh", "msbfs.cu"):
+    for f in ("msbfs_dev.cuh", "msbfs.cu", "cc_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1409_0035_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

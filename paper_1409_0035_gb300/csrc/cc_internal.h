@@ -12,8 +12,10 @@ namespace ccg {
 
 constexpr int kBlock = 256;          // threads per CTA of the traversal kernel
 // Degree classes of the traversal (build-time tunables).
+// Medium nodes (a warp each, no chunk tasks) up to 256 arcs: headline
+// traversal 0.761 ms at 128, 0.740-0.747 at 256 and 384, 0.755 at 512.
 #ifndef CC_MEDIUM_MAX_DEG
-#define CC_MEDIUM_MAX_DEG 128
+#define CC_MEDIUM_MAX_DEG 256
 #endif
 #ifndef CC_CHUNK
 #define CC_CHUNK 256

@@ -25,9 +25,9 @@ def dist_table(og, sources, roundtrip=False):
     return np.concatenate(pmap(lambda c: orc.dist_table(og, c, roundtrip), chunks), axis=0)
 
 
-def picks(degree, sample, seed, hubs=20, per_class=45, bounds=(4, 32, 128), extra=()):
+def picks(degree, sample, seed, hubs=20, per_class=45, bounds=(4, 32, 256), extra=()):
     """Sorted distinct nodes: the `hubs` highest degrees, `per_class`
-    random nodes from each degree class (<= 4, <= 32, <= 128, larger: the
+    random nodes from each degree class (<= 4, <= 32, <= 256, larger: the
     tiny, light, medium and heavy nodes of the traversal), the first and
     last sampled nodes and `extra`."""
     deg = np.asarray(degree)
