@@ -25,6 +25,8 @@ CC_ERR_CUDA = -6
 CC_ERR_TOO_LARGE = -7
 CC_ERR_NO_DEVICE = -8
 CC_MAX_K = 2048
+# estimators (index of cc_out.s_hat / closeness and of the result arrays)
+CC_EST_SAMPLING, CC_EST_PIVOTING, CC_EST_PIVOT_UPPER, CC_EST_HYBRID = 0, 1, 2, 3
 CC_NUM_EST = 4
 EST_NAMES = ("sampling", "pivoting", "pivot_upper", "hybrid")
 

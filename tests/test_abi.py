@@ -61,3 +61,17 @@ def test_graph_build_without_device_reports_no_device(lib):
     with pytest.raises(cc.CCError) as e:
         cc.cc_graph_from_edges(3, np.array([0, 1]), np.array([1, 2]))
     assert e.value.code == cc.CC_ERR_NO_DEVICE
+
+
+def test_binding_constants_match_the_header():
+    """Every CC_* constant the binding defines equals the header's #define
+    of the same name (error codes, estimator indices, parameters, limits)."""
+    import paper_1409_0035_gb300 as cc
+    text = open(os.path.join(ROOT, "include", "cc.h")).read()
+    defines = {m.group(1): int(m.group(2))
+               for m in re.finditer(r"#define\s+(CC_\w+)\s+\(?(-?\d+)\)?", text)}
+    names = [n for n in dir(cc) if n.startswith("CC_") and isinstance(getattr(cc, n), int)]
+    assert len(names) >= 20
+    for n in names:
+        assert n in defines, n
+        assert getattr(cc, n) == defines[n], n
